@@ -1,0 +1,318 @@
+/*
+ * fgs.h -- C ABI of the GB300 (sm_103a) Fourier-seeded Gaussian-splatting mapping path.
+ *
+ * The paper (FGS-SLAM, arXiv 2503.01109) optimises a dense map of 3D Gaussians
+ * G{mu, S, R, alpha, c} (Sec. III) by rasterisation rendering (eq1) and seeds new
+ * Gaussians where a Fourier high-pass of the frame says detail lives (Sec. III-A,
+ * eq2-eq11).  This library is that data-parallel path: every entry point launches
+ * hand-written CUDA kernels on the caller's stream.
+ *
+ * Equations are named by their LaTeX labels eq1..eq16.  The paper has no eq6, so
+ * from eq7 on the printed equation number is one less than the label.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every pointer named d_* or documented as "device" is device memory owned by
+ *    the caller.  Host structs (fgs_camera, fgs_gaussians, ...) are read during the
+ *    call only; the device pointers inside them must stay valid until the stream
+ *    work completes.  The library never allocates device memory: scratch comes
+ *    from caller-given workspace (size queried with the *_workspace_size calls).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous, never synchronise the host, and can be captured
+ *    into a CUDA graph.
+ *  - The return value reports argument and launch errors (fgs_status).  On a
+ *    non-zero return nothing was launched or the launch failed; the message is in
+ *    fgs_last_error() (thread-local).  No C++ exception crosses the ABI.
+ *  - Conditions found on the device (capacity exceeded, bounded wait timed out,
+ *    non-finite value) are OR-ed as FGS_DEV_* bits into *d_status (int32 device
+ *    word).  The caller reads it after synchronising; outputs of a call that set
+ *    a bit are not valid.
+ *  - Camera model: pinhole, OpenCV axes (x right, y down, z forward), pixel (x, y)
+ *    centred at integer coordinates, world_to_cam = [R | t] row-major 3x4.
+ *  - Gaussian parameters are structure-of-arrays planes of float32 with plane
+ *    stride `capacity`: means[3][cap], log_scales[3][cap], quats[4][cap] (w, x, y,
+ *    z; normalised inside the kernels), opacity_logits[cap], rgb[3][cap] (colour
+ *    directly, spherical-harmonics degree 0).  Scale = exp(log_scale), opacity =
+ *    sigmoid(logit).
+ *  - Multi-view images are concatenated view after view: view v starts at pixel
+ *    offset sum_{u<v} W_u H_u; colour planes of a view are [3][H_v][W_v].
+ *  - Tiles of every view are numbered globally: view v's tiles start at
+ *    sum_{u<v} tiles_x(u) * tiles_y(u), row-major inside the view.
+ */
+#ifndef FGS_H
+#define FGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FGS_VERSION 100
+
+typedef int32_t fgs_status;
+enum {
+  FGS_OK = 0,
+  FGS_ERR_INVALID_ARGUMENT = 1,
+  FGS_ERR_CUDA = 2,
+  FGS_ERR_CAPACITY = 3,
+  FGS_ERR_TIMEOUT = 4,
+  FGS_ERR_UNSUPPORTED = 5,
+  FGS_ERR_NONFINITE = 6
+};
+
+/* Bits OR-ed into the device status word. */
+enum {
+  FGS_DEV_PAIR_OVERFLOW = 1, /* (tile, Gaussian) pairs exceeded pair_capacity        */
+  FGS_DEV_TIMEOUT = 2,       /* a bounded device wait gave up                         */
+  FGS_DEV_NONFINITE = 4,     /* a non-finite value was met where one is not allowed   */
+  FGS_DEV_MAP_FULL = 8,      /* seeding wanted more Gaussians than the map capacity   */
+  FGS_DEV_WORK_OVERFLOW = 16 /* a window work list exceeded its capacity              */
+};
+
+#define FGS_MAX_VIEWS 16
+
+typedef struct {
+  int32_t width, height;
+  float fx, fy, cx, cy;
+  float world_to_cam[12]; /* row-major [R | t] */
+  float znear;            /* Gaussians with camera z < znear are culled */
+} fgs_camera;
+
+typedef struct {
+  int64_t n;             /* Gaussians in use (host count, or upper bound when d_n is set) */
+  int64_t capacity;      /* plane stride in elements                                     */
+  int64_t *d_n;          /* optional device count (<= n); NULL = use n                     */
+  float *means;          /* [3][capacity]                                                 */
+  float *log_scales;     /* [3][capacity]                                                 */
+  float *quats;          /* [4][capacity]  w, x, y, z                                     */
+  float *opacity_logits; /* [capacity]                                                    */
+  float *rgb;            /* [3][capacity]                                                 */
+} fgs_gaussians;
+
+/* Per-view screen-space splats (the "2D projection" of Sec. III).  Record r of
+ * view v lives at index v * stride + r. */
+typedef struct {
+  int64_t stride;   /* records per view (>= the Gaussians' n)                          */
+  float *splat;     /* [n_views][stride][8]: mean2d.x, mean2d.y, conic a, b, c,       */
+                    /*   opacity, depth (camera z), unused                              */
+  int32_t *radius;  /* [n_views][stride]  ceil(3 sqrt(lambda_max)); 0 = culled          */
+  uint16_t *rect;   /* [n_views][stride][4] inclusive tile bounds x0, y0, x1, y1        */
+                    /*   (x0 > x1 = touches no tile)                                    */
+} fgs_projected;
+
+typedef struct {
+  int32_t tile_w, tile_h; /* 8x8, 16x16 or 16x32 (w x h)                             */
+  int32_t batch_depth;    /* Gaussians staged per shared-memory batch: 32..256, pow2  */
+} fgs_tiling;
+
+/* ---------------------------------------------------------------------------------
+ * fgs_project -- EWA projection of every Gaussian into every view (Sec. III: the
+ * covariance C = R S S^T R^T and its 2D projection that eq1 blends).
+ *   p = R_cam mu + t; culled if p.z < znear.
+ *   Sigma' = J R_cam C R_cam^T J^T + 0.3 I, J the perspective Jacobian at p with
+ *   x/z, y/z clamped to +-1.3 tan(half field of view).  conic = Sigma'^-1.
+ *   mean2d = (fx x/z + cx, fy y/z + cy); radius = ceil(3 sqrt(lambda_max(Sigma')));
+ *   rect = tiles whose pixel-centre box meets [mean2d -+ 3 sqrt(diag Sigma')].
+ *   opacity = sigmoid(logit).
+ * in : g (n Gaussians), cams[n_views] (host), tiling.
+ * out: out->splat/radius/rect for n_views x g->n records (stride out->stride >= n).
+ * err: INVALID_ARGUMENT for n_views outside 1..FGS_MAX_VIEWS, bad tiling, NULLs. */
+fgs_status fgs_project(const fgs_gaussians *g, const fgs_camera *cams, int32_t n_views,
+                       fgs_tiling tiling, fgs_projected *out, int32_t *d_status, void *stream);
+
+/* Total tile count of a view set under a tiling (host helper; -1 on bad input). */
+int64_t fgs_num_tiles(const fgs_camera *cams, int32_t n_views, fgs_tiling tiling);
+
+/* ---------------------------------------------------------------------------------
+ * fgs_bin_sort -- tile binning and depth ordering of the splats that eq1 blends
+ * front to back.  Produces, for every global tile, the list of Gaussians whose
+ * rect contains the tile, ordered by (float32 depth bits, Gaussian id).
+ *   tile_keys[k], ids[k] for k < *d_num_pairs: global tile index and Gaussian id,
+ *   sorted by (tile, depth, id).  tile_ranges[2*t], [2*t+1] = [start, end) of tile t
+ *   (0, 0 for an empty tile).
+ * ws/ws_bytes: scratch of at least fgs_bin_sort_workspace_size(n_views*stride,
+ *   pair_capacity) bytes, 256-byte aligned.
+ * Device errors: FGS_DEV_PAIR_OVERFLOW when the pair count exceeds pair_capacity;
+ *   *d_num_pairs then holds the required count and the lists are not valid.
+ * err: INVALID_ARGUMENT for small workspace, pair_capacity outside 1..2^31-1. */
+fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const fgs_camera *cams,
+                        int32_t n_views, fgs_tiling tiling, void *ws, size_t ws_bytes,
+                        uint32_t *tile_keys, int32_t *ids, int64_t pair_capacity,
+                        int32_t *tile_ranges, int64_t *d_num_pairs, int32_t *d_status,
+                        void *stream);
+size_t fgs_bin_sort_workspace_size(int64_t n_records, int64_t pair_capacity);
+
+/* ---------------------------------------------------------------------------------
+ * fgs_render_fwd -- alpha blending of eq1 for the three readings the paper gives
+ * (colour gamma = c, depth gamma = d, opacity gamma = 1), front to back per pixel:
+ *   power = -(a dx^2 + c dy^2)/2 - b dx dy, d = mean2d - pixel; skipped if > 0;
+ *   alpha = min(0.99, opacity e^power), skipped if < 1/255;
+ *   stop before a Gaussian whose T (1 - alpha) < 1e-4;
+ *   C += rgb alpha T, D += z alpha T, A += alpha T, T *= (1 - alpha).
+ * out (per view, concatenated): color [3][H][W], depth [H][W] (unnormalised
+ *   sum z alpha T), alpha [H][W] (sum alpha T), t_final [H][W] (T after the last
+ *   blended Gaussian), n_contrib [H][W] (1 + list position of the last blended
+ *   Gaussian, 0 if none).  The backward reads t_final and n_contrib.
+ * Background is 0. */
+fgs_status fgs_render_fwd(const fgs_projected *proj, const fgs_gaussians *g,
+                          const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
+                          const int32_t *ids, const int32_t *tile_ranges, float *color,
+                          float *depth, float *alpha, float *t_final, int32_t *n_contrib,
+                          int32_t *d_status, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * fgs_render_bwd -- reverse-mode adjoint of fgs_render_fwd and fgs_project: the
+ * gradient of the mapping loss (eq16) with respect to every Gaussian parameter,
+ * given dL/d(colour, depth, alpha) per pixel.  The per-pixel transmittance is
+ * recomputed back to front by division by (1 - alpha) (alpha <= 0.99), nothing is
+ * stored per (pixel, Gaussian).
+ * grad2d: scratch [n_views][stride][8] floats (zeroed by the call).
+ * grads : gradients are ADDED into grads' planes (caller zeroes them); layout as g.
+ * dL_ddepth and dL_dalpha may be NULL (treated as zero). */
+fgs_status fgs_render_bwd(const fgs_gaussians *g, const fgs_projected *proj,
+                          const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
+                          const int32_t *ids, const int32_t *tile_ranges,
+                          const float *t_final, const int32_t *n_contrib,
+                          const float *dL_dcolor, const float *dL_ddepth,
+                          const float *dL_dalpha, float *grad2d, fgs_gaussians *grads,
+                          int32_t *d_status, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * fgs_loss -- the mapping loss of eq16 per view, summed over views:
+ *   w_l1_color * mean|C - C_gt| + w_l1_depth * mean_px([D_gt > 0] |D - D_gt|)
+ *   + w_ssim * (1 - mean SSIM(C, C_gt)),
+ * SSIM with an 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2, zero
+ * padding, averaged over the 3 H W colour samples.  (eq16's (1 - lambda_i) is
+ * w_ssim.)  Writes dL/dC and dL/dD and ADDS the loss value to *d_loss.
+ * ws: fgs_loss_workspace_size(cams, n_views) bytes.  The value is reduced in a
+ * fixed order, so it is bit-reproducible run to run. */
+typedef struct {
+  float w_l1_color, w_l1_depth, w_ssim;
+} fgs_loss_params;
+fgs_status fgs_loss(const fgs_camera *cams, int32_t n_views, const float *color,
+                    const float *depth, const float *color_gt, const float *depth_gt,
+                    const fgs_loss_params *params, float *dL_dcolor, float *dL_ddepth,
+                    float *d_loss, void *ws, size_t ws_bytes, void *stream);
+size_t fgs_loss_workspace_size(const fgs_camera *cams, int32_t n_views);
+
+/* fgs_scale_reg -- scale regulariser eq15 (per-Gaussian mean of the first two
+ * linear scales, epsilon = 0) times `weight`; ADDS its gradient to
+ * grads->log_scales and its value to *d_loss.  ws: fgs_scale_reg_workspace_size. */
+fgs_status fgs_scale_reg(const fgs_gaussians *g, float weight, fgs_gaussians *grads,
+                         float *d_loss, void *ws, size_t ws_bytes, void *stream);
+size_t fgs_scale_reg_workspace_size(int64_t n);
+
+/* fgs_adam -- bias-corrected Adam step on every Gaussian parameter (the map
+ * optimisation of Sec. III-D; the paper does not name the optimiser).
+ * lr per group: means, log_scales, quats, opacity, rgb.  The step number t >= 1 is
+ * params->step, or, when d_step is not NULL, *d_step + 1 read on the device
+ * (the call then increments *d_step, so a captured graph can be replayed). */
+typedef struct {
+  float lr[5];
+  float beta1, beta2, eps;
+  int32_t step;
+} fgs_adam_params;
+fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads, fgs_gaussians *m,
+                    fgs_gaussians *v, const fgs_adam_params *hp, int32_t *d_step,
+                    void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * fgs_fourier_seed -- adaptive densification of Sec. III-A for one frame.
+ *   gray = 0.299 R + 0.587 G + 0.114 B of rgb_gt; F = DFT2(gray) (eq2);
+ *   centred (eq3, read as the standard spectrum shift); high-pass H = 1 -
+ *   exp(-D^2 / (2 D0^2)) with D in Nyquist units (eq5, eq7); inverse DFT (eq8);
+ *   E = |I_h|.  256-bin histogram of E / max E, triangle threshold t;
+ *   M_h = bin > t, M_l = not M_h.  Missing region (eq9):
+ *   M_m = (A < tau_alpha) | (D/A - D_gt > tau_depth_rel D_gt) | (sum|C - C_gt| > 3 tau_color),
+ *   all pixels when r_alpha is NULL.  Seeds (eq10): M_h & M_m on the m-grid and
+ *   M_l & M_m on the n-grid (x % s == 0 && y % s == 0), valid depth only, high
+ *   seeds first then low, row-major, at most max_new.  New Gaussians (eq11):
+ *   back-projected from depth_gt, log-scale log(alpha_{h|l} d / f) on all axes
+ *   (f = (fx + fy)/2), identity rotation, rgb of the frame, logit init_logit;
+ *   when `prior` is not NULL the learned prior replaces scale and logit unless its
+ *   log-scale is further than prior_max_dev from the eq11 value (fgs_prior_infer).
+ * Appends at g->d_n ? *g->d_n : g->n and increments *g->d_n when set.
+ * out: mask (uint8 per pixel: bit0 M_h, bit1 M_l, bit2 M_m, bit3 seeded),
+ *   energy (E, nullable), *d_num_new, *d_threshold (bin t), appended Gaussians.
+ * ws: fgs_fourier_seed_workspace_size(W, H). */
+typedef struct {
+  float d0;          /* high-pass cutoff in Nyquist units (0.25)       */
+  int32_t m, n;      /* sampling spacing in high / low frequency areas */
+  float alpha_h, alpha_l;
+  float tau_alpha, tau_depth_rel, tau_color;
+  int32_t max_new;
+  float init_logit;
+  float prior_max_dev; /* natural-log distance for the learned prior's fallback */
+} fgs_seed_params;
+
+typedef struct {
+  /* BF16 weights (uint16 bit patterns), row-major [out][in], and FP32 biases. */
+  const uint16_t *w1; /* [128][272] (input: 256 log-magnitudes, depth, 15 zeros) */
+  const float *b1;    /* [128]                                                   */
+  const uint16_t *w2; /* [128][128] */
+  const float *b2;    /* [128]      */
+  const uint16_t *w3; /* [8][128]  rows 4..7 zero */
+  const float *b3;    /* [8]        rows 4..7 zero */
+} fgs_mlp;
+
+fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_gt, const float *r_color,
+                            const float *r_depth, const float *r_alpha,
+                            const fgs_camera *cam, const fgs_seed_params *params,
+                            const fgs_mlp *prior, uint8_t *mask, float *energy,
+                            fgs_gaussians *g, int32_t *d_num_new, int32_t *d_threshold,
+                            void *ws, size_t ws_bytes, int32_t *d_status, void *stream);
+size_t fgs_fourier_seed_workspace_size(int32_t width, int32_t height);
+
+/* ---------------------------------------------------------------------------------
+ * Learned seeding prior (not in the paper; an extension).  Features per seed
+ * pixel (x, y): the 16x16 grayscale patch with top-left (x-8, y-8), clamped to the
+ * image, its 2D DFT magnitude as log(1 + |F|) in natural frequency order (256),
+ * then the depth, then 15 zeros -> BF16 row of 272.  MLP 272 -> 128 -> 128 -> 4,
+ * GELU (erf form), BF16 operands, FP32 accumulation, activations rounded to BF16
+ * before each product.  Output: log-scale x, y, z and opacity logit.
+ *
+ * fgs_prior_features: gray [H][W] (or NULL and rgb [3][H][W]), depth [H][W],
+ *   seed_xy [n][2] int32 -> features [n][272] BF16.
+ * fgs_prior_infer: features -> out [n][4] float. */
+#define FGS_PRIOR_IN 272
+#define FGS_PRIOR_HID 128
+#define FGS_PRIOR_OUT 4
+fgs_status fgs_prior_features(const float *rgb, const float *depth, int32_t width,
+                              int32_t height, const int32_t *seed_xy, int64_t n,
+                              uint16_t *features, void *stream);
+fgs_status fgs_prior_infer(const fgs_mlp *mlp, const uint16_t *features, int64_t n,
+                           float *out, void *stream);
+
+/* fgs_prior_train -- one Adam step of the prior on a batch: mean squared error
+ * over the batch's n x 4 outputs against `targets`, gradients through the MLP,
+ * Adam on the FP32 master weights, BF16 copies refreshed.  *d_loss receives the
+ * batch loss (before the step). */
+typedef struct {
+  float *w1, *b1, *w2, *b2, *w3, *b3; /* FP32 masters, same shapes as fgs_mlp */
+  float *m;                           /* Adam first moments, all params packed */
+  float *v;                           /* Adam second moments                    */
+} fgs_mlp_master;
+typedef struct {
+  float lr, beta1, beta2, eps;
+  int32_t step; /* t >= 1 */
+} fgs_train_params;
+fgs_status fgs_prior_train(fgs_mlp *mlp_bf16_out, fgs_mlp_master *master,
+                           const uint16_t *features, const float *targets, int64_t n,
+                           const fgs_train_params *hp, float *d_loss, void *ws,
+                           size_t ws_bytes, void *stream);
+size_t fgs_prior_train_workspace_size(int64_t n);
+int64_t fgs_prior_num_params(void);
+
+/* ---------------------------------------------------------------------------------
+ * Auxiliary. */
+const char *fgs_last_error(void);
+int32_t fgs_version(void);
+/* Kernel launches issued by this library in this process (host counter). */
+int64_t fgs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FGS_H */
