@@ -1,0 +1,339 @@
+"""Benchmark of the mapping hot path at 1200x680 with a 1M-Gaussian map.
+
+Workload (synthetic stand-in for a Replica-sized RGB-D sequence): a room-shaped
+1M-Gaussian map, a ground-truth room scene whose renders are the frames, and a
+seeded smooth 1200x680 (f = 600) camera trajectory.  One step is one frame:
+
+  1. render the map at the frame's pose (project, bin + sort, blend);
+  2. Fourier seeding of the frame (DFT, high-pass, triangle threshold, missing
+     region, equidistant samples, back-projection; learned prior when trained),
+     appending up to 50k Gaussians;
+  3. ITERS_PER_FRAME mapping iterations (project, bin + sort, blend, loss with
+     SSIM and the scale regulariser, adjoint, Adam).
+
+The metric is mapping iterations per second (ITERS_PER_FRAME per step).  Inputs
+(the map, all frames' colour and depth) are resident in HBM before timing; the
+working set is far larger than the 129 MB L2.  ``e2e`` repeats the measurement
+with each frame copied from pinned host memory and the loss read back every step.
+
+``--impl reference`` times the FP64 CPU oracle of the same iteration instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+W, H, F = 1200, 680, 600.0
+N_MAP = 1_000_000
+N_GT = 1_000_000
+ITERS_PER_FRAME = 3
+METRIC = "fwd+bwd mapping iters/s @1200x680, 1M Gaussians"
+WORKLOAD = "room map 1M Gaussians, 1200x680 f=600, seeded trajectory; per frame: render + Fourier seeding (<=50k) + 3 mapping iterations"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--tile", default="16x16")
+    p.add_argument("--batch", type=int, default=128)
+    p.add_argument("--mapping-only", action="store_true", help="steps of mapping iterations without seeding")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------------------------
+
+def build_workload(seed_offset: int, n_frames: int, tile, batch, device):
+    import torch
+
+    from paper_2503_01109_gb300 import fgs, synthetic as syn
+    from paper_2503_01109_gb300.frames import FramePipeline
+
+    cams = syn.trajectory(n_frames, seed=100 + seed_offset, width=W, height=H, f=F)
+    scene = syn.room_scene(N_MAP, seed=seed_offset, kind="map")
+    gt = syn.room_scene(N_GT, seed=1000 + seed_offset, kind="gt")
+    pipe = FramePipeline(scene, cams, gt, capacity=N_MAP + (n_frames + 1) * 50_000, tile=tile, batch=batch,
+                         iters_per_frame=ITERS_PER_FRAME, device=device)
+    return pipe
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+    from paper_2503_01109_gb300 import fgs
+
+    tw, th = (int(x) for x in args.tile.split("x"))
+    n_frames = args.warmup + args.steps
+    pipe = build_workload(rank, n_frames, (tw, th), args.batch, device)
+    step = pipe.mapping_step if args.mapping_only else pipe.frame_step
+    iters_per_step = 1 if args.mapping_only else ITERS_PER_FRAME
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up frames
+    for k in range(args.warmup):
+        step(k)
+    barrier()
+    pipe.check()
+    stream = torch.cuda.current_stream()
+    # per-kernel timing of the dominant kernels (events around each launch on this stream)
+    pipe.kernel_timer.enable()
+    with ClockSampler(local) as clk:
+        barrier()
+        l0 = fgs.launch_count()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(args.warmup, args.warmup + args.steps):
+            step(k)
+        t1.record(stream)
+        barrier()
+        launches = fgs.launch_count() - l0
+        ms = t0.elapsed_time(t1)
+    pipe.kernel_timer.disable()
+    pipe.check()
+    clocks = clk.summary()
+    ms_t = torch.tensor([ms], device=device)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    total_iters = iters_per_step * args.steps * world
+    value = total_iters / (ms_max / 1e3)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = pipe.e2e_measure(args.warmup, args.steps, step)
+        e2e_t = torch.tensor([e2e["ms"]], device=device)
+        if world > 1:
+            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        e2e = {"value": total_iters / (float(e2e_t.item()) / 1e3), "unit": "iters/s",
+               "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
+
+    peaks = load_peaks()
+    roof = pipe.roofline(peaks)
+    out = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if not args.mapping_only else WORKLOAD + " (mapping iterations only)",
+                   "width": W, "height": H, "gaussians": N_MAP, "gt_gaussians": N_GT,
+                   "iters_per_step": iters_per_step, "tile": args.tile, "batch_depth": args.batch,
+                   "l2": "inputs larger than L2 (map + optimiser state + pair lists >> 129 MB)",
+                   "final_gaussians": pipe.live_count(), "pairs_last": pipe.last_pairs(),
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
+        "kernels_ms_per_step": pipe.kernel_timer.summary(args.steps),
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(pipe)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def oracle_iteration(scene_np: dict, cam: dict, color_gt: np.ndarray, depth_gt: np.ndarray, rows: int, y0: int):
+    """One FP64 oracle mapping iteration (project, bin, blend, eq16 loss, adjoint,
+    eq15, Adam) on a horizontal band of `rows` image rows starting at y0.  Returns
+    the estimated seconds of a full-frame iteration: the per-Gaussian stages as
+    timed plus the per-pixel stages scaled by H / rows."""
+    from oracle import render as orr
+    band = dict(cam)
+    band["height"], band["cy"] = rows, cam["cy"] - y0
+    cg = np.ascontiguousarray(color_gt[:, y0:y0 + rows], np.float64)
+    dg = np.ascontiguousarray(depth_gt[y0:y0 + rows], np.float64)
+    t0 = time.perf_counter()
+    sa = orr.aos(scene_np)
+    pr = orr.project(sa, band)
+    t1 = time.perf_counter()
+    _, ids, ranges = orr.bin_sort([band], 16, 16, pr["depth"][None].astype(np.float32), pr["radius"][None],
+                                  pr["rect"][None])
+    out = orr.render_fwd(pr, sa["rgb"], band, ids, ranges)
+    _, dC, dD = orr.loss(out["color"], out["depth"], cg, dg, 0.9, 0.1, 0.1)
+    g2, grgb = orr.render_bwd(pr, sa["rgb"], band, ids, ranges, dC, dD)
+    t2 = time.perf_counter()
+    grads = orr.project_bwd(sa, band, g2)
+    grads["rgb"] = grgb
+    _, greg = orr.scale_reg(sa["log_scales"], 0.01)
+    grads["log_scales"] += greg
+    lrs = {"means": 1e-3, "log_scales": 5e-3, "quats": 1e-3, "logits": 5e-2, "rgb": 2.5e-3}
+    for k, lr in lrs.items():
+        p = sa[k].reshape(-1)
+        orr.adam(p, np.ascontiguousarray(grads[k].reshape(-1)), np.zeros_like(p), np.zeros_like(p), lr, t=1)
+    t3 = time.perf_counter()
+    per_gauss = (t1 - t0) + (t3 - t2)
+    per_pix = t2 - t1
+    return per_gauss + per_pix * (cam["height"] / rows), (t3 - t0)
+
+
+def band_rows(budget_s: float) -> int:
+    return 32 if budget_s >= 15 else 16
+
+
+def cpu_baseline(pipe, budget_s: float = 20.0):
+    """The FP64 oracle's mapping iteration on a bounded sample of the workload:
+    the map as the GPU left it, the last frame, a band of tile rows."""
+    from oracle import render as orr
+    k = (len(pipe.cams) - 1)
+    cam = pipe.cams[k]
+    scene = pipe.g.to_scene(pipe.live_count())
+    color = pipe.colors[k].view(3, H, W).cpu().numpy()
+    depth = pipe.depths[k].view(H, W).cpu().numpy()
+    rows = band_rows(budget_s)
+    y0 = (H // 2 // 16) * 16
+    est, wall = oracle_iteration(scene, cam, color, depth, rows, y0)
+    return {"value": 1.0 / est, "unit": "iters/s", "cores": orr.num_threads(), "kind": "oracle",
+            "sample": f"one mapping iteration on rows {y0}-{y0 + rows} of 680 ({pipe.live_count()} Gaussians); "
+                      f"{wall:.1f} s wall, per-pixel stages scaled by {H / rows:.1f}"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import render as orr
+    from paper_2503_01109_gb300 import synthetic as syn
+
+    n_frames = args.warmup + args.steps
+    per_step_budget = max(4.0, 150.0 / max(n_frames, 1))
+    rows = 16 if per_step_budget < 15 else 32
+    cams = syn.trajectory(n_frames, seed=100, width=W, height=H, f=F)
+    scene = syn.room_scene(N_MAP, seed=0, kind="map")
+    gt = syn.room_scene(N_GT, seed=1000, kind="gt")
+    y0 = (H // 2 // 16) * 16
+    est = []
+    for k in range(n_frames):
+        band = dict(cams[k])
+        band["height"], band["cy"] = rows, cams[k]["cy"] - y0
+        ref = orr.render_views(gt, [band])["out"][0]          # target band (untimed set-up)
+        color = np.zeros((3, H, W)); depth = np.zeros((H, W))
+        color[:, y0:y0 + rows] = ref["color"]
+        depth[y0:y0 + rows] = np.where(ref["alpha"] > 0.5, ref["depth"] / np.maximum(ref["alpha"], 1e-6), 0.0)
+        e, _ = oracle_iteration(scene, cams[k], color, depth, rows, y0)
+        if k >= args.warmup:
+            est.append(e)
+    ms = 1e3 * float(np.mean(est))
+    value = 1e3 / ms
+    desc = (f"FP64 C oracle, one mapping iteration per step on rows {y0}-{y0 + rows} of 680 with the full 1M map; "
+            f"per-pixel stages scaled by {H / rows:.1f}")
+    out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "width": W, "height": H, "gaussians": N_MAP},
+           "cpu_baseline": {"value": value, "unit": "iters/s", "cores": orr.num_threads(), "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

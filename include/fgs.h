@@ -179,6 +179,23 @@ fgs_status fgs_render_bwd(const fgs_gaussians *g, const fgs_projected *proj,
                           const float *dL_dalpha, float *grad2d, fgs_gaussians *grads,
                           int32_t *d_status, void *stream);
 
+/* The two halves of fgs_render_bwd as separate calls (one kernel each):
+ * fgs_render_bwd_splats ADDS the per-splat gradients (mean2d, conic, opacity,
+ *   depth) into grad2d [n_views][stride][8] and the colour gradients into
+ *   grads->rgb; the caller zeroes both first.
+ * fgs_project_bwd ADDS the chain rule of fgs_project from grad2d into grads'
+ *   means, log_scales, quats and opacity_logits. */
+fgs_status fgs_render_bwd_splats(const fgs_gaussians *g, const fgs_projected *proj,
+                                 const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
+                                 const int32_t *ids, const int32_t *tile_ranges,
+                                 const float *t_final, const int32_t *n_contrib,
+                                 const float *dL_dcolor, const float *dL_ddepth,
+                                 const float *dL_dalpha, float *grad2d, fgs_gaussians *grads,
+                                 int32_t *d_status, void *stream);
+fgs_status fgs_project_bwd(const fgs_gaussians *g, const fgs_projected *proj,
+                           const fgs_camera *cams, int32_t n_views, const float *grad2d,
+                           fgs_gaussians *grads, void *stream);
+
 /* ---------------------------------------------------------------------------------
  * fgs_loss -- the mapping loss of eq16 per view, summed over views:
  *   w_l1_color * mean|C - C_gt| + w_l1_depth * mean_px([D_gt > 0] |D - D_gt|)
@@ -311,6 +328,9 @@ const char *fgs_last_error(void);
 int32_t fgs_version(void);
 /* Kernel launches issued by this library in this process (host counter). */
 int64_t fgs_launch_count(void);
+/* cudaMemsetAsync of `bytes` bytes at device pointer dst on the stream (used to
+ * clear gradient planes and loss accumulators between mapping iterations). */
+fgs_status fgs_memset_async(void *dst, int32_t value, size_t bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,454 @@
+// binsort.cu -- tile binning and depth ordering of the splats eq1 blends front to back.
+//
+// The required order of every tile's list is (float32 depth bits, Gaussian id).
+// Instead of radix-sorting 64-bit (tile | depth) keys of every (tile, Gaussian)
+// pair, the records are sorted by depth ONCE (n_views * n keys, stable, so equal
+// depths stay in id order), pairs are emitted in that order, and a stable sort on
+// the tile index alone (a few bits, one or two 8-bit passes) finishes the job:
+// within a tile the pairs keep their emission order, which is depth then id.
+//
+// The radix sort is LSD, 8-bit digits, reduce-then-scan: an upsweep histogram per
+// block chunk, one exclusive scan of the digit-major counts, and a downsweep that
+// ranks 2048-item tiles stably with warp match-any, reorders them in shared memory
+// and writes each digit run coalesced.  Item counts may live on the device (the
+// pair count), so the whole binning can be captured in a CUDA graph.
+#include "common.cuh"
+
+namespace fgs {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
+constexpr int kSortMaxBlocks = 1024;
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ uint32_t item_count(const int64_t *d_count, int64_t host_count, int64_t cap) {
+  int64_t c = d_count ? *d_count : host_count;
+  if (c > cap) c = cap;
+  if (c < 0) c = 0;
+  return (uint32_t)c;
+}
+
+__device__ __forceinline__ void block_chunk(uint32_t count, uint32_t nb, uint32_t b, uint32_t &lo,
+                                            uint32_t &hi) {
+  uint32_t tiles = (count + kSortTile - 1) / kSortTile;
+  uint32_t per = (tiles + nb - 1) / nb;
+  uint64_t l = (uint64_t)b * per * kSortTile, h = l + (uint64_t)per * kSortTile;
+  lo = (uint32_t)(l < count ? l : count);
+  hi = (uint32_t)(h < count ? h : count);
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
+                                                                const int64_t *d_count, int64_t host_count,
+                                                                int64_t cap, int shift,
+                                                                uint32_t *__restrict__ counts) {
+  __shared__ uint32_t hist[kSortThreads / 32][256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int d = lane; d < 256; d += 32) hist[warp][d] = 0;
+  __syncthreads();
+  const uint32_t count = item_count(d_count, host_count, cap);
+  uint32_t lo, hi;
+  block_chunk(count, gridDim.x, blockIdx.x, lo, hi);
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += kSortThreads)
+    atomicAdd(&hist[warp][(keys[i] >> shift) & 255u], 1u);
+  __syncthreads();
+  if (threadIdx.x < 256) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) s += hist[w][threadIdx.x];
+    counts[threadIdx.x * gridDim.x + blockIdx.x] = s;  // digit-major
+  }
+}
+
+// Exclusive scan of n (<= 1024 * per-thread segment) uint32 values by one block.
+__global__ void __launch_bounds__(kScanThreads) k_scan_small(uint32_t *__restrict__ data, int n) {
+  __shared__ uint32_t part[kScanThreads];
+  const int per = (n + kScanThreads - 1) / kScanThreads;
+  const int lo = threadIdx.x * per, hi = min(n, lo + per);
+  uint32_t s = 0;
+  for (int i = lo; i < hi; ++i) s += data[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < kScanThreads; off <<= 1) {
+    uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - s;
+  for (int i = lo; i < hi; ++i) {
+    uint32_t v = data[i];
+    data[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
+    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+    uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const int64_t *d_count,
+    int64_t host_count, int64_t cap, int shift, const uint32_t *__restrict__ offsets) {
+  constexpr int W = kSortThreads / 32;
+  __shared__ uint32_t s_whist[W][256];
+  __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_prefix[256];
+  __shared__ uint32_t s_total[256];
+  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint32_t count = item_count(d_count, host_count, cap);
+  uint32_t lo, hi;
+  block_chunk(count, gridDim.x, blockIdx.x, lo, hi);
+  if (threadIdx.x < 256) s_base[threadIdx.x] = offsets[threadIdx.x * gridDim.x + blockIdx.x];
+  __syncthreads();
+  for (uint32_t tile = lo; tile < hi; tile += kSortTile) {
+    for (int d = lane; d < 256; d += 32) s_whist[warp][d] = 0;
+    __syncwarp();
+    uint32_t k[kSortItems], v[kSortItems], local[kSortItems];
+    int dig[kSortItems];
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const uint32_t idx = tile + warp * (32 * kSortItems) + it * 32 + lane;
+      const bool valid = idx < hi;
+      k[it] = valid ? keys_in[idx] : 0u;
+      v[it] = valid ? vals_in[idx] : 0u;
+      dig[it] = valid ? (int)((k[it] >> shift) & 255u) : 256;
+      const uint32_t peers = __match_any_sync(0xffffffffu, dig[it]);
+      uint32_t base = 0;
+      if (valid) base = s_whist[warp][dig[it]];
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) s_whist[warp][dig[it]] = base + __popc(peers);
+      __syncwarp();
+      local[it] = base + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        uint32_t c = s_whist[w][threadIdx.x];
+        s_whist[w][threadIdx.x] = run;
+        run += c;
+      }
+      s_total[threadIdx.x] = run;
+      s_prefix[threadIdx.x] = run;
+    }
+    __syncthreads();
+    // exclusive scan of the 256 digit totals (Hillis-Steele on 256 threads)
+    for (int off = 1; off < 256; off <<= 1) {
+      uint32_t add = 0;
+      if (threadIdx.x < 256 && threadIdx.x >= off) add = s_prefix[threadIdx.x - off];
+      __syncthreads();
+      if (threadIdx.x < 256) s_prefix[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (threadIdx.x < 256) s_prefix[threadIdx.x] -= s_total[threadIdx.x];
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      if (dig[it] < 256) {
+        const uint32_t pos = s_prefix[dig[it]] + s_whist[warp][dig[it]] + local[it];
+        s_keys[pos] = k[it];
+        s_vals[pos] = v[it];
+      }
+    }
+    __syncthreads();
+    const uint32_t n_tile = min((uint32_t)kSortTile, hi - tile);
+    for (uint32_t i = threadIdx.x; i < n_tile; i += kSortThreads) {
+      const uint32_t key = s_keys[i];
+      const uint32_t d = (key >> shift) & 255u;
+      const uint32_t out = s_base[d] + (i - s_prefix[d]);
+      keys_out[out] = key;
+      vals_out[out] = s_vals[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) s_base[threadIdx.x] += s_total[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// Stable LSD sort of (key, value) over bits [0, bits).  Result lands in (k0, v0)
+// when the number of passes is even, in (k1, v1) otherwise.
+static fgs_status radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int64_t *d_count,
+                             int64_t host_count, int64_t cap, int bits, int nblocks, uint32_t *counts,
+                             cudaStream_t st) {
+  const int passes = (bits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    uint32_t *ki = (p & 1) ? k1 : k0, *vi = (p & 1) ? v1 : v0;
+    uint32_t *ko = (p & 1) ? k0 : k1, *vo = (p & 1) ? v0 : v1;
+    k_radix_upsweep<<<nblocks, kSortThreads, 0, st>>>(ki, d_count, host_count, cap, shift, counts);
+    k_scan_small<<<1, kScanThreads, 0, st>>>(counts, 256 * nblocks);
+    k_radix_downsweep<<<nblocks, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_count, host_count, cap, shift,
+                                                        counts);
+    count_launch(3);
+  }
+  FGS_CHECK_LAUNCH("radix_sort");
+  return FGS_OK;
+}
+
+static int sort_blocks(int64_t cap) {
+  int64_t tiles = (cap + kSortTile - 1) / kSortTile;
+  int64_t nb = std::min<int64_t>(std::min<int64_t>(tiles, kSortMaxBlocks), 4 * (int64_t)num_sms());
+  return (int)std::max<int64_t>(nb, 1);
+}
+
+// ---------------------------------------------------------------------------------
+// record keys for the depth sort: float32 depth bits of a record with tiles, else
+// 0xFFFFFFFF (sorted last; such records emit nothing)
+
+__global__ void k_depth_keys(const float4 *__restrict__ splat, const int32_t *__restrict__ radius,
+                             const uint2 *__restrict__ rect, int64_t n, int64_t stride, int n_views,
+                             uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= (int64_t)n_views * n) return;
+  const int64_t v = j / n, i = j - v * n;
+  const int64_t r = v * stride + i;
+  uint32_t key = 0xFFFFFFFFu;
+  if (radius[r] > 0) {
+    const uint2 rc = rect[r];
+    if ((rc.x & 0xFFFFu) <= (rc.y & 0xFFFFu) && (rc.x >> 16) <= (rc.y >> 16))
+      key = __float_as_uint(splat[2 * r + 1].z);
+  }
+  keys[j] = key;
+  vals[j] = (uint32_t)r;
+}
+
+__device__ __forceinline__ uint32_t rect_tiles(uint2 rc) {
+  const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu, y1 = rc.y >> 16;
+  if (x0 > x1 || y0 > y1) return 0u;
+  return (x1 - x0 + 1u) * (y1 - y0 + 1u);
+}
+
+// Tiles per sorted record, then per-block sums for the scan.
+constexpr int kScanBlock = 1024;
+
+__global__ void __launch_bounds__(kScanBlock) k_counts_blocksum(const uint32_t *__restrict__ skeys,
+                                                                const uint32_t *__restrict__ svals,
+                                                                const uint2 *__restrict__ rect, int64_t R,
+                                                                uint32_t *__restrict__ cnt,
+                                                                uint32_t *__restrict__ bsum) {
+  __shared__ uint32_t red[kScanBlock / 32];
+  const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+  uint32_t c = 0;
+  if (j < R && skeys[j] != 0xFFFFFFFFu) c = rect_tiles(rect[svals[j]]);
+  if (j < R) cnt[j] = c;
+  uint32_t s = c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t t = red[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the block sums with 64-bit total; the total is the pair count.
+__global__ void __launch_bounds__(kScanThreads) k_scan_bsum(uint32_t *__restrict__ bsum, int nb,
+                                                            int64_t *__restrict__ d_num_pairs,
+                                                            int64_t pair_cap, int32_t *__restrict__ d_status,
+                                                            int64_t *__restrict__ d_sort_count) {
+  __shared__ unsigned long long part[kScanThreads];
+  const int per = (nb + kScanThreads - 1) / kScanThreads;
+  const int lo = threadIdx.x * per, hi = min(nb, lo + per);
+  unsigned long long s = 0;
+  for (int i = lo; i < hi; ++i) s += bsum[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < kScanThreads; off <<= 1) {
+    unsigned long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned long long run = part[threadIdx.x] - s;
+  for (int i = lo; i < hi; ++i) {
+    uint32_t v = bsum[i];
+    bsum[i] = (uint32_t)(run > 0xFFFFFFFFull ? 0xFFFFFFFFull : run);
+    run += v;
+  }
+  if (threadIdx.x == kScanThreads - 1) {
+    const unsigned long long total = part[kScanThreads - 1];
+    *d_num_pairs = (int64_t)total;
+    const bool over = total > (unsigned long long)pair_cap;
+    if (over && d_status) atomicOr(d_status, FGS_DEV_PAIR_OVERFLOW);
+    *d_sort_count = over ? 0 : (int64_t)total;
+  }
+}
+
+// Emits the (tile, id) pairs of every sorted record at its scanned offset.  A
+// warp cooperates on one record at a time so that large footprints do not
+// serialise a single thread.
+__global__ void __launch_bounds__(kScanBlock) k_emit(const uint32_t *__restrict__ skeys,
+                                                     const uint32_t *__restrict__ svals,
+                                                     const uint2 *__restrict__ rect,
+                                                     const uint32_t *__restrict__ cnt,
+                                                     const uint32_t *__restrict__ bsum, int64_t R,
+                                                     int64_t stride, DevViews vs, const int64_t *d_sort_count,
+                                                     uint32_t *__restrict__ tile_keys, uint32_t *__restrict__ ids) {
+  __shared__ uint32_t warp_sum[kScanBlock / 32];
+  const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t c = j < R ? cnt[j] : 0u;
+  // block-local exclusive scan of c
+  uint32_t incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_sum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kScanBlock / 32 ? warp_sum[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < kScanBlock / 32) warp_sum[lane] = wi - w;
+  }
+  __syncthreads();
+  const uint32_t off = bsum[blockIdx.x] + warp_sum[warp] + (incl - c);
+  const int64_t sort_count = *d_sort_count;  // 0 on overflow: emit nothing
+  // warp-cooperative emission: each lane's record in turn
+  uint32_t pending = __ballot_sync(0xffffffffu, c > 0 && sort_count > 0);
+  while (pending) {
+    const int src = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const uint32_t rc_off = __shfl_sync(0xffffffffu, off, src);
+    const uint32_t rc_cnt = __shfl_sync(0xffffffffu, c, src);
+    const uint32_t rec = __shfl_sync(0xffffffffu, j < R ? svals[j] : 0u, src);
+    const uint2 rc = rect[rec];
+    const uint32_t v = (uint32_t)(rec / stride), id = (uint32_t)(rec - (uint64_t)v * stride);
+    const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu;
+    const uint32_t w = x1 - x0 + 1u;
+    const uint32_t tb = (uint32_t)vs.cam[v].tile_base, tx = (uint32_t)vs.cam[v].tiles_x;
+    for (uint32_t q = lane; q < rc_cnt; q += 32) {
+      const uint32_t dy = q / w, dx = q - dy * w;
+      tile_keys[rc_off + q] = tb + (y0 + dy) * tx + (x0 + dx);
+      ids[rc_off + q] = id;
+    }
+  }
+}
+
+__global__ void k_tile_ranges(const uint32_t *__restrict__ tile_keys, const int64_t *d_sort_count,
+                              int64_t cap, int2 *__restrict__ ranges) {
+  const int64_t P = *d_sort_count;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P && k < cap;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t t = tile_keys[k];
+    if (k == 0 || tile_keys[k - 1] != t) ranges[t].x = (int)k;
+    if (k == P - 1 || tile_keys[k + 1] != t) ranges[t].y = (int)(k + 1);
+  }
+}
+
+struct BinWs {
+  uint32_t *dk0, *dv0, *dk1, *dv1;  // depth sort ping-pong, R each
+  uint32_t *cnt;                    // R
+  uint32_t *bsum;                   // ceil(R / 1024)
+  uint32_t *tk1, *tv1;              // tile sort ping-pong, pair_capacity each
+  uint32_t *counts;                 // 256 * kSortMaxBlocks
+  int64_t *sort_count;              // 1
+  size_t bytes;
+};
+
+static BinWs carve(void *base, int64_t R, int64_t cap) {
+  BinWs w;
+  char *p = static_cast<char *>(base);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char *q = p ? p + off : nullptr;
+    off += align_up(bytes);
+    return q;
+  };
+  const size_t r4 = (size_t)std::max<int64_t>(R, 1) * 4, c4 = (size_t)std::max<int64_t>(cap, 1) * 4;
+  w.dk0 = (uint32_t *)take(r4);
+  w.dv0 = (uint32_t *)take(r4);
+  w.dk1 = (uint32_t *)take(r4);
+  w.dv1 = (uint32_t *)take(r4);
+  w.cnt = (uint32_t *)take(r4);
+  w.bsum = (uint32_t *)take((size_t)((R + kScanBlock - 1) / kScanBlock + 1) * 4);
+  w.tk1 = (uint32_t *)take(c4);
+  w.tv1 = (uint32_t *)take(c4);
+  w.counts = (uint32_t *)take((size_t)256 * kSortMaxBlocks * 4);
+  w.sort_count = (int64_t *)take(8);
+  w.bytes = off;
+  return w;
+}
+
+static int bits_for(int64_t v) {
+  int b = 0;
+  while ((int64_t(1) << b) < v) ++b;
+  return b;
+}
+
+}  // namespace fgs
+
+using namespace fgs;
+
+extern "C" size_t fgs_bin_sort_workspace_size(int64_t n_records, int64_t pair_capacity) {
+  if (n_records < 0 || pair_capacity < 0) return 0;
+  return carve(nullptr, n_records, pair_capacity).bytes;
+}
+
+extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const fgs_camera *cams,
+                                   int32_t n_views, fgs_tiling tiling, void *ws, size_t ws_bytes,
+                                   uint32_t *tile_keys, int32_t *ids, int64_t pair_capacity,
+                                   int32_t *tile_ranges, int64_t *d_num_pairs, int32_t *d_status,
+                                   void *stream) {
+  FGS_CHECK_ARG(proj && proj->splat && proj->radius && proj->rect, "fgs_bin_sort: NULL projection");
+  FGS_CHECK_ARG(tiling_ok(tiling), "fgs_bin_sort: unsupported tiling");
+  FGS_CHECK_ARG(n >= 0 && proj->stride >= n, "fgs_bin_sort: need 0 <= n <= stride");
+  FGS_CHECK_ARG(pair_capacity >= 1 && pair_capacity <= 0x7FFFFFFFll, "fgs_bin_sort: pair_capacity");
+  FGS_CHECK_ARG(tile_keys && ids && tile_ranges && d_num_pairs, "fgs_bin_sort: NULL output");
+  DevViews vs;
+  if (!make_views(cams, n_views, tiling.tile_w, tiling.tile_h, &vs)) return FGS_ERR_INVALID_ARGUMENT;
+  FGS_CHECK_ARG((int64_t)n_views * proj->stride < 0xFFFFFFFFll, "fgs_bin_sort: too many records");
+  const int64_t R = (int64_t)n_views * n;
+  BinWs w = carve(ws, R, pair_capacity);
+  FGS_CHECK_ARG(ws != nullptr && ws_bytes >= w.bytes, "fgs_bin_sort: workspace %zu < %zu bytes", ws_bytes,
+                w.bytes);
+  FGS_CHECK_ARG((reinterpret_cast<uintptr_t>(ws) & 255) == 0, "fgs_bin_sort: workspace not 256-byte aligned");
+  cudaStream_t st = as_stream(stream);
+  FGS_CUDA(cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)vs.total_tiles, st), "memset ranges");
+  if (R == 0) {
+    FGS_CUDA(cudaMemsetAsync(d_num_pairs, 0, 8, st), "memset pairs");
+    return FGS_OK;
+  }
+  const float4 *splat = reinterpret_cast<const float4 *>(proj->splat);
+  const uint2 *rect = reinterpret_cast<const uint2 *>(proj->rect);
+  {
+    const int th = 256;
+    k_depth_keys<<<(unsigned)((R + th - 1) / th), th, 0, st>>>(splat, proj->radius, rect, n, proj->stride,
+                                                              n_views, w.dk0, w.dv0);
+    count_launch();
+  }
+  // depth sort: 4 passes, result back in (dk0, dv0)
+  fgs_status s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, nullptr, R, R, 32, sort_blocks(R), w.counts, st);
+  if (s != FGS_OK) return s;
+  const int64_t nb = (R + kScanBlock - 1) / kScanBlock;
+  k_counts_blocksum<<<(unsigned)nb, kScanBlock, 0, st>>>(w.dk0, w.dv0, rect, R, w.cnt, w.bsum);
+  k_scan_bsum<<<1, kScanThreads, 0, st>>>(w.bsum, (int)nb, d_num_pairs, pair_capacity, d_status, w.sort_count);
+  // emit into the buffer the tile sort ends in the caller's arrays
+  const int tbits = std::max(1, bits_for(vs.total_tiles));
+  const int passes = (tbits + 7) / 8;
+  uint32_t *ek = (passes & 1) ? w.tk1 : tile_keys;
+  uint32_t *ev = (passes & 1) ? w.tv1 : reinterpret_cast<uint32_t *>(ids);
+  k_emit<<<(unsigned)nb, kScanBlock, 0, st>>>(w.dk0, w.dv0, rect, w.cnt, w.bsum, R, proj->stride, vs,
+                                              w.sort_count, ek, ev);
+  count_launch(3);
+  FGS_CHECK_LAUNCH("fgs_bin_sort emit");
+  s = radix_sort(ek, ev, (passes & 1) ? tile_keys : w.tk1, (passes & 1) ? reinterpret_cast<uint32_t *>(ids) : w.tv1,
+                 w.sort_count, 0, pair_capacity, tbits, sort_blocks(pair_capacity), w.counts, st);
+  if (s != FGS_OK) return s;
+  k_tile_ranges<<<4 * num_sms(), 256, 0, st>>>(tile_keys, w.sort_count, pair_capacity,
+                                               reinterpret_cast<int2 *>(tile_ranges));
+  count_launch();
+  FGS_CHECK_LAUNCH("fgs_bin_sort ranges");
+  return FGS_OK;
+}

@@ -1,0 +1,315 @@
+// project.cu -- EWA projection of the Gaussians (Sec. III: C = R S S^T R^T and its
+// 2D projection) and its adjoint.
+//
+// One thread per Gaussian handles every view: the parameters are read once with
+// coalesced structure-of-arrays loads and each view's 32-byte splat record is
+// written with two float4 stores (consecutive threads, consecutive records).
+#include "common.cuh"
+
+namespace fgs {
+
+struct GaussLocal {
+  float mu[3], s[3], qn[4], qinv, R[9], Sigma[6], o;  // Sigma: xx, xy, xz, yy, yz, zz
+};
+
+__device__ __forceinline__ void load_gaussian(const GaussPtrs &g, int64_t i, GaussLocal &L) {
+  const int64_t c = g.cap;
+  L.mu[0] = g.means[i];
+  L.mu[1] = g.means[c + i];
+  L.mu[2] = g.means[2 * c + i];
+  float q0 = g.quats[i], q1 = g.quats[c + i], q2 = g.quats[2 * c + i], q3 = g.quats[3 * c + i];
+  float len = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+  L.qinv = 1.0f / len;
+  float w = q0 * L.qinv, x = q1 * L.qinv, y = q2 * L.qinv, z = q3 * L.qinv;
+  L.qn[0] = w; L.qn[1] = x; L.qn[2] = y; L.qn[3] = z;
+  L.R[0] = 1.f - 2.f * (y * y + z * z); L.R[1] = 2.f * (x * y - w * z); L.R[2] = 2.f * (x * z + w * y);
+  L.R[3] = 2.f * (x * y + w * z); L.R[4] = 1.f - 2.f * (x * x + z * z); L.R[5] = 2.f * (y * z - w * x);
+  L.R[6] = 2.f * (x * z - w * y); L.R[7] = 2.f * (y * z + w * x); L.R[8] = 1.f - 2.f * (x * x + y * y);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) L.s[k] = expf(g.log_scales[k * c + i]);
+  float M[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) M[3 * r + k] = L.R[3 * r + k] * L.s[k];
+  L.Sigma[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+  L.Sigma[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+  L.Sigma[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+  L.Sigma[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+  L.Sigma[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+  L.Sigma[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+  L.o = 1.0f / (1.0f + expf(-g.logits[i]));
+}
+
+struct ViewLocal {
+  float p[3];
+  float uc, vc;
+  bool clamp_u, clamp_v;
+  float T[6];  // J R_cam, 2x3
+  float a, b, c, det;
+};
+
+// Returns false when culled (behind the near plane or degenerate covariance).
+__device__ __forceinline__ bool project_view(const GaussLocal &L, const DevCam &cm, ViewLocal &V) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    V.p[r] = cm.R[3 * r] * L.mu[0] + cm.R[3 * r + 1] * L.mu[1] + cm.R[3 * r + 2] * L.mu[2] + cm.t[r];
+  const float z = V.p[2];
+  if (!(z >= cm.znear)) return false;
+  const float rz = 1.0f / z;
+  const float limx = kJacClamp * (0.5f * (float)cm.W / cm.fx);
+  const float limy = kJacClamp * (0.5f * (float)cm.H / cm.fy);
+  const float u = V.p[0] * rz, v = V.p[1] * rz;
+  V.uc = fminf(fmaxf(u, -limx), limx);
+  V.vc = fminf(fmaxf(v, -limy), limy);
+  V.clamp_u = V.uc != u;
+  V.clamp_v = V.vc != v;
+  const float jx = cm.fx * rz, jy = cm.fy * rz;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    V.T[k] = jx * (cm.R[k] - V.uc * cm.R[6 + k]);
+    V.T[3 + k] = jy * (cm.R[3 + k] - V.vc * cm.R[6 + k]);
+  }
+  const float *S = L.Sigma;
+  // rows of T Sigma
+  float t0[3], t1[3];
+  t0[0] = V.T[0] * S[0] + V.T[1] * S[1] + V.T[2] * S[2];
+  t0[1] = V.T[0] * S[1] + V.T[1] * S[3] + V.T[2] * S[4];
+  t0[2] = V.T[0] * S[2] + V.T[1] * S[4] + V.T[2] * S[5];
+  t1[0] = V.T[3] * S[0] + V.T[4] * S[1] + V.T[5] * S[2];
+  t1[1] = V.T[3] * S[1] + V.T[4] * S[3] + V.T[5] * S[4];
+  t1[2] = V.T[3] * S[2] + V.T[4] * S[4] + V.T[5] * S[5];
+  V.a = t0[0] * V.T[0] + t0[1] * V.T[1] + t0[2] * V.T[2] + kDilation;
+  V.b = t0[0] * V.T[3] + t0[1] * V.T[4] + t0[2] * V.T[5];
+  V.c = t1[0] * V.T[3] + t1[1] * V.T[4] + t1[2] * V.T[5] + kDilation;
+  V.det = V.a * V.c - V.b * V.b;
+  return V.det > 0.0f;
+}
+
+__global__ void k_project(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_n, DevViews vs,
+                          int tw, int th, float4 *__restrict__ splat, int32_t *__restrict__ radius,
+                          uint2 *__restrict__ rect, int64_t stride) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool alive = i < live_count(d_n, n);
+  GaussLocal L;
+  if (alive) load_gaussian(g, i, L);
+#pragma unroll 1
+  for (int v = 0; v < vs.n; ++v) {
+    const DevCam &cm = vs.cam[v];
+    const int64_t r = v * stride + i;
+    ViewLocal V;
+    if (!alive || !project_view(L, cm, V)) {
+      splat[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      splat[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      radius[r] = 0;
+      rect[r] = make_uint2(1u | (1u << 16), 0u);
+      continue;
+    }
+    const float rdet = 1.0f / V.det;
+    const float ca = V.c * rdet, cb = -V.b * rdet, cc = V.a * rdet;
+    const float rz = 1.0f / V.p[2];
+    const float mx = cm.fx * V.p[0] * rz + cm.cx;
+    const float my = cm.fy * V.p[1] * rz + cm.cy;
+    const float mid = 0.5f * (V.a + V.c);
+    const float lam = mid + sqrtf(fmaxf(0.0f, mid * mid - V.det));
+    const int rad = (int)ceilf(kSupportSigma * sqrtf(lam));
+    const float ex = kSupportSigma * sqrtf(V.a), ey = kSupportSigma * sqrtf(V.c);
+    float x0 = ceilf((mx - ex - (float)(tw - 1)) / (float)tw);
+    float x1 = floorf((mx + ex) / (float)tw);
+    float y0 = ceilf((my - ey - (float)(th - 1)) / (float)th);
+    float y1 = floorf((my + ey) / (float)th);
+    x0 = fmaxf(x0, 0.f);
+    y0 = fmaxf(y0, 0.f);
+    x1 = fminf(x1, (float)(cm.tiles_x - 1));
+    y1 = fminf(y1, (float)(cm.tiles_y - 1));
+    uint2 rc = make_uint2(1u | (1u << 16), 0u);
+    if (x0 <= x1 && y0 <= y1)
+      rc = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+    splat[2 * r] = make_float4(mx, my, ca, cb);
+    splat[2 * r + 1] = make_float4(cc, L.o, V.p[2], 0.f);
+    radius[r] = rad;
+    rect[r] = rc;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Adjoint.  grad2d[v][stride] records: mean2d x, y, conic a, b, c, opacity, depth, -.
+// Gradients are added to grads' planes; the thread owns its Gaussian, so no atomics.
+__global__ void k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_n, DevViews vs,
+                              const int32_t *__restrict__ radius, const float4 *__restrict__ grad2d,
+                              int64_t stride, GaussGrads out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n || i >= live_count(d_n, n)) return;
+  GaussLocal L;
+  load_gaussian(g, i, L);
+  float gmu[3] = {0.f, 0.f, 0.f};
+  float GSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (symmetric, xx xy xz yy yz zz)
+  float go = 0.f;
+  bool any = false;
+#pragma unroll 1
+  for (int v = 0; v < vs.n; ++v) {
+    const int64_t r = v * stride + i;
+    if (radius[r] <= 0) continue;
+    const DevCam &cm = vs.cam[v];
+    ViewLocal V;
+    if (!project_view(L, cm, V)) continue;
+    any = true;
+    const float4 gA4 = grad2d[2 * r], gB4 = grad2d[2 * r + 1];
+    const float rdet = 1.0f / V.det;
+    const float A = V.c * rdet, B = -V.b * rdet, C = V.a * rdet;
+    // dL/dSigma' = -Sigma'^-1 G Sigma'^-1 in terms of the conic (A, B, C)
+    const float gA = gA4.z, gB = gA4.w, gC = gB4.x;
+    const float ga = -(gA * A * A + gB * A * B + gC * B * B);
+    const float gb = -(2.f * gA * A * B + gB * (A * C + B * B) + 2.f * gC * B * C);
+    const float gc = -(gA * B * B + gB * B * C + gC * C * C);
+    go += gB4.y;
+    // G' (2x2 symmetric, off-diagonal gb/2)
+    const float G00 = ga, G01 = 0.5f * gb, G11 = gc;
+    // dL/dSigma += T^T G' T
+    const float *T = V.T;
+    float TG0[3], TG1[3];  // columns: (G' T)_{0,k}, (G' T)_{1,k}
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      TG0[k] = G00 * T[k] + G01 * T[3 + k];
+      TG1[k] = G01 * T[k] + G11 * T[3 + k];
+    }
+    GSig[0] += T[0] * TG0[0] + T[3] * TG1[0];
+    GSig[1] += T[0] * TG0[1] + T[3] * TG1[1];
+    GSig[2] += T[0] * TG0[2] + T[3] * TG1[2];
+    GSig[3] += T[1] * TG0[1] + T[4] * TG1[1];
+    GSig[4] += T[1] * TG0[2] + T[4] * TG1[2];
+    GSig[5] += T[2] * TG0[2] + T[5] * TG1[2];
+    // dL/dT = 2 G' T Sigma
+    const float *S = L.Sigma;
+    float GT[6];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const float *tg = rr == 0 ? TG0 : TG1;
+      GT[3 * rr + 0] = 2.f * (tg[0] * S[0] + tg[1] * S[1] + tg[2] * S[2]);
+      GT[3 * rr + 1] = 2.f * (tg[0] * S[1] + tg[1] * S[3] + tg[2] * S[4]);
+      GT[3 * rr + 2] = 2.f * (tg[0] * S[2] + tg[1] * S[4] + tg[2] * S[5]);
+    }
+    // T = J R_cam: dL/dJ = dL/dT R_cam^T (only J00, J02, J11, J12 are non-zero)
+    const float *Rc = cm.R;
+    const float GJ00 = GT[0] * Rc[0] + GT[1] * Rc[1] + GT[2] * Rc[2];
+    const float GJ02 = GT[0] * Rc[6] + GT[1] * Rc[7] + GT[2] * Rc[8];
+    const float GJ11 = GT[3] * Rc[3] + GT[4] * Rc[4] + GT[5] * Rc[5];
+    const float GJ12 = GT[3] * Rc[6] + GT[4] * Rc[7] + GT[5] * Rc[8];
+    const float x = V.p[0], y = V.p[1], z = V.p[2];
+    const float rz = 1.0f / z, rz2 = rz * rz;
+    float gp0 = 0.f, gp1 = 0.f, gp2 = 0.f;
+    gp2 += -(GJ00 * cm.fx + GJ11 * cm.fy) * rz2;
+    if (V.clamp_u) {
+      gp2 += GJ02 * cm.fx * V.uc * rz2;
+    } else {  // J02 = -fx x / z^2
+      gp0 += -GJ02 * cm.fx * rz2;
+      gp2 += GJ02 * 2.f * cm.fx * x * rz2 * rz;
+    }
+    if (V.clamp_v) {
+      gp2 += GJ12 * cm.fy * V.vc * rz2;
+    } else {
+      gp1 += -GJ12 * cm.fy * rz2;
+      gp2 += GJ12 * 2.f * cm.fy * y * rz2 * rz;
+    }
+    // mean2d = (fx x/z + cx, fy y/z + cy); depth gamma = z
+    gp0 += gA4.x * cm.fx * rz;
+    gp1 += gA4.y * cm.fy * rz;
+    gp2 += -(gA4.x * cm.fx * x + gA4.y * cm.fy * y) * rz2 + gB4.z;
+    // p = R_cam mu + t
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gmu[k] += Rc[k] * gp0 + Rc[3 + k] * gp1 + Rc[6 + k] * gp2;
+  }
+  const int64_t c = out.cap;
+  out.logits[i] += go * L.o * (1.f - L.o);
+  if (!any) return;
+  out.means[i] += gmu[0];
+  out.means[c + i] += gmu[1];
+  out.means[2 * c + i] += gmu[2];
+  // Sigma = M M^T, M = R diag(s): dL/dM = 2 GSig M
+  float M[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) M[3 * r + k] = L.R[3 * r + k] * L.s[k];
+  const float GS[9] = {GSig[0], GSig[1], GSig[2], GSig[1], GSig[3], GSig[4], GSig[2], GSig[4], GSig[5]};
+  float gR[9];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float gs = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float gm = 2.f * (GS[3 * r] * M[k] + GS[3 * r + 1] * M[3 + k] + GS[3 * r + 2] * M[6 + k]);
+      gs += gm * L.R[3 * r + k];
+      gR[3 * r + k] = gm * L.s[k];
+    }
+    out.log_scales[k * c + i] += gs * L.s[k];
+  }
+  const float w = L.qn[0], qx = L.qn[1], qy = L.qn[2], qz = L.qn[3];
+  float gq[4];
+  gq[0] = 2.f * (-gR[1] * qz + gR[2] * qy + gR[3] * qz - gR[5] * qx - gR[6] * qy + gR[7] * qx);
+  gq[1] = 2.f * (gR[1] * qy + gR[2] * qz + gR[3] * qy - 2.f * gR[4] * qx - gR[5] * w + gR[6] * qz +
+                 gR[7] * w - 2.f * gR[8] * qx);
+  gq[2] = 2.f * (-2.f * gR[0] * qy + gR[1] * qx + gR[2] * w + gR[3] * qx + gR[5] * qz - gR[6] * w +
+                 gR[7] * qz - 2.f * gR[8] * qy);
+  gq[3] = 2.f * (-2.f * gR[0] * qz - gR[1] * w + gR[2] * qx + gR[3] * w - 2.f * gR[4] * qz +
+                 gR[5] * qy + gR[6] * qx + gR[7] * qy);
+  const float dot = w * gq[0] + qx * gq[1] + qy * gq[2] + qz * gq[3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out.quats[k * c + i] += (gq[k] - L.qn[k] * dot) * L.qinv;
+}
+
+fgs_status launch_project_bwd(const fgs_gaussians *g, const DevViews &vs, const int32_t *radius,
+                              const float *grad2d, int64_t stride, fgs_gaussians *grads,
+                              cudaStream_t st) {
+  if (g->n == 0) return FGS_OK;
+  const int threads = 256;
+  const int64_t blocks = (g->n + threads - 1) / threads;
+  k_project_bwd<<<(unsigned)blocks, threads, 0, st>>>(gauss_ptrs(g), g->n, g->d_n, vs, radius,
+                                                       reinterpret_cast<const float4 *>(grad2d), stride,
+                                                       gauss_grads(grads));
+  count_launch();
+  FGS_CHECK_LAUNCH("project_bwd");
+  return FGS_OK;
+}
+
+}  // namespace fgs
+
+using namespace fgs;
+
+extern "C" fgs_status fgs_project(const fgs_gaussians *g, const fgs_camera *cams, int32_t n_views,
+                                  fgs_tiling tiling, fgs_projected *out, int32_t *d_status,
+                                  void *stream) {
+  (void)d_status;
+  if (!gaussians_ok(g, "g")) return FGS_ERR_INVALID_ARGUMENT;
+  FGS_CHECK_ARG(tiling_ok(tiling), "fgs_project: unsupported tiling %dx%d/%d", tiling.tile_w,
+                tiling.tile_h, tiling.batch_depth);
+  FGS_CHECK_ARG(out && out->splat && out->radius && out->rect, "fgs_project: NULL output");
+  FGS_CHECK_ARG(out->stride >= g->n, "fgs_project: stride < n");
+  FGS_CHECK_ARG((reinterpret_cast<uintptr_t>(out->splat) & 15) == 0 &&
+                    (reinterpret_cast<uintptr_t>(out->rect) & 7) == 0,
+                "fgs_project: splat must be 16-byte and rect 8-byte aligned");
+  DevViews vs;
+  if (!make_views(cams, n_views, tiling.tile_w, tiling.tile_h, &vs)) return FGS_ERR_INVALID_ARGUMENT;
+  if (g->n == 0) return FGS_OK;
+  const int threads = 256;
+  const int64_t blocks = (g->n + threads - 1) / threads;
+  k_project<<<(unsigned)blocks, threads, 0, as_stream(stream)>>>(
+      gauss_ptrs(g), g->n, g->d_n, vs, tiling.tile_w, tiling.tile_h,
+      reinterpret_cast<float4 *>(out->splat), out->radius, reinterpret_cast<uint2 *>(out->rect),
+      out->stride);
+  count_launch();
+  FGS_CHECK_LAUNCH("fgs_project");
+  return FGS_OK;
+}
+
+extern "C" fgs_status fgs_project_bwd(const fgs_gaussians *g, const fgs_projected *proj, const fgs_camera *cams,
+                                      int32_t n_views, const float *grad2d, fgs_gaussians *grads, void *stream) {
+  if (!gaussians_ok(g, "g") || !gaussians_ok(grads, "grads")) return FGS_ERR_INVALID_ARGUMENT;
+  FGS_CHECK_ARG(grads->n >= g->n, "fgs_project_bwd: grads->n < g->n");
+  FGS_CHECK_ARG(proj && proj->radius && proj->stride >= g->n && grad2d, "fgs_project_bwd: NULL argument");
+  FGS_CHECK_ARG((reinterpret_cast<uintptr_t>(grad2d) & 15) == 0, "fgs_project_bwd: grad2d alignment");
+  DevViews vs;
+  if (!make_views(cams, n_views, 16, 16, &vs)) return FGS_ERR_INVALID_ARGUMENT;
+  return launch_project_bwd(g, vs, proj->radius, grad2d, proj->stride, grads, as_stream(stream));
+}

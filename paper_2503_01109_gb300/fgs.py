@@ -1,0 +1,392 @@
+"""Thin ctypes binding of libfgs.so (the C ABI in include/fgs.h).
+
+Every ``fgs_*`` function here marshals torch tensors into the C structs and
+calls the entry point of the same name; all computation runs in the library's
+CUDA kernels on the current torch stream.  There is no fallback: a missing or
+unloadable library raises.
+
+Besides the raw calls, :class:`GaussianMap` keeps the structure-of-arrays
+Gaussian planes (``[14][capacity]`` float32: means 3, log-scales 3, quaternion 4,
+opacity logit 1, rgb 3) and :class:`Frame` the per-view render buffers.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfgs.so")
+
+c_void_p, c_int32, c_int64, c_float, c_size_t = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
+                                                 ctypes.c_size_t)
+
+FGS_DEV_PAIR_OVERFLOW, FGS_DEV_TIMEOUT, FGS_DEV_NONFINITE, FGS_DEV_MAP_FULL, FGS_DEV_WORK_OVERFLOW = 1, 2, 4, 8, 16
+MAX_VIEWS = 16
+PRIOR_IN, PRIOR_HID, PRIOR_OUT = 272, 128, 4
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("fx", c_float), ("fy", c_float), ("cx", c_float),
+                ("cy", c_float), ("world_to_cam", c_float * 12), ("znear", c_float)]
+
+
+class Gaussians(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("capacity", c_int64), ("d_n", c_void_p), ("means", c_void_p),
+                ("log_scales", c_void_p), ("quats", c_void_p), ("opacity_logits", c_void_p), ("rgb", c_void_p)]
+
+
+class Projected(ctypes.Structure):
+    _fields_ = [("stride", c_int64), ("splat", c_void_p), ("radius", c_void_p), ("rect", c_void_p)]
+
+
+class Tiling(ctypes.Structure):
+    _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch_depth", c_int32)]
+
+
+class LossParams(ctypes.Structure):
+    _fields_ = [("w_l1_color", c_float), ("w_l1_depth", c_float), ("w_ssim", c_float)]
+
+
+class AdamParams(ctypes.Structure):
+    _fields_ = [("lr", c_float * 5), ("beta1", c_float), ("beta2", c_float), ("eps", c_float), ("step", c_int32)]
+
+
+class SeedParams(ctypes.Structure):
+    _fields_ = [("d0", c_float), ("m", c_int32), ("n", c_int32), ("alpha_h", c_float), ("alpha_l", c_float),
+                ("tau_alpha", c_float), ("tau_depth_rel", c_float), ("tau_color", c_float), ("max_new", c_int32),
+                ("init_logit", c_float), ("prior_max_dev", c_float)]
+
+
+class MLP(ctypes.Structure):
+    _fields_ = [("w1", c_void_p), ("b1", c_void_p), ("w2", c_void_p), ("b2", c_void_p), ("w3", c_void_p),
+                ("b3", c_void_p)]
+
+
+class MLPMaster(ctypes.Structure):
+    _fields_ = [("w1", c_void_p), ("b1", c_void_p), ("w2", c_void_p), ("b2", c_void_p), ("w3", c_void_p),
+                ("b3", c_void_p), ("m", c_void_p), ("v", c_void_p)]
+
+
+class TrainParams(ctypes.Structure):
+    _fields_ = [("lr", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float), ("step", c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "fgs_project": ([c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_num_tiles": ([c_void_p, c_int32, Tiling], c_int64),
+    "fgs_bin_sort": ([c_void_p, c_int64, c_void_p, c_int32, Tiling, c_void_p, c_size_t, c_void_p, c_void_p, c_int64,
+                      c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_bin_sort_workspace_size": ([c_int64, c_int64], c_size_t),
+    "fgs_render_fwd": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p, c_void_p,
+                        c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_render_bwd": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p, c_void_p,
+                        c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_render_bwd_splats": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p,
+                               c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_project_bwd": ([c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_loss": ([c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                  c_void_p, c_size_t, c_void_p], c_int32),
+    "fgs_loss_workspace_size": ([c_void_p, c_int32], c_size_t),
+    "fgs_scale_reg": ([c_void_p, c_float, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p], c_int32),
+    "fgs_scale_reg_workspace_size": ([c_int64], c_size_t),
+    "fgs_adam": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_last_error": ([], ctypes.c_char_p),
+    "fgs_version": ([], c_int32),
+    "fgs_launch_count": ([], c_int64),
+    "fgs_memset_async": ([c_void_p, c_int32, c_size_t, c_void_p], c_int32),
+}
+_OPTIONAL = {
+    "fgs_fourier_seed": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                          c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
+    "fgs_fourier_seed_workspace_size": ([c_int32, c_int32], c_size_t),
+    "fgs_prior_features": ([c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p], c_int32),
+    "fgs_prior_infer": ([c_void_p, c_void_p, c_int64, c_void_p, c_void_p], c_int32),
+    "fgs_prior_train": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_size_t,
+                         c_void_p], c_int32),
+    "fgs_prior_train_workspace_size": ([c_int64], c_size_t),
+    "fgs_prior_num_params": ([], c_int64),
+}
+
+
+def lib():
+    """Loads libfgs.so (raises when it is missing: there is no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libfgs.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes, f.restype = args, res
+            for name, (args, res) in _OPTIONAL.items():
+                if hasattr(L, name):
+                    f = getattr(L, name)
+                    f.argtypes, f.restype = args, res
+            _lib = L
+    return _lib
+
+
+class FGSError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise FGSError(f"{what} failed with status {rc}: {lib().fgs_last_error().decode()}")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def launch_count() -> int:
+    return int(lib().fgs_launch_count())
+
+
+# ----------------------------------------------------------------------------------
+# host structs
+
+def camera_struct(cam: dict) -> Camera:
+    c = Camera()
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    c.fx, c.fy, c.cx, c.cy = float(cam["fx"]), float(cam["fy"]), float(cam["cx"]), float(cam["cy"])
+    w2c = np.asarray(cam["world_to_cam"], np.float32).reshape(-1)
+    for k in range(12):
+        c.world_to_cam[k] = float(w2c[k])
+    c.znear = float(cam.get("znear", 0.2))
+    return c
+
+
+def camera_array(cams: list):
+    arr = (Camera * len(cams))()
+    for i, cam in enumerate(cams):
+        arr[i] = camera_struct(cam)
+    return arr
+
+
+def tiling(tile_w=16, tile_h=16, batch_depth=128) -> Tiling:
+    return Tiling(int(tile_w), int(tile_h), int(batch_depth))
+
+
+def num_tiles(cams: list, til: Tiling) -> int:
+    t = lib().fgs_num_tiles(camera_array(cams), len(cams), til)
+    if t < 0:
+        raise FGSError("bad cameras or tiling")
+    return int(t)
+
+
+# ----------------------------------------------------------------------------------
+# device containers
+
+PLANES = {"means": (0, 3), "log_scales": (3, 6), "quats": (6, 10), "logits": (10, 11), "rgb": (11, 14)}
+
+
+class GaussianMap:
+    """Structure-of-arrays Gaussian planes [14][capacity] on one device buffer."""
+
+    def __init__(self, capacity: int, device="cuda", n: int = 0):
+        self.capacity = int(capacity)
+        self.buf = torch.zeros(14, self.capacity, dtype=torch.float32, device=device)
+        self.n = int(n)
+        self.d_n = torch.zeros(1, dtype=torch.int64, device=device)
+
+    @classmethod
+    def from_scene(cls, scene: dict, capacity: int | None = None, device="cuda") -> "GaussianMap":
+        n = scene["means"].shape[-1]
+        g = cls(capacity or n, device, n)
+        for k, (a, b) in PLANES.items():
+            g.buf[a:b, :n] = torch.as_tensor(np.asarray(scene[k], np.float32).reshape(b - a, n), device=device)
+        g.d_n.fill_(n)
+        return g
+
+    def zeros_like(self) -> "GaussianMap":
+        g = GaussianMap(self.capacity, self.buf.device, self.n)
+        g.d_n.copy_(self.d_n)
+        return g
+
+    def plane(self, name):
+        a, b = PLANES[name]
+        return self.buf[a:b]
+
+    def struct(self, use_device_count: bool = False, n: int | None = None) -> Gaussians:
+        s = Gaussians()
+        # with the device count, n is only an upper bound: the whole capacity
+        s.n = (self.capacity if use_device_count else self.n) if n is None else int(n)
+        s.capacity = self.capacity
+        s.d_n = self.d_n.data_ptr() if use_device_count else None
+        base = self.buf.data_ptr()
+        row = 4 * self.capacity
+        s.means, s.log_scales, s.quats = base, base + 3 * row, base + 6 * row
+        s.opacity_logits, s.rgb = base + 10 * row, base + 11 * row
+        return s
+
+    def to_scene(self, n: int | None = None) -> dict:
+        n = self.n if n is None else n
+        out = {}
+        for k, (a, b) in PLANES.items():
+            v = self.buf[a:b, :n].detach().cpu().numpy()
+            out[k] = v[0].copy() if b - a == 1 else v.copy()
+        return out
+
+
+class Projection:
+    """Per-view splat records of a map: splat [V][stride][8], radius, rect."""
+
+    def __init__(self, n_views: int, stride: int, device="cuda"):
+        self.n_views, self.stride = n_views, int(stride)
+        self.splat = torch.zeros(n_views, self.stride, 8, dtype=torch.float32, device=device)
+        self.radius = torch.zeros(n_views, self.stride, dtype=torch.int32, device=device)
+        self.rect = torch.zeros(n_views, self.stride, 4, dtype=torch.int16, device=device)
+
+    def struct(self) -> Projected:
+        return Projected(self.stride, self.splat.data_ptr(), self.radius.data_ptr(), self.rect.data_ptr())
+
+
+def image_sizes(cams: list):
+    return [int(c["width"]) * int(c["height"]) for c in cams]
+
+
+class Frame:
+    """Render outputs / upstream gradients of a view set (concatenated per view)."""
+
+    def __init__(self, cams: list, device="cuda"):
+        P = sum(image_sizes(cams))
+        self.cams = cams
+        self.total_pix = P
+        self.color = torch.zeros(3 * P, dtype=torch.float32, device=device)
+        self.depth = torch.zeros(P, dtype=torch.float32, device=device)
+        self.alpha = torch.zeros(P, dtype=torch.float32, device=device)
+        self.t_final = torch.zeros(P, dtype=torch.float32, device=device)
+        self.n_contrib = torch.zeros(P, dtype=torch.int32, device=device)
+
+    def view(self, v: int) -> dict:
+        sizes = image_sizes(self.cams)
+        o = sum(sizes[:v])
+        H, W = self.cams[v]["height"], self.cams[v]["width"]
+        return {"color": self.color[3 * o:3 * o + 3 * H * W].view(3, H, W), "depth": self.depth[o:o + H * W].view(H, W),
+                "alpha": self.alpha[o:o + H * W].view(H, W), "t_final": self.t_final[o:o + H * W].view(H, W),
+                "n_contrib": self.n_contrib[o:o + H * W].view(H, W)}
+
+
+def pack_images(cams: list, colors: list, depths: list, device="cuda"):
+    """Concatenates per-view colour [3][H][W] and depth [H][W] arrays."""
+    c = torch.cat([torch.as_tensor(np.asarray(x, np.float32)).reshape(-1) for x in colors]).to(device)
+    d = torch.cat([torch.as_tensor(np.asarray(x, np.float32)).reshape(-1) for x in depths]).to(device)
+    return c, d
+
+
+# ----------------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+
+def fgs_project(g: GaussianMap, cams: list, til: Tiling, proj: Projection, status: torch.Tensor | None = None,
+                use_device_count: bool = False):
+    gs = g.struct(use_device_count)
+    ps = proj.struct()
+    _check(lib().fgs_project(ctypes.byref(gs), camera_array(cams), len(cams), til, ctypes.byref(ps), _ptr(status),
+                             _stream()), "fgs_project")
+
+
+def fgs_bin_sort_workspace_size(n_records: int, pair_capacity: int) -> int:
+    return int(lib().fgs_bin_sort_workspace_size(int(n_records), int(pair_capacity)))
+
+
+def fgs_bin_sort(proj: Projection, n: int, cams: list, til: Tiling, ws: torch.Tensor, tile_keys: torch.Tensor,
+                 ids: torch.Tensor, tile_ranges: torch.Tensor, num_pairs: torch.Tensor, status: torch.Tensor | None):
+    ps = proj.struct()
+    _check(lib().fgs_bin_sort(ctypes.byref(ps), int(n), camera_array(cams), len(cams), til, _ptr(ws),
+                              ws.numel() * ws.element_size(), _ptr(tile_keys), _ptr(ids), tile_keys.numel(),
+                              _ptr(tile_ranges), _ptr(num_pairs), _ptr(status), _stream()), "fgs_bin_sort")
+
+
+def fgs_render_fwd(proj: Projection, g: GaussianMap, cams: list, til: Tiling, ids, tile_ranges, frame: Frame,
+                   status=None):
+    ps = proj.struct()
+    gs = g.struct()
+    _check(lib().fgs_render_fwd(ctypes.byref(ps), ctypes.byref(gs), camera_array(cams), len(cams), til, _ptr(ids),
+                                _ptr(tile_ranges), _ptr(frame.color), _ptr(frame.depth), _ptr(frame.alpha),
+                                _ptr(frame.t_final), _ptr(frame.n_contrib), _ptr(status), _stream()),
+           "fgs_render_fwd")
+
+
+def fgs_render_bwd(g: GaussianMap, proj: Projection, cams: list, til: Tiling, ids, tile_ranges, frame: Frame,
+                   dC, dD, dA, grad2d, grads: GaussianMap, status=None, use_device_count: bool = False):
+    gs = g.struct(use_device_count)
+    ps = proj.struct()
+    gr = grads.struct(use_device_count)
+    _check(lib().fgs_render_bwd(ctypes.byref(gs), ctypes.byref(ps), camera_array(cams), len(cams), til, _ptr(ids),
+                                _ptr(tile_ranges), _ptr(frame.t_final), _ptr(frame.n_contrib), _ptr(dC), _ptr(dD),
+                                _ptr(dA), _ptr(grad2d), ctypes.byref(gr), _ptr(status), _stream()),
+           "fgs_render_bwd")
+
+
+def fgs_render_bwd_splats(g: GaussianMap, proj: Projection, cams: list, til: Tiling, ids, tile_ranges, frame: Frame,
+                          dC, dD, dA, grad2d, grads: GaussianMap, status=None, use_device_count: bool = False):
+    gs, ps, gr = g.struct(use_device_count), proj.struct(), grads.struct(use_device_count)
+    _check(lib().fgs_render_bwd_splats(ctypes.byref(gs), ctypes.byref(ps), camera_array(cams), len(cams), til,
+                                       _ptr(ids), _ptr(tile_ranges), _ptr(frame.t_final), _ptr(frame.n_contrib),
+                                       _ptr(dC), _ptr(dD), _ptr(dA), _ptr(grad2d), ctypes.byref(gr), _ptr(status),
+                                       _stream()), "fgs_render_bwd_splats")
+
+
+def fgs_project_bwd(g: GaussianMap, proj: Projection, cams: list, grad2d, grads: GaussianMap,
+                    use_device_count: bool = False):
+    gs, ps, gr = g.struct(use_device_count), proj.struct(), grads.struct(use_device_count)
+    _check(lib().fgs_project_bwd(ctypes.byref(gs), ctypes.byref(ps), camera_array(cams), len(cams), _ptr(grad2d),
+                                 ctypes.byref(gr), _stream()), "fgs_project_bwd")
+
+
+def fgs_loss_workspace_size(cams: list) -> int:
+    return int(lib().fgs_loss_workspace_size(camera_array(cams), len(cams)))
+
+
+def fgs_loss(cams: list, color, depth, color_gt, depth_gt, w_c, w_d, w_s, dC, dD, loss_acc, ws):
+    p = LossParams(float(w_c), float(w_d), float(w_s))
+    _check(lib().fgs_loss(camera_array(cams), len(cams), _ptr(color), _ptr(depth), _ptr(color_gt), _ptr(depth_gt),
+                          ctypes.byref(p), _ptr(dC), _ptr(dD), _ptr(loss_acc), _ptr(ws),
+                          ws.numel() * ws.element_size(), _stream()), "fgs_loss")
+
+
+def fgs_scale_reg_workspace_size(n: int) -> int:
+    return int(lib().fgs_scale_reg_workspace_size(int(n)))
+
+
+def fgs_scale_reg(g: GaussianMap, weight: float, grads: GaussianMap, loss_acc, ws, use_device_count=False):
+    gs, gr = g.struct(use_device_count), grads.struct(use_device_count)
+    _check(lib().fgs_scale_reg(ctypes.byref(gs), float(weight), ctypes.byref(gr), _ptr(loss_acc), _ptr(ws),
+                               ws.numel() * ws.element_size(), _stream()), "fgs_scale_reg")
+
+
+DEFAULT_LR = (1e-3, 5e-3, 1e-3, 5e-2, 2.5e-3)
+
+
+def fgs_adam(g: GaussianMap, grads: GaussianMap, m: GaussianMap, v: GaussianMap, lr=DEFAULT_LR, beta1=0.9,
+             beta2=0.999, eps=1e-15, step: int = 1, d_step=None, use_device_count=False):
+    hp = AdamParams()
+    for k in range(5):
+        hp.lr[k] = float(lr[k])
+    hp.beta1, hp.beta2, hp.eps, hp.step = beta1, beta2, eps, int(step)
+    gs, gr, ms, vs = (x.struct(use_device_count) for x in (g, grads, m, v))
+    _check(lib().fgs_adam(ctypes.byref(gs), ctypes.byref(gr), ctypes.byref(ms), ctypes.byref(vs), ctypes.byref(hp),
+                          _ptr(d_step), _stream()), "fgs_adam")
+
+
+def fgs_memset_async(t: torch.Tensor, value: int = 0):
+    _check(lib().fgs_memset_async(_ptr(t), int(value), t.numel() * t.element_size(), _stream()), "fgs_memset_async")
+
+
+def ws_tensor(nbytes: int, device="cuda") -> torch.Tensor:
+    """Workspace of at least nbytes, 256-byte aligned (torch allocations are)."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)

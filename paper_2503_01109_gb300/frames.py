@@ -1,0 +1,233 @@
+"""Per-frame mapping pipeline over a camera trajectory (the benchmark workload).
+
+For every frame: render the map at the frame's pose (eq1's colour, depth and
+opacity readings), seed new Gaussians with the Fourier analysis of Sec. III-A
+(eq2-eq11, plus the learned prior when one is given), then run a few mapping
+iterations (Sec. III-D).  The live Gaussian count stays on the device, so a
+frame needs no host synchronisation.
+
+Ground-truth frames are renders of a separate seeded scene made with the same
+library (colour, and depth normalised by the rendered opacity where it exceeds
+0.5, else 0 = invalid), standing in for an RGB-D sensor.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import fgs
+from .mapping import Mapper, PAPER_LOSS, PAPER_REG
+
+
+class KernelTimer:
+    """CUDA events around selected library calls on the current stream."""
+
+    def __init__(self):
+        self.on = False
+        self.events = {}
+
+    def enable(self):
+        self.on = True
+        self.events = {}
+
+    def disable(self):
+        self.on = False
+
+    def span(self, name):
+        timer = self
+
+        class _Span:
+            def __enter__(self_):
+                if timer.on:
+                    self_.e0 = torch.cuda.Event(enable_timing=True)
+                    self_.e0.record(torch.cuda.current_stream())
+
+            def __exit__(self_, *a):
+                if timer.on:
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e1.record(torch.cuda.current_stream())
+                    timer.events.setdefault(name, []).append((self_.e0, e1))
+        return _Span()
+
+    def durations(self, name):
+        return [a.elapsed_time(b) for a, b in self.events.get(name, [])]
+
+    def summary(self, steps):
+        return {k: round(sum(self.durations(k)) / max(steps, 1), 4) for k in self.events}
+
+
+class TimedMapper(Mapper):
+    """Mapper whose render and adjoint calls are bracketed by timer spans and whose
+    per-launch work (sum of per-pixel contributor counts) is snapshotted."""
+
+    def __init__(self, *a, timer: KernelTimer | None = None, **kw):
+        super().__init__(*a, **kw)
+        self.timer = timer or KernelTimer()
+        self.nc_snap = []          # (render belongs to an iteration, n_contrib copy)
+        self._in_iteration = False
+
+    def render(self):
+        with self.timer.span("project"):
+            fgs.fgs_project(self.g, self.cams, self.til, self.proj, self.status, self.use_dc)
+        n = self.g.capacity if self.use_dc else self.g.n
+        with self.timer.span("bin_sort"):
+            fgs.fgs_bin_sort(self.proj, n, self.cams, self.til, self.ws_bin, self.tile_keys, self.ids, self.ranges,
+                             self.num_pairs, self.status)
+        with self.timer.span("render_fwd"):
+            fgs.fgs_render_fwd(self.proj, self.g, self.cams, self.til, self.ids, self.ranges, self.frame, self.status)
+        if self.timer.on:
+            snap = torch.empty_like(self.frame.n_contrib)
+            snap.copy_(self.frame.n_contrib)   # device copy (copy engine), summed after timing
+            self.nc_snap.append((self._in_iteration, snap))
+
+    def backward(self, dC, dD, dA=None):
+        fgs.fgs_memset_async(self.grads.buf)
+        fgs.fgs_memset_async(self.grad2d)
+        with self.timer.span("render_bwd"):
+            fgs.fgs_render_bwd_splats(self.g, self.proj, self.cams, self.til, self.ids, self.ranges, self.frame, dC,
+                                      dD, dA, self.grad2d, self.grads, self.status, self.use_dc)
+        with self.timer.span("project_bwd"):
+            fgs.fgs_project_bwd(self.g, self.proj, self.cams, self.grad2d, self.grads, self.use_dc)
+
+    def iteration(self):
+        self._in_iteration = True
+        self.render()
+        self._in_iteration = False
+        fgs.fgs_memset_async(self.loss_acc)
+        with self.timer.span("loss"):
+            fgs.fgs_loss(self.cams, self.frame.color, self.frame.depth, self.color_gt, self.depth_gt, *self.loss_w,
+                         self.dC, self.dD, self.loss_acc, self.ws_loss)
+        self.backward(self.dC, self.dD)
+        if self.reg_w != 0.0:
+            fgs.fgs_scale_reg(self.g, self.reg_w, self.grads, self.loss_acc, self.ws_reg, self.use_dc)
+        self.host_step += 1
+        with self.timer.span("adam"):
+            fgs.fgs_adam(self.g, self.grads, self.m, self.v, self.lr, step=self.host_step,
+                         d_step=self.d_step if self.use_dc else None, use_device_count=self.use_dc)
+
+
+def render_targets(gt_scene: dict, cams: list, tile=(16, 16), batch=128, device="cuda"):
+    """Colour and normalised depth of the ground-truth scene at every pose."""
+    g = fgs.GaussianMap.from_scene(gt_scene, device=device)
+    m = Mapper(g, cams[:1], fgs.tiling(*tile, batch), use_device_count=False)
+    colors, depths = [], []
+    for cam in cams:
+        m.set_cameras([cam])
+        m.render()
+        A = m.frame.alpha
+        D = torch.where(A > 0.5, m.frame.depth / A.clamp_min(1e-6), torch.zeros_like(A))
+        colors.append(m.frame.color.clone())
+        depths.append(D)
+    torch.cuda.synchronize()
+    m.check_status()
+    del m, g
+    return colors, depths
+
+
+class FramePipeline:
+    def __init__(self, scene: dict, cams: list, gt_scene: dict, capacity: int, tile=(16, 16), batch=128,
+                 iters_per_frame: int = 3, device="cuda", loss_w=PAPER_LOSS, reg_w=PAPER_REG, seed_params=None,
+                 prior=None):
+        self.cams = cams
+        self.iters = iters_per_frame
+        self.kernel_timer = KernelTimer()
+        self.colors, self.depths = render_targets(gt_scene, cams, tile, batch, device)
+        self.g = fgs.GaussianMap.from_scene(scene, capacity, device)
+        self.mapper = TimedMapper(self.g, cams[:1], fgs.tiling(*tile, batch), loss_w=loss_w, reg_w=reg_w,
+                                  use_device_count=True, timer=self.kernel_timer)
+        self.seeder = None
+        try:
+            from .seeding import Seeder
+            self.seeder = Seeder(self.mapper, seed_params, prior)
+        except (ImportError, AttributeError, fgs.FGSError):
+            self.seeder = None
+        self.loss_host = torch.zeros(1, dtype=torch.float32).pin_memory()
+        self.stage_c = torch.zeros_like(self.colors[0])
+        self.stage_d = torch.zeros_like(self.depths[0])
+
+    # ------------------------------------------------------------------------------
+    def _use_frame(self, k: int, from_host=None):
+        self.mapper.set_cameras([self.cams[k]])
+        if from_host is None:       # frames already resident in HBM: point at them
+            self.mapper.color_gt = self.colors[k]
+            self.mapper.depth_gt = self.depths[k]
+        else:                       # end-to-end: copy this frame from pinned host memory
+            c, d = from_host
+            self.stage_c.copy_(c, non_blocking=True)
+            self.stage_d.copy_(d, non_blocking=True)
+            self.mapper.color_gt, self.mapper.depth_gt = self.stage_c, self.stage_d
+
+    def mapping_step(self, k: int, from_host=None):
+        self._use_frame(k % len(self.cams), from_host)
+        self.mapper.iteration()
+
+    def frame_step(self, k: int, from_host=None):
+        self._use_frame(k % len(self.cams), from_host)
+        if self.seeder is not None:
+            with self.kernel_timer.span("seed"):
+                self.seeder.seed_frame(self.mapper.color_gt, self.mapper.depth_gt, self.cams[k % len(self.cams)])
+        for _ in range(self.iters):
+            self.mapper.iteration()
+
+    # ------------------------------------------------------------------------------
+    def check(self):
+        torch.cuda.synchronize()
+        self.mapper.check_status()
+
+    def live_count(self) -> int:
+        return int(self.g.d_n.item())
+
+    def last_pairs(self) -> int:
+        return int(self.mapper.num_pairs.item())
+
+    def e2e_measure(self, warmup: int, steps: int, step_fn):
+        """The same steps with each frame's colour + depth copied from pinned host
+        memory and the loss read back to the host inside the timed region."""
+        hosts = [(c.cpu().pin_memory(), d.cpu().pin_memory()) for c, d in zip(self.colors, self.depths)]
+        h2d = hosts[0][0].numel() * 4 + hosts[0][1].numel() * 4
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(warmup, warmup + steps):
+            step_fn(k, from_host=hosts[k % len(hosts)])
+            self.loss_host.copy_(self.mapper.loss_acc, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"ms": e0.elapsed_time(e1), "h2d": h2d, "d2h": 4}
+
+    # ------------------------------------------------------------------------------
+    # roofline of the dominant kernel
+    FLOP_FWD_PAIR = 27  # per evaluated (pixel, splat): see the design doc
+    FLOP_BWD_PAIR = 68
+
+    def contributor_work(self, iterations_only: bool = False):
+        """Sum over pixels of contributor counts, one entry per timed render."""
+        return [int(s.sum().item()) for it, s in self.mapper.nc_snap if it or not iterations_only]
+
+    def roofline(self, peaks: dict):
+        t = self.kernel_timer
+        totals = {k: sum(t.durations(k)) for k in t.events}
+        if not totals:
+            return None
+        fwd = t.durations("render_fwd")
+        bwd = t.durations("render_bwd")
+        name = max(("render_fwd", "render_bwd"), key=lambda k: totals.get(k, 0.0))
+        durs = fwd if name == "render_fwd" else bwd
+        per_pair = self.FLOP_FWD_PAIR if name == "render_fwd" else self.FLOP_BWD_PAIR
+        # the bwd of iteration i walks the lists rendered by the fwd of iteration i;
+        # the seeding render of a frame has no backward
+        w = self.contributor_work(iterations_only=(name == "render_bwd"))
+        n = min(len(w), len(durs))
+        if n == 0:
+            return None
+        flops = np.array(w[-n:], np.float64) * per_pair
+        secs = np.array(durs[-n:], np.float64) / 1e3
+        achieved = float(np.mean(flops / secs)) / 1e12
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 FLOP x max SM clock
+        return {"kernel": name, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)",
+                "share_of_step": round(totals[name] / sum(totals.values()), 3),
+                "avg_launch_ms": round(float(np.mean(durs)), 4)}
