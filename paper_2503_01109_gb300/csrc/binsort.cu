@@ -20,7 +20,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
 constexpr int kSortMaxBlocks = 1024;
-constexpr int kScanThreads = 1024;
+constexpr int kScanThreads = 1024;  // also the largest block count of a sort pass
 
 __device__ __forceinline__ uint32_t item_count(const int64_t *d_count, int64_t host_count, int64_t cap) {
   int64_t c = d_count ? *d_count : host_count;
@@ -43,14 +43,19 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
                                                                 int64_t cap, int shift,
                                                                 uint32_t *__restrict__ counts) {
   __shared__ uint32_t hist[kSortThreads / 32][256];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int d = lane; d < 256; d += 32) hist[warp][d] = 0;
+  const int warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x & 31; d < 256; d += 32) hist[warp][d] = 0;
   __syncthreads();
   const uint32_t count = item_count(d_count, host_count, cap);
   uint32_t lo, hi;
   block_chunk(count, gridDim.x, blockIdx.x, lo, hi);
-  for (uint32_t i = lo + threadIdx.x; i < hi; i += kSortThreads)
-    atomicAdd(&hist[warp][(keys[i] >> shift) & 255u], 1u);
+  const int lane = threadIdx.x & 31;
+  for (uint32_t i0 = lo; i0 < hi; i0 += kSortThreads) {
+    const uint32_t i = i0 + threadIdx.x;
+    const int d = i < hi ? (int)((keys[i] >> shift) & 255u) : 256;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (d < 256 && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][d], (uint32_t)__popc(peers));
+  }
   __syncthreads();
   if (threadIdx.x < 256) {
     uint32_t s = 0;
@@ -60,33 +65,42 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
   }
 }
 
-// Exclusive scan of n (<= 1024 * per-thread segment) uint32 values by one block.
-__global__ void __launch_bounds__(kScanThreads) k_scan_small(uint32_t *__restrict__ data, int n) {
-  __shared__ uint32_t part[kScanThreads];
-  const int per = (n + kScanThreads - 1) / kScanThreads;
-  const int lo = threadIdx.x * per, hi = min(n, lo + per);
-  uint32_t s = 0;
-  for (int i = lo; i < hi; ++i) s += data[i];
-  part[threadIdx.x] = s;
+// Per-digit exclusive scan over the blocks' counts (one CTA per digit, nb <= 1024),
+// in place; digit_total[d] receives the digit's item count.
+__global__ void __launch_bounds__(kScanThreads) k_digit_scan(uint32_t *__restrict__ counts, int nb,
+                                                             uint32_t *__restrict__ digit_total) {
+  __shared__ uint32_t warp_sum[kScanThreads / 32];
+  const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *row = counts + (size_t)d * nb;
+  const uint32_t c = threadIdx.x < nb ? row[threadIdx.x] : 0u;
+  uint32_t incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_sum[warp] = incl;
   __syncthreads();
-  for (int off = 1; off < kScanThreads; off <<= 1) {
-    uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = warp_sum[lane];
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    warp_sum[lane] = wi - w;
+    if (lane == 31) digit_total[d] = wi;
   }
-  uint32_t run = part[threadIdx.x] - s;
-  for (int i = lo; i < hi; ++i) {
-    uint32_t v = data[i];
-    data[i] = run;
-    run += v;
-  }
+  __syncthreads();
+  if (threadIdx.x < nb) row[threadIdx.x] = warp_sum[warp] + incl - c;
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const int64_t *d_count,
-    int64_t host_count, int64_t cap, int shift, const uint32_t *__restrict__ offsets) {
+    int64_t host_count, int64_t cap, int shift, const uint32_t *__restrict__ offsets,
+    const uint32_t *__restrict__ digit_total) {
   constexpr int W = kSortThreads / 32;
   __shared__ uint32_t s_whist[W][256];
   __shared__ uint32_t s_base[256];
@@ -99,7 +113,19 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
   const uint32_t count = item_count(d_count, host_count, cap);
   uint32_t lo, hi;
   block_chunk(count, gridDim.x, blockIdx.x, lo, hi);
-  if (threadIdx.x < 256) s_base[threadIdx.x] = offsets[threadIdx.x * gridDim.x + blockIdx.x];
+  // exclusive prefix of the digit totals, plus this block's offset inside each digit
+  if (threadIdx.x < 256) s_prefix[threadIdx.x] = digit_total[threadIdx.x];
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {
+    uint32_t add = 0;
+    if (threadIdx.x < 256 && threadIdx.x >= off) add = s_prefix[threadIdx.x - off];
+    __syncthreads();
+    if (threadIdx.x < 256) s_prefix[threadIdx.x] += add;
+    __syncthreads();
+  }
+  if (threadIdx.x < 256)
+    s_base[threadIdx.x] = s_prefix[threadIdx.x] - digit_total[threadIdx.x] +
+                          offsets[threadIdx.x * gridDim.x + blockIdx.x];
   __syncthreads();
   for (uint32_t tile = lo; tile < hi; tile += kSortTile) {
     for (int d = lane; d < 256; d += 32) s_whist[warp][d] = 0;
@@ -171,16 +197,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
 // when the number of passes is even, in (k1, v1) otherwise.
 static fgs_status radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int64_t *d_count,
                              int64_t host_count, int64_t cap, int bits, int nblocks, uint32_t *counts,
-                             cudaStream_t st) {
+                             uint32_t *digit_total, cudaStream_t st) {
   const int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
     uint32_t *ki = (p & 1) ? k1 : k0, *vi = (p & 1) ? v1 : v0;
     uint32_t *ko = (p & 1) ? k0 : k1, *vo = (p & 1) ? v0 : v1;
     k_radix_upsweep<<<nblocks, kSortThreads, 0, st>>>(ki, d_count, host_count, cap, shift, counts);
-    k_scan_small<<<1, kScanThreads, 0, st>>>(counts, 256 * nblocks);
+    k_digit_scan<<<256, kScanThreads, 0, st>>>(counts, nblocks, digit_total);
     k_radix_downsweep<<<nblocks, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_count, host_count, cap, shift,
-                                                        counts);
+                                                        counts, digit_total);
     count_launch(3);
   }
   FGS_CHECK_LAUNCH("radix_sort");
@@ -338,12 +364,14 @@ __global__ void __launch_bounds__(kScanBlock) k_emit(const uint32_t *__restrict_
 
 __global__ void k_tile_ranges(const uint32_t *__restrict__ tile_keys, const int64_t *d_sort_count,
                               int64_t cap, int2 *__restrict__ ranges) {
-  const int64_t P = *d_sort_count;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P && k < cap;
-       k += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t P = min(*d_sort_count, cap);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += stride) {
     const uint32_t t = tile_keys[k];
-    if (k == 0 || tile_keys[k - 1] != t) ranges[t].x = (int)k;
-    if (k == P - 1 || tile_keys[k + 1] != t) ranges[t].y = (int)(k + 1);
+    const uint32_t prev = k > 0 ? tile_keys[k - 1] : 0xFFFFFFFFu;
+    const uint32_t next = k + 1 < P ? tile_keys[k + 1] : 0xFFFFFFFFu;
+    if (prev != t) ranges[t].x = (int)k;
+    if (next != t) ranges[t].y = (int)(k + 1);
   }
 }
 
@@ -353,6 +381,7 @@ struct BinWs {
   uint32_t *bsum;                   // ceil(R / 1024)
   uint32_t *tk1, *tv1;              // tile sort ping-pong, pair_capacity each
   uint32_t *counts;                 // 256 * kSortMaxBlocks
+  uint32_t *digit_total;            // 256
   int64_t *sort_count;              // 1
   size_t bytes;
 };
@@ -376,6 +405,7 @@ static BinWs carve(void *base, int64_t R, int64_t cap) {
   w.tk1 = (uint32_t *)take(c4);
   w.tv1 = (uint32_t *)take(c4);
   w.counts = (uint32_t *)take((size_t)256 * kSortMaxBlocks * 4);
+  w.digit_total = (uint32_t *)take(256 * 4);
   w.sort_count = (int64_t *)take(8);
   w.bytes = off;
   return w;
@@ -429,7 +459,7 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
     count_launch();
   }
   // depth sort: 4 passes, result back in (dk0, dv0)
-  fgs_status s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, nullptr, R, R, 32, sort_blocks(R), w.counts, st);
+  fgs_status s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, nullptr, R, R, 32, sort_blocks(R), w.counts, w.digit_total, st);
   if (s != FGS_OK) return s;
   const int64_t nb = (R + kScanBlock - 1) / kScanBlock;
   k_counts_blocksum<<<(unsigned)nb, kScanBlock, 0, st>>>(w.dk0, w.dv0, rect, R, w.cnt, w.bsum);
@@ -444,9 +474,9 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   count_launch(3);
   FGS_CHECK_LAUNCH("fgs_bin_sort emit");
   s = radix_sort(ek, ev, (passes & 1) ? tile_keys : w.tk1, (passes & 1) ? reinterpret_cast<uint32_t *>(ids) : w.tv1,
-                 w.sort_count, 0, pair_capacity, tbits, sort_blocks(pair_capacity), w.counts, st);
+                 w.sort_count, 0, pair_capacity, tbits, sort_blocks(pair_capacity), w.counts, w.digit_total, st);
   if (s != FGS_OK) return s;
-  k_tile_ranges<<<4 * num_sms(), 256, 0, st>>>(tile_keys, w.sort_count, pair_capacity,
+  k_tile_ranges<<<32 * num_sms(), 256, 0, st>>>(tile_keys, w.sort_count, pair_capacity,
                                                reinterpret_cast<int2 *>(tile_ranges));
   count_launch();
   FGS_CHECK_LAUNCH("fgs_bin_sort ranges");

@@ -171,7 +171,9 @@ def test_autograd_function_uses_the_adjoint(cuda_device):
     m2.render()
     m2.backward(w, torch.zeros_like(m2.frame.depth))
     torch.cuda.synchronize()
-    assert torch.allclose(auto, m2.grads.buf, rtol=1e-5, atol=1e-9)
+    # float atomics accumulate in a different order in the two runs
+    bad, _ = grad_close(auto.cpu().numpy(), m2.grads.buf.cpu().numpy(), rel=1e-4)
+    assert not bad.any()
 
 
 def test_loss_matches_oracle(cuda_device):
