@@ -214,6 +214,31 @@ fgs_status fgs_loss(const fgs_camera *cams, int32_t n_views, const float *color,
                     float *d_loss, void *ws, size_t ws_bytes, void *stream);
 size_t fgs_loss_workspace_size(const fgs_camera *cams, int32_t n_views);
 
+/* fgs_loss_noalloc -- fgs_loss without a workspace argument, for callers that
+ * may not allocate device memory: a host that owns every device byte through
+ * its own pool, or a real-time loop where cudaMalloc's latency and implicit
+ * synchronisation are not acceptable.  The paper has no counterpart; this is a
+ * deployment convenience.
+ *   Same arguments, layouts, outputs and device behaviour as fgs_loss (the loss
+ *   value is ADDED to *d_loss).  The per-tile partial sums go to a scratch array
+ *   compiled into the library: FGS_LOSS_NOALLOC_MAX_TILES doubles (512 KiB),
+ *   i.e. at most that many 16x16 loss tiles over all views (sum over views of
+ *   ceil(W/16) * ceil(H/16); 65536 tiles = 16.7 M pixels, 20 views of 1200x680).
+ *   Larger view sets return FGS_ERR_CAPACITY before anything is launched.
+ *   Every device that loads the library holds the array until the process
+ *   exits.  The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) and caches it, so make that first call before any
+ *   stream capture on that device.  The call allocates nothing.
+ *   All calls share the one array: calls whose kernels can overlap on the GPU
+ *   (different streams without ordering) race on it and give wrong sums.
+ *   Nothing in the array needs clearing: every call writes each partial it
+ *   reads. */
+#define FGS_LOSS_NOALLOC_MAX_TILES 65536
+fgs_status fgs_loss_noalloc(const fgs_camera *cams, int32_t n_views, const float *color,
+                            const float *depth, const float *color_gt, const float *depth_gt,
+                            const fgs_loss_params *params, float *dL_dcolor, float *dL_ddepth,
+                            float *d_loss, void *stream);
+
 /* fgs_scale_reg -- scale regulariser eq15 (per-Gaussian mean of the first two
  * linear scales, epsilon = 0) times `weight`; ADDS its gradient to
  * grads->log_scales and its value to *d_loss.  ws: fgs_scale_reg_workspace_size. */

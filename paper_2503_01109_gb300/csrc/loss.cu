@@ -9,6 +9,7 @@
 // HBM.  Loss values are reduced per CTA into a workspace and summed in a fixed
 // order by one CTA, so the value is reproducible bit for bit.
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -394,5 +395,84 @@ extern "C" fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads
   k_adam<<<dim3(bx, 14), 256, 0, st>>>(P, params->n, params->d_n, hp->beta1, hp->beta2, hp->eps, hp->step, d_step);
   count_launch();
   FGS_CHECK_LAUNCH("fgs_adam");
+  return FGS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Allocation-free variant of fgs_loss.  Its per-CTA partial sums live in a
+// file-scope device array instead of caller workspace, for callers that may not
+// allocate device memory.  Host code must not pass the array's name to a kernel:
+// on the host that name is only a stand-in, so the device address is looked up
+// with cudaGetSymbolAddress once per device and cached.
+namespace fgs {
+
+static __device__ __align__(256) double g_loss_scratch[FGS_LOSS_NOALLOC_MAX_TILES];
+
+static std::mutex g_loss_scratch_mu;
+static double *g_loss_scratch_dev[64] = {nullptr};
+
+static fgs_status loss_scratch_address(double **out) {
+  int dev = -1;
+  FGS_CUDA(cudaGetDevice(&dev), "fgs_loss_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= 64) {
+    set_error("fgs_loss_noalloc: device ordinal %d out of range", dev);
+    return FGS_ERR_INVALID_ARGUMENT;
+  }
+  std::lock_guard<std::mutex> lock(g_loss_scratch_mu);
+  if (g_loss_scratch_dev[dev] == nullptr) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_loss_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      set_error("fgs_loss_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return FGS_ERR_CUDA;
+    }
+    g_loss_scratch_dev[dev] = static_cast<double *>(p);
+  }
+  *out = g_loss_scratch_dev[dev];
+  return FGS_OK;
+}
+
+}  // namespace fgs
+
+extern "C" fgs_status fgs_loss_noalloc(const fgs_camera *cams, int32_t n_views, const float *color,
+                                       const float *depth, const float *color_gt, const float *depth_gt,
+                                       const fgs_loss_params *params, float *dL_dcolor, float *dL_ddepth,
+                                       float *d_loss, void *stream) {
+  FGS_CHECK_ARG(color && depth && color_gt && depth_gt && params && dL_dcolor && dL_ddepth && d_loss,
+                "fgs_loss_noalloc: NULL argument");
+  LossArgs a;
+  int blocks = 0;
+  if (!loss_views(cams, n_views, &a.lv, &blocks)) return FGS_ERR_INVALID_ARGUMENT;
+  if (blocks > FGS_LOSS_NOALLOC_MAX_TILES) {
+    set_error("fgs_loss_noalloc: %d loss tiles (16x16 px) exceed the built-in scratch of %d tiles; "
+              "use fgs_loss with a workspace",
+              blocks, FGS_LOSS_NOALLOC_MAX_TILES);
+    return FGS_ERR_CAPACITY;
+  }
+  double *scratch = nullptr;
+  const fgs_status s = loss_scratch_address(&scratch);
+  if (s != FGS_OK) return s;
+  a.color = color;
+  a.depth = depth;
+  a.color_gt = color_gt;
+  a.depth_gt = depth_gt;
+  a.w_c = params->w_l1_color;
+  a.w_d = params->w_l1_depth;
+  a.w_s = params->w_ssim;
+  a.dC = dL_dcolor;
+  a.dD = dL_ddepth;
+  a.partials = scratch;
+  double g[11], gs = 0.0;
+  for (int i = 0; i < 11; ++i) {
+    g[i] = std::exp(-(double)((i - 5) * (i - 5)) / (2.0 * 1.5 * 1.5));
+    gs += g[i];
+  }
+  for (int i = 0; i < 11; ++i) a.g[i] = (float)(g[i] / gs);
+  const size_t smem = sizeof(float) * (2 * kLIn * kLIn + 5 * kLIn * kLMid + 5 * kLMid * kLMid);
+  cudaStream_t st = as_stream(stream);
+  k_loss<<<blocks, kLThreads, smem, st>>>(a);
+  k_reduce_partials<<<1, 256, 0, st>>>(scratch, blocks, d_loss);
+  count_launch(2);
+  FGS_CHECK_LAUNCH("fgs_loss_noalloc");
   return FGS_OK;
 }

@@ -113,6 +113,8 @@ _OPTIONAL = {
                          c_void_p], c_int32),
     "fgs_prior_train_workspace_size": ([c_int64], c_size_t),
     "fgs_prior_num_params": ([], c_int64),
+    "fgs_loss_noalloc": ([c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                          c_void_p, c_void_p], c_int32),
 }
 
 
@@ -357,6 +359,14 @@ def fgs_loss(cams: list, color, depth, color_gt, depth_gt, w_c, w_d, w_s, dC, dD
     _check(lib().fgs_loss(camera_array(cams), len(cams), _ptr(color), _ptr(depth), _ptr(color_gt), _ptr(depth_gt),
                           ctypes.byref(p), _ptr(dC), _ptr(dD), _ptr(loss_acc), _ptr(ws),
                           ws.numel() * ws.element_size(), _stream()), "fgs_loss")
+
+
+def fgs_loss_noalloc(cams: list, color, depth, color_gt, depth_gt, w_c, w_d, w_s, dC, dD, loss_acc):
+    """fgs_loss with its scratch in a fixed array inside the library (no workspace)."""
+    p = LossParams(float(w_c), float(w_d), float(w_s))
+    _check(lib().fgs_loss_noalloc(camera_array(cams), len(cams), _ptr(color), _ptr(depth), _ptr(color_gt),
+                                  _ptr(depth_gt), ctypes.byref(p), _ptr(dC), _ptr(dD), _ptr(loss_acc), _stream()),
+           "fgs_loss_noalloc")
 
 
 def fgs_scale_reg_workspace_size(n: int) -> int:
