@@ -265,7 +265,8 @@ fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads, fgs_gauss
  *   gray = 0.299 R + 0.587 G + 0.114 B of rgb_gt; F = DFT2(gray) (eq2);
  *   centred (eq3, read as the standard spectrum shift); high-pass H = 1 -
  *   exp(-D^2 / (2 D0^2)) with D in Nyquist units (eq5, eq7); inverse DFT (eq8);
- *   E = |I_h|.  256-bin histogram of E / max E, triangle threshold t;
+ *   E = |I_h|.  256-bin histogram of E / max E, triangle threshold t (a frame
+ *   whose max E is at most 1e-5 of its peak |gray| has no high-frequency region);
  *   M_h = bin > t, M_l = not M_h.  Missing region (eq9):
  *   M_m = (A < tau_alpha) | (D/A - D_gt > tau_depth_rel D_gt) | (sum|C - C_gt| > 3 tau_color),
  *   all pixels when r_alpha is NULL.  Seeds (eq10): M_h & M_m on the m-grid and
@@ -278,7 +279,8 @@ fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads, fgs_gauss
  * Appends at g->d_n ? *g->d_n : g->n and increments *g->d_n when set.
  * out: mask (uint8 per pixel: bit0 M_h, bit1 M_l, bit2 M_m, bit3 seeded),
  *   energy (E, nullable), *d_num_new, *d_threshold (bin t), appended Gaussians.
- * ws: fgs_fourier_seed_workspace_size(W, H). */
+ * ws: fgs_fourier_seed_workspace_size(W, H, max_new) bytes, 256-byte aligned.
+ * err: UNSUPPORTED when W or H has a prime factor above 17 (the FFT's radices). */
 typedef struct {
   float d0;          /* high-pass cutoff in Nyquist units (0.25)       */
   int32_t m, n;      /* sampling spacing in high / low frequency areas */
@@ -305,7 +307,7 @@ fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_gt, const fl
                             const fgs_mlp *prior, uint8_t *mask, float *energy,
                             fgs_gaussians *g, int32_t *d_num_new, int32_t *d_threshold,
                             void *ws, size_t ws_bytes, int32_t *d_status, void *stream);
-size_t fgs_fourier_seed_workspace_size(int32_t width, int32_t height);
+size_t fgs_fourier_seed_workspace_size(int32_t width, int32_t height, int32_t max_new);
 
 /* ---------------------------------------------------------------------------------
  * Learned seeding prior (not in the paper; an extension).  Features per seed
@@ -315,7 +317,7 @@ size_t fgs_fourier_seed_workspace_size(int32_t width, int32_t height);
  * GELU (erf form), BF16 operands, FP32 accumulation, activations rounded to BF16
  * before each product.  Output: log-scale x, y, z and opacity logit.
  *
- * fgs_prior_features: gray [H][W] (or NULL and rgb [3][H][W]), depth [H][W],
+ * fgs_prior_features: rgb [3][H][W] (gray = BT.601 luma), depth [H][W],
  *   seed_xy [n][2] int32 -> features [n][272] BF16.
  * fgs_prior_infer: features -> out [n][4] float. */
 #define FGS_PRIOR_IN 272
@@ -330,7 +332,10 @@ fgs_status fgs_prior_infer(const fgs_mlp *mlp, const uint16_t *features, int64_t
 /* fgs_prior_train -- one Adam step of the prior on a batch: mean squared error
  * over the batch's n x 4 outputs against `targets`, gradients through the MLP,
  * Adam on the FP32 master weights, BF16 copies refreshed.  *d_loss receives the
- * batch loss (before the step). */
+ * batch loss (before the step), ADDED.  After the call the first
+ * fgs_prior_num_params() floats of ws hold the batch gradient in packed order
+ * (w1 [128][272], b1, w2 [128][128], b2, w3 [8][128], b3 [8]); the Adam moments
+ * in master->m / master->v use the same order. */
 typedef struct {
   float *w1, *b1, *w2, *b2, *w3, *b3; /* FP32 masters, same shapes as fgs_mlp */
   float *m;                           /* Adam first moments, all params packed */

@@ -12,7 +12,9 @@ Follows the paper's steps in its order and notation, with plain numpy:
    from the centre in Nyquist units (D = 1 at the Nyquist frequency on each axis);
 5. eq8, the inverse DFT of the un-centred filtered spectrum, divided by H W (the
    printed eq8 sums over x, y with swapped limits; read as the standard inverse);
-6. E = |I_h| and its 256-bin histogram over [0, max E];
+6. E = |I_h| and its 256-bin histogram over [0, max E] (a frame whose max E is
+   at most 1e-5 of its peak gray has no high-frequency region: E is 0 in exact
+   arithmetic and only rounding noise otherwise);
 7. the triangle threshold between the histogram's peak and its far end;
 8. M_h = bin > t, M_l = not M_h; eq9's missing region; eq10's intersections;
    equidistant sampling with spacings m < n; eq11's radius r = alpha d / f.
@@ -91,21 +93,28 @@ def high_frequency_energy(rgb: np.ndarray, d0: float = 0.25) -> np.ndarray:
     return np.abs(Ih)
 
 
-def bins_f32(E32: np.ndarray) -> np.ndarray:
+NOISE_FLOOR = 1e-5   # max E at or below this fraction of the peak gray is rounding noise
+
+
+def bins_f32(E32: np.ndarray, gray_max32=None) -> np.ndarray:
     """Histogram bin of each pixel, decided in float32:
-    bin = min(255, floor((256 * e) / max E)); all zero when max E is 0."""
+    bin = min(255, floor((256 * e) / max E)); all zero when max E is not above
+    NOISE_FLOOR * max |gray| (a frame without high-frequency content: in exact
+    arithmetic E is then 0, any float rounding leaves only noise)."""
     E32 = np.asarray(E32, np.float32)
     mx = np.float32(E32.max()) if E32.size else np.float32(0)
-    if not mx > 0:
+    floor = np.float32(0) if gray_max32 is None else np.float32(NOISE_FLOOR) * np.float32(gray_max32)
+    if not mx > floor:
         return np.zeros(E32.shape, np.int32)
     q = (np.float32(256.0) * E32) / mx          # both float32, IEEE round to nearest
     return np.minimum(np.floor(q), 255).astype(np.int32)
 
 
-def bins_f64(E: np.ndarray) -> np.ndarray:
+def bins_f64(E: np.ndarray, gray_max=None) -> np.ndarray:
     E = np.asarray(E, np.float64)
     mx = E.max()
-    if not mx > 0:
+    floor = 0.0 if gray_max is None else NOISE_FLOOR * gray_max
+    if not mx > floor:
         return np.zeros(E.shape, np.int32)
     return np.minimum(np.floor(256.0 * E / mx), 255).astype(np.int32)
 
@@ -210,7 +219,13 @@ def seed_frame(rgb_gt, depth_gt, cam, r_color=None, r_depth=None, r_alpha=None, 
     """Sec. III-A end to end for one frame.  With energy32 given (teacher
     forcing), the histogram, threshold and masks start from that float32 E."""
     E = high_frequency_energy(rgb_gt, d0)
-    bins = bins_f32(energy32) if energy32 is not None else bins_f64(E)
+    gmax = float(np.abs(gray(rgb_gt)).max())
+    if energy32 is not None:
+        r = np.asarray(rgb_gt, np.float32)
+        g32 = (np.float32(0.299) * r[0] + np.float32(0.587) * r[1] + np.float32(0.114) * r[2]).astype(np.float32)
+        bins = bins_f32(energy32, np.abs(g32).max())
+    else:
+        bins = bins_f64(E, gmax)
     hist = histogram(bins)
     t = triangle_threshold(hist)
     Mh = bins > t

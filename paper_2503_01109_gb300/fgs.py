@@ -106,7 +106,7 @@ _SIGS = {
 _OPTIONAL = {
     "fgs_fourier_seed": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                           c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
-    "fgs_fourier_seed_workspace_size": ([c_int32, c_int32], c_size_t),
+    "fgs_fourier_seed_workspace_size": ([c_int32, c_int32, c_int32], c_size_t),
     "fgs_prior_features": ([c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p], c_int32),
     "fgs_prior_infer": ([c_void_p, c_void_p, c_int64, c_void_p, c_void_p], c_int32),
     "fgs_prior_train": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_size_t,
@@ -400,3 +400,51 @@ def fgs_memset_async(t: torch.Tensor, value: int = 0):
 def ws_tensor(nbytes: int, device="cuda") -> torch.Tensor:
     """Workspace of at least nbytes, 256-byte aligned (torch allocations are)."""
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# ----------------------------------------------------------------------------------
+# Fourier seeding and the learned prior
+
+def seed_params(d0=0.25, m=2, n=8, alpha_h=1.0, alpha_l=4.0, tau_alpha=0.5, tau_depth_rel=0.05, tau_color=0.1,
+                max_new=50000, init_logit=0.0, prior_max_dev=math.log(4.0)) -> SeedParams:
+    """Defaults are the readings of Sec. III-A's unstated constants (see the header)."""
+    return SeedParams(float(d0), int(m), int(n), float(alpha_h), float(alpha_l), float(tau_alpha),
+                      float(tau_depth_rel), float(tau_color), int(max_new), float(init_logit), float(prior_max_dev))
+
+
+def fgs_fourier_seed_workspace_size(width: int, height: int, max_new: int) -> int:
+    return int(lib().fgs_fourier_seed_workspace_size(int(width), int(height), int(max_new)))
+
+
+def fgs_fourier_seed(rgb_gt, depth_gt, r_color, r_depth, r_alpha, cam: dict, params: SeedParams, prior, mask,
+                     energy, g: GaussianMap, num_new, threshold, ws, status=None, use_device_count: bool = True):
+    gs = g.struct(use_device_count)
+    cs = camera_struct(cam)
+    _check(lib().fgs_fourier_seed(_ptr(rgb_gt), _ptr(depth_gt), _ptr(r_color), _ptr(r_depth), _ptr(r_alpha),
+                                  ctypes.byref(cs), ctypes.byref(params),
+                                  None if prior is None else ctypes.byref(prior), _ptr(mask), _ptr(energy),
+                                  ctypes.byref(gs), _ptr(num_new), _ptr(threshold), _ptr(ws),
+                                  ws.numel() * ws.element_size(), _ptr(status), _stream()), "fgs_fourier_seed")
+
+
+def fgs_prior_features(rgb, depth, width: int, height: int, seed_xy, n: int, features):
+    _check(lib().fgs_prior_features(_ptr(rgb), _ptr(depth), int(width), int(height), _ptr(seed_xy), int(n),
+                                    _ptr(features), _stream()), "fgs_prior_features")
+
+
+def fgs_prior_infer(mlp: MLP, features, n: int, out):
+    _check(lib().fgs_prior_infer(ctypes.byref(mlp), _ptr(features), int(n), _ptr(out), _stream()), "fgs_prior_infer")
+
+
+def fgs_prior_train(mlp: MLP, master: MLPMaster, features, targets, n: int, hp: TrainParams, loss_acc, ws):
+    _check(lib().fgs_prior_train(ctypes.byref(mlp), ctypes.byref(master), _ptr(features), _ptr(targets), int(n),
+                                 ctypes.byref(hp), _ptr(loss_acc), _ptr(ws), ws.numel() * ws.element_size(),
+                                 _stream()), "fgs_prior_train")
+
+
+def fgs_prior_train_workspace_size(n: int) -> int:
+    return int(lib().fgs_prior_train_workspace_size(int(n)))
+
+
+def fgs_prior_num_params() -> int:
+    return int(lib().fgs_prior_num_params())

@@ -1,0 +1,41 @@
+"""Fourier seeding of a frame into a map (Sec. III-A, eq2-eq11) on the device.
+
+:class:`Seeder` owns the workspace, mask and counters for one image size and
+calls ``fgs_fourier_seed`` with the map's render at the frame's pose (for the
+missing-region check of eq9); new Gaussians are appended at the map's device
+count, so no host synchronisation is needed.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import fgs
+
+
+class Seeder:
+    def __init__(self, mapper, params: fgs.SeedParams | None = None, prior=None):
+        if not hasattr(fgs.lib(), "fgs_fourier_seed"):
+            raise AttributeError("fgs_fourier_seed missing from libfgs.so")
+        cam = mapper.cams[0]
+        W, H = int(cam["width"]), int(cam["height"])
+        dev = mapper.g.buf.device
+        self.mapper = mapper
+        self.params = params or fgs.seed_params()
+        self.prior = prior
+        self.ws = fgs.ws_tensor(fgs.fgs_fourier_seed_workspace_size(W, H, self.params.max_new), dev)
+        self.mask = torch.zeros(H * W, dtype=torch.uint8, device=dev)
+        self.energy = torch.zeros(H * W, dtype=torch.float32, device=dev)
+        self.num_new = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.threshold = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def seed_frame(self, color_gt, depth_gt, cam: dict, render_first: bool = True, first_frame: bool = False):
+        """Render the map at `cam` (eq1 colour, depth, opacity), then seed."""
+        m = self.mapper
+        m.set_cameras([cam])
+        if render_first and not first_frame:
+            m.render()
+        f = m.frame
+        mlp = None if self.prior is None else self.prior.mlp_struct()
+        fgs.fgs_fourier_seed(color_gt, depth_gt, None if first_frame else f.color, None if first_frame else f.depth,
+                             None if first_frame else f.alpha, cam, self.params, mlp, self.mask, self.energy, m.g,
+                             self.num_new, self.threshold, self.ws, m.status, use_device_count=True)

@@ -176,3 +176,42 @@ def subset(scene: dict, idx) -> dict:
 
 def concat(a: dict, b: dict) -> dict:
     return {k: np.ascontiguousarray(np.concatenate([a[k], b[k]], axis=-1)) for k in a}
+
+
+def textured_frame(width: int, height: int, seed: int) -> dict:
+    """An RGB-D frame drawn directly (not rendered): flat patches and striped or
+    checkered patches of 2-8 px period on a 16-px grid, plus a smooth depth map in
+    [1.5, 4] m with a few invalid (0) pixels.  Returns rgb [3][H][W], depth [H][W]."""
+    rng = np.random.default_rng(seed)
+    ys, xs = np.mgrid[0:height, 0:width].astype(np.float64)
+    rgb = np.zeros((3, height, width))
+    cell = 16
+    for cy in range(0, height, cell):
+        for cx in range(0, width, cell):
+            sl = (slice(cy, cy + cell), slice(cx, cx + cell))
+            base = rng.uniform(0.1, 0.9, 3)
+            if rng.uniform() < 0.5:
+                alt = rng.uniform(0.1, 0.9, 3)
+                period = rng.uniform(2, 8)
+                ang = rng.uniform(0, math.pi)
+                t = (np.cos(ang) * xs[sl] + np.sin(ang) * ys[sl]) / period
+                on = (np.floor(t) % 2 == 0)
+                for c in range(3):
+                    rgb[c][sl] = np.where(on, alt[c], base[c])
+            else:
+                for c in range(3):
+                    rgb[c][sl] = base[c]
+    a, b, c0 = rng.uniform(-0.5, 0.5, 3)
+    depth = 2.5 + a * (xs / width - 0.5) + b * (ys / height - 0.5) + 0.3 * np.sin(xs / 37.0 + c0) * np.cos(ys / 23.0)
+    depth[rng.uniform(0, 1, depth.shape) < 0.01] = 0.0
+    return {"rgb": rgb.astype(np.float32), "depth": depth.astype(np.float32)}
+
+
+def fake_render(width: int, height: int, seed: int) -> dict:
+    """Stand-in render outputs for the missing-region check: colour, unnormalised
+    depth and opacity drawn at random (opacity spread around the 0.5 threshold)."""
+    rng = np.random.default_rng(seed)
+    A = np.clip(rng.uniform(-0.2, 1.2, (height, width)), 0.0, 1.0)
+    D = rng.uniform(1.5, 4.0, (height, width)) * A
+    C = rng.uniform(0, 1, (3, height, width))
+    return {"color": C.astype(np.float32), "depth": D.astype(np.float32), "alpha": A.astype(np.float32)}

@@ -1,0 +1,92 @@
+"""GPU parity of the learned prior: features, tensor-core MLP forward and the
+training step's gradients against the oracle MLP with BF16 emulation."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import prior as op
+from paper_2503_01109_gb300 import fgs, prior as gp, synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+def _frame_and_seeds(W=200, H=120, n=300, seed=0):
+    fr = syn.textured_frame(W, H, seed)
+    rng = np.random.default_rng(seed)
+    xy = np.stack([rng.integers(0, W, n), rng.integers(0, H, n)], 1).astype(np.int32)
+    xy[:4] = [[0, 0], [W - 1, H - 1], [3, H - 2], [W - 5, 1]]       # clamped patches at the corners
+    return fr, xy
+
+
+def _gpu_features(fr, xy):
+    H, W = fr["depth"].shape
+    rgb = torch.as_tensor(fr["rgb"]).reshape(-1).cuda()
+    depth = torch.as_tensor(fr["depth"]).reshape(-1).cuda()
+    return gp.features(rgb, depth, W, H, torch.as_tensor(xy).cuda())
+
+
+def test_features_match_oracle(cuda_device):
+    fr, xy = _frame_and_seeds()
+    f = _gpu_features(fr, xy)
+    torch.cuda.synchronize()
+    got = op.from_bits(f.cpu().numpy().view(np.uint16))
+    gray = 0.299 * fr["rgb"][0].astype(np.float64) + 0.587 * fr["rgb"][1] + 0.114 * fr["rgb"][2]
+    ref = op.patch_features(gray, fr["depth"].astype(np.float64), xy)
+    # both sides round to BF16; a value within float32 reach of a rounding tie may land one BF16 step
+    # apart, and bins that are exactly 0 in FP64 keep float32 DFT noise (|F| <= 256 * 1e-7)
+    step = np.abs(ref) * 2.0 ** -7 * 1.01 + 1e-4
+    assert np.all(np.abs(got - ref) <= step)
+    big = np.abs(ref) > 0.25          # bins well above the float32 DFT noise round identically
+    assert (got[big] == ref[big]).mean() > 0.99
+
+
+def test_mlp_forward_matches_oracle(cuda_device):
+    fr, xy = _frame_and_seeds(n=1000, seed=1)
+    f = _gpu_features(fr, xy)
+    params = gp.init_params(3)
+    mlp = gp.PriorMLP(params)
+    y = mlp.infer(f)
+    torch.cuda.synchronize()
+    x = op.from_bits(f.cpu().numpy().view(np.uint16)).astype(np.float64)
+    ref = op.forward(params, x)["y"]
+    assert np.abs(y.cpu().numpy() - ref).max() <= 2e-3 * (1 + np.abs(ref).max())
+    assert np.median(np.abs(y.cpu().numpy() - ref)) < 1e-4
+
+
+def test_training_gradients_match_oracle(cuda_device):
+    fr, xy = _frame_and_seeds(n=777, seed=2)
+    f = _gpu_features(fr, xy)
+    rng = np.random.default_rng(5)
+    t = rng.normal(0, 1, (777, 4)).astype(np.float32)
+    params = gp.init_params(4)
+    mlp = gp.PriorMLP(params)
+    loss = mlp.train_step(f, torch.as_tensor(t).cuda(), lr=1e-3)
+    torch.cuda.synchronize()
+    grad = mlp.ws[: 4 * fgs.fgs_prior_num_params()].view(torch.float32).cpu().numpy()
+    x = op.from_bits(f.cpu().numpy().view(np.uint16)).astype(np.float64)
+    L, g, _ = op.loss_and_grads(params, x, t)
+    assert float(loss.item()) == pytest.approx(L, rel=1e-3)
+    off = 0
+    for k in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        size = int(np.prod(gp.SHAPES[k]))
+        got = grad[off:off + size].reshape(gp.SHAPES[k])
+        off += size
+        ref = g[k]
+        floor = 1e-3 * np.abs(ref).max()
+        bad = np.abs(got - ref) > 2e-2 * np.maximum(np.abs(ref), floor)
+        assert bad.mean() < 0.01, (k, bad.sum())
+
+
+def test_training_reduces_the_loss(cuda_device):
+    """A regression target that depends on the features: 200 Adam steps lower the MSE."""
+    fr, xy = _frame_and_seeds(W=320, H=240, n=4096, seed=3)
+    f = _gpu_features(fr, xy)
+    x = op.from_bits(f.cpu().numpy().view(np.uint16)).astype(np.float64)
+    t = np.stack([-4.0 - 0.2 * x[:, 1], -4.0 + 0.1 * x[:, 17], -5.0 + 0.05 * x[:, 0], 2.0 - 0.3 * x[:, 256]], 1)
+    tt = torch.as_tensor(t.astype(np.float32)).cuda()
+    mlp = gp.PriorMLP(gp.init_params(5))
+    first = float(mlp.train_step(f, tt, lr=3e-3).item())
+    for _ in range(200):
+        last = mlp.train_step(f, tt, lr=3e-3)
+    torch.cuda.synchronize()
+    assert float(last.item()) < 0.2 * first

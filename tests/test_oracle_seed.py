@@ -57,8 +57,14 @@ def test_centre_matches_fftshift():
 def test_constant_frame_has_no_high_frequency_energy():
     """H(centre) = 0 removes the DC term: a constant frame has E = 0 everywhere."""
     rgb = np.full((3, 48, 64), 0.37)
-    assert osd.high_frequency_energy(rgb, 0.25).max() < 1e-12
+    E = osd.high_frequency_energy(rgb, 0.25)
+    assert E.max() < 1e-12
     assert osd.bins_f64(np.zeros((4, 4))).max() == 0
+    # the rounding noise left in E is below the noise floor: no high-frequency bins
+    assert osd.bins_f64(E, 0.37).max() == 0
+    assert osd.bins_f32(E.astype(np.float32), np.float32(0.37)).max() == 0
+    out = osd.seed_frame(rgb, np.ones((48, 64)), syn.pinhole(64, 48, 60.0))
+    assert not (out["mask"] & 1).any() and not out["is_high"].any()
 
 
 @pytest.mark.parametrize("k0,d0", [(5, 0.25), (20, 0.25), (3, 0.1)])
