@@ -310,6 +310,33 @@ fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_gt, const fl
 size_t fgs_fourier_seed_workspace_size(int32_t width, int32_t height, int32_t max_new);
 
 /* ---------------------------------------------------------------------------------
+ * fgs_render_window -- a keyframe window (the co-visible and random keyframes the
+ * map is optimised over, Sec. III-C/D) rendered (eq1), scored (eq16 without eq15)
+ * and differentiated in one persistent cooperative launch: every CTA of a grid
+ * that fits on the GPU at once claims (view, tile) items and loss tiles from atomic
+ * counters in three phases -- blend, loss, adjoint -- separated by grid barriers,
+ * so views of mixed resolution balance across the SMs.
+ *   Inputs as fgs_render_fwd / fgs_loss / fgs_render_bwd for the view set (the
+ *   projection and the sorted lists of all views, from fgs_project and
+ *   fgs_bin_sort).  Outputs: the render (color, depth, alpha, t_final, n_contrib),
+ *   dL/dC and dL/dD, the loss ADDED to *d_loss, and the splat gradients ADDED to
+ *   grad2d [n_views][stride][8] and grads->rgb (the caller zeroes both); chain them
+ *   to the Gaussians with fgs_project_bwd.
+ *   ws: fgs_render_window_workspace_size(cams, n_views) bytes, 256-byte aligned.
+ *   Device errors: every barrier wait is bounded (2 s); a CTA that gives up sets
+ *   FGS_DEV_TIMEOUT and returns, and the outputs are then invalid.
+ *   err: UNSUPPORTED when the kernel cannot be made co-resident. */
+fgs_status fgs_render_window(const fgs_gaussians *g, const fgs_projected *proj,
+                             const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
+                             const int32_t *ids, const int32_t *tile_ranges,
+                             const float *color_gt, const float *depth_gt,
+                             const fgs_loss_params *lp, float *color, float *depth, float *alpha,
+                             float *t_final, int32_t *n_contrib, float *dL_dcolor,
+                             float *dL_ddepth, float *grad2d, fgs_gaussians *grads, float *d_loss,
+                             void *ws, size_t ws_bytes, int32_t *d_status, void *stream);
+size_t fgs_render_window_workspace_size(const fgs_camera *cams, int32_t n_views);
+
+/* ---------------------------------------------------------------------------------
  * Learned seeding prior (not in the paper; an extension).  Features per seed
  * pixel (x, y): the 16x16 grayscale patch with top-left (x-8, y-8), clamped to the
  * image, its 2D DFT magnitude as log(1 + |F|) in natural frequency order (256),

@@ -113,6 +113,10 @@ _OPTIONAL = {
                          c_void_p], c_int32),
     "fgs_prior_train_workspace_size": ([c_int64], c_size_t),
     "fgs_prior_num_params": ([], c_int64),
+    "fgs_render_window": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p, c_void_p,
+                           c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                           c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
+    "fgs_render_window_workspace_size": ([c_void_p, c_int32], c_size_t),
     "fgs_loss_noalloc": ([c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                           c_void_p, c_void_p], c_int32),
 }
@@ -448,3 +452,23 @@ def fgs_prior_train_workspace_size(n: int) -> int:
 
 def fgs_prior_num_params() -> int:
     return int(lib().fgs_prior_num_params())
+
+
+# ----------------------------------------------------------------------------------
+# persistent keyframe window
+
+def fgs_render_window_workspace_size(cams: list) -> int:
+    return int(lib().fgs_render_window_workspace_size(camera_array(cams), len(cams)))
+
+
+def fgs_render_window(g: GaussianMap, proj: Projection, cams: list, til: Tiling, ids, tile_ranges, color_gt, depth_gt,
+                      w_c, w_d, w_s, frame: Frame, dC, dD, grad2d, grads: GaussianMap, loss_acc, ws, status,
+                      use_device_count: bool = True):
+    gs, ps, gr = g.struct(use_device_count), proj.struct(), grads.struct(use_device_count)
+    lp = LossParams(float(w_c), float(w_d), float(w_s))
+    _check(lib().fgs_render_window(ctypes.byref(gs), ctypes.byref(ps), camera_array(cams), len(cams), til, _ptr(ids),
+                                   _ptr(tile_ranges), _ptr(color_gt), _ptr(depth_gt), ctypes.byref(lp),
+                                   _ptr(frame.color), _ptr(frame.depth), _ptr(frame.alpha), _ptr(frame.t_final),
+                                   _ptr(frame.n_contrib), _ptr(dC), _ptr(dD), _ptr(grad2d), ctypes.byref(gr),
+                                   _ptr(loss_acc), _ptr(ws), ws.numel() * ws.element_size(), _ptr(status),
+                                   _stream()), "fgs_render_window")

@@ -1,0 +1,88 @@
+"""Batched keyframe window: all views' forward, loss and adjoint in one persistent
+launch (``fgs_render_window``), plus the tile-size / batch-depth autotuner.
+
+A window iteration is: project every Gaussian into every view, bin and sort all
+views at once, the persistent render-loss-adjoint launch, the projection adjoint,
+eq15, Adam.  It allocates and synchronises nothing, so it is captured into a CUDA
+graph and replayed (:meth:`Window.capture`).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import fgs
+from .mapping import Mapper, PAPER_LOSS, PAPER_REG
+
+TILES = ((8, 8), (16, 16), (16, 32))
+BATCHES = (32, 64, 128, 256)
+
+
+class Window(Mapper):
+    def __init__(self, g: fgs.GaussianMap, cams: list, til: fgs.Tiling | None = None, **kw):
+        kw.setdefault("use_device_count", True)
+        super().__init__(g, cams, til, **kw)
+        self.ws_win = fgs.ws_tensor(fgs.fgs_render_window_workspace_size(self.cams), g.buf.device)
+        self.graph = None
+
+    def iteration(self):
+        fgs.fgs_project(self.g, self.cams, self.til, self.proj, self.status, self.use_dc)
+        n = self.g.capacity if self.use_dc else self.g.n
+        fgs.fgs_bin_sort(self.proj, n, self.cams, self.til, self.ws_bin, self.tile_keys, self.ids, self.ranges,
+                         self.num_pairs, self.status)
+        fgs.fgs_memset_async(self.grads.buf)
+        fgs.fgs_memset_async(self.grad2d)
+        fgs.fgs_memset_async(self.loss_acc)
+        fgs.fgs_render_window(self.g, self.proj, self.cams, self.til, self.ids, self.ranges, self.color_gt,
+                              self.depth_gt, *self.loss_w, self.frame, self.dC, self.dD, self.grad2d, self.grads,
+                              self.loss_acc, self.ws_win, self.status, self.use_dc)
+        fgs.fgs_project_bwd(self.g, self.proj, self.cams, self.grad2d, self.grads, self.use_dc)
+        if self.reg_w != 0.0:
+            fgs.fgs_scale_reg(self.g, self.reg_w, self.grads, self.loss_acc, self.ws_reg, self.use_dc)
+        self.host_step += 1
+        fgs.fgs_adam(self.g, self.grads, self.m, self.v, self.lr, step=self.host_step,
+                     d_step=self.d_step if self.use_dc else None, use_device_count=self.use_dc)
+
+    def capture(self, warmup: int = 2):
+        """Capture one iteration into a CUDA graph (after `warmup` eager ones)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.iteration()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.iteration()
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+
+
+def time_config(g: fgs.GaussianMap, cams, color_gt, depth_gt, tile, batch, reps=5, warmup=2, **kw) -> float:
+    """Milliseconds per window iteration of one (tile, batch) choice, on a copy of
+    the map (the trial's Adam steps do not touch the caller's map)."""
+    trial = g.zeros_like()
+    trial.buf.copy_(g.buf)
+    w = Window(trial, cams, fgs.tiling(tile[0], tile[1], batch), **kw)
+    w.set_target(color_gt, depth_gt)
+    for _ in range(warmup):
+        w.iteration()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        w.iteration()
+    e1.record()
+    torch.cuda.synchronize()
+    w.check_status()
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune(g: fgs.GaussianMap, cams, color_gt, depth_gt, tiles=TILES, batches=BATCHES, reps=5, **kw):
+    """Times every (tile, batch) choice and returns (best tiling, {(tile, batch): ms})."""
+    table = {}
+    for tile in tiles:
+        for batch in batches:
+            table[(tile, batch)] = time_config(g, cams, color_gt, depth_gt, tile, batch, reps=reps, **kw)
+    (tile, batch), _ = min(table.items(), key=lambda kv: kv[1])
+    return fgs.tiling(tile[0], tile[1], batch), table

@@ -1,0 +1,110 @@
+"""The persistent window launch equals the separate forward / loss / adjoint
+calls on a mixed-resolution view set, replays from a CUDA graph, and the
+autotuner returns a valid tiling."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import render as orr
+from paper_2503_01109_gb300 import fgs, synthetic as syn
+from paper_2503_01109_gb300.mapping import Mapper
+from paper_2503_01109_gb300.window import Window, autotune
+
+from gpu_helpers import grad_close
+
+pytestmark = pytest.mark.gpu
+
+
+def views():
+    return [syn.pinhole(70, 45, 60.0), syn.pinhole(64, 48, 55.0, syn.look_pose([0.05, 0.02, 0.1], 0.1, 0.03)),
+            syn.pinhole(33, 20, 30.0, syn.look_pose([-0.1, 0.0, 0.0], -0.1, 0.0))]
+
+
+def targets(cams, seed):
+    fr = [syn.textured_frame(c["width"], c["height"], seed + i) for i, c in enumerate(cams)]
+    return fgs.pack_images(cams, [f["rgb"] for f in fr], [f["depth"] for f in fr])
+
+
+@pytest.mark.parametrize("tile,batch", [((16, 16), 128), ((8, 8), 32), ((16, 32), 256), ((16, 16), 64)])
+def test_window_equals_separate_calls(cuda_device, tile, batch):
+    cams = views()
+    sc = syn.tiny_scene(2500, seed=7)
+    cg, dg = targets(cams, 3)
+    til = fgs.tiling(tile[0], tile[1], batch)
+    # separate calls
+    ref = Mapper(fgs.GaussianMap.from_scene(sc), cams, til, reg_w=0.0, use_device_count=True)
+    ref.set_target(cg, dg)
+    ref.render()
+    fgs.fgs_memset_async(ref.loss_acc)
+    fgs.fgs_loss(cams, ref.frame.color, ref.frame.depth, cg, dg, 0.9, 0.1, 0.1, ref.dC, ref.dD, ref.loss_acc,
+                 ref.ws_loss)
+    ref.backward(ref.dC, ref.dD)
+    # one persistent launch
+    win = Window(fgs.GaussianMap.from_scene(sc), cams, til, reg_w=0.0)
+    win.set_target(cg, dg)
+    fgs.fgs_project(win.g, cams, til, win.proj, win.status, True)
+    fgs.fgs_bin_sort(win.proj, win.g.capacity, cams, til, win.ws_bin, win.tile_keys, win.ids, win.ranges,
+                     win.num_pairs, win.status)
+    for t in (win.grads.buf, win.grad2d, win.loss_acc):
+        fgs.fgs_memset_async(t)
+    fgs.fgs_render_window(win.g, win.proj, cams, til, win.ids, win.ranges, cg, dg, 0.9, 0.1, 0.1, win.frame, win.dC,
+                          win.dD, win.grad2d, win.grads, win.loss_acc, win.ws_win, win.status)
+    fgs.fgs_project_bwd(win.g, win.proj, cams, win.grad2d, win.grads, True)
+    torch.cuda.synchronize()
+    assert int(win.status.item()) == 0 and int(ref.status.item()) == 0
+    for k in ("color", "depth", "alpha", "t_final"):
+        assert torch.equal(getattr(win.frame, k), getattr(ref.frame, k)), k
+    assert torch.equal(win.frame.n_contrib, ref.frame.n_contrib)
+    assert torch.equal(win.dC, ref.dC) and torch.equal(win.dD, ref.dD)
+    assert float(win.loss_acc.item()) == pytest.approx(float(ref.loss_acc.item()), rel=1e-6)
+    bad, _ = grad_close(win.grads.buf.cpu().numpy(), ref.grads.buf.cpu().numpy(), rel=1e-4)
+    assert not bad.any()
+
+
+def test_window_gradients_match_oracle(cuda_device):
+    """End to end against the FP64 oracle on the mixed-resolution window (eq16
+    with SSIM; gradients through the whole chain)."""
+    cams = views()
+    sc = syn.tiny_scene(2000, seed=11)
+    frs = [syn.textured_frame(c["width"], c["height"], 20 + i) for i, c in enumerate(cams)]
+    cg, dg = fgs.pack_images(cams, [f["rgb"] for f in frs], [f["depth"] for f in frs])
+    win = Window(fgs.GaussianMap.from_scene(sc), cams, fgs.tiling(16, 16, 128), reg_w=0.0)
+    win.set_target(cg, dg)
+    win.iteration()
+    torch.cuda.synchronize()
+    st = orr.render_views(sc, cams)
+    dCs, dDs, L = [], [], 0.0
+    for v, f in enumerate(frs):
+        o = st["out"][v]
+        l, dC, dD = orr.loss(o["color"], o["depth"], f["rgb"], f["depth"], 0.9, 0.1, 0.1)
+        L += l
+        dCs.append(dC)
+        dDs.append(dD)
+    assert float(win.loss_acc.item()) == pytest.approx(L, rel=1e-4)
+    ref = orr.grads_to_planes(orr.backward_views(st, cams, dCs, dDs))
+    for key in ("means", "log_scales", "quats", "logits", "rgb"):
+        got = win.grads.plane(key)[:, :2000].cpu().numpy().reshape(ref[key].shape)
+        bad, _ = grad_close(got, ref[key])
+        assert bad.mean() < 0.01, key
+
+
+def test_window_graph_replay_and_autotune(cuda_device):
+    cams = views()
+    sc = syn.tiny_scene(1500, seed=2)
+    cg, dg = targets(cams, 9)
+    best, table = autotune(fgs.GaussianMap.from_scene(sc, capacity=1600), cams, cg, dg, reps=2)
+    assert len(table) == 12 and (best.tile_w, best.tile_h) in [(8, 8), (16, 16), (16, 32)]
+    eager = Window(fgs.GaussianMap.from_scene(sc, capacity=1600), cams, best)
+    graphed = Window(fgs.GaussianMap.from_scene(sc, capacity=1600), cams, best)
+    for w in (eager, graphed):
+        w.set_target(cg, dg)
+    for _ in range(2):
+        eager.iteration()
+    graphed.capture(warmup=2)
+    for _ in range(3):
+        eager.iteration()
+        graphed.replay()
+    torch.cuda.synchronize()
+    assert int(eager.d_step.item()) == int(graphed.d_step.item()) == 5
+    assert int(graphed.status.item()) == 0
+    assert torch.allclose(graphed.g.buf, eager.g.buf, rtol=1e-4, atol=1e-5)
