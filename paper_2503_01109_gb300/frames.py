@@ -124,14 +124,29 @@ def render_targets(gt_scene: dict, cams: list, tile=(16, 16), batch=128, device=
     return colors, depths
 
 
+def render_targets_views(gt_scene: dict, cams: list, tile=(16, 16), batch=128, device="cuda"):
+    """Targets of a view set of possibly different resolutions, concatenated as the
+    library's multi-view images: (colour [3 sum HW], depth [sum HW])."""
+    colors, depths = [], []
+    for cam in cams:
+        c, d = render_targets(gt_scene, [cam], tile, batch, device)
+        colors.append(c[0])
+        depths.append(d[0])
+    return torch.cat(colors), torch.cat(depths)
+
+
 class FramePipeline:
     def __init__(self, scene: dict, cams: list, gt_scene: dict, capacity: int, tile=(16, 16), batch=128,
                  iters_per_frame: int = 3, device="cuda", loss_w=PAPER_LOSS, reg_w=PAPER_REG, seed_params=None,
-                 prior=None):
+                 prior=None, extra_views: list | None = None):
         self.cams = cams
         self.iters = iters_per_frame
         self.kernel_timer = KernelTimer()
         self.colors, self.depths = render_targets(gt_scene, cams, tile, batch, device)
+        # targets of other view sets (e.g. a keyframe window of mixed resolutions)
+        self.extra = None
+        if extra_views:
+            self.extra = render_targets_views(gt_scene, extra_views, tile, batch, device)
         self.g = fgs.GaussianMap.from_scene(scene, capacity, device)
         self.mapper = TimedMapper(self.g, cams[:1], fgs.tiling(*tile, batch), loss_w=loss_w, reg_w=reg_w,
                                   use_device_count=True, timer=self.kernel_timer)
