@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--batch", type=int, default=128)
     p.add_argument("--mapping-only", action="store_true", help="steps of mapping iterations without seeding")
     p.add_argument("--no-window", action="store_true", help="skip the keyframe-window measurement")
+    p.add_argument("--no-convergence", action="store_true", help="skip the iterations-to-PSNR comparison")
     return p.parse_args()
 
 
@@ -194,6 +195,26 @@ def window_measure(pipe, steps: int, warmup: int):
             "autotune_ms": {f"{t[0]}x{t[1]}/{b}": round(v, 3) for (t, b), v in sorted(table.items())}}
 
 
+def convergence_measure(seed_offset: int = 0):
+    """Iterations and wall time to 30 dB from an empty map: plain per-view
+    Fourier-prior loop vs the learned prior vs the learned prior with a 3-keyframe
+    window, on a test trajectory; the prior is trained on a training trajectory of
+    the same ground-truth scene."""
+    from paper_2503_01109_gb300 import synthetic as syn
+    from paper_2503_01109_gb300.convergence import compare
+    from paper_2503_01109_gb300.frames import render_targets
+
+    gt = syn.room_scene(N_GT, seed=2000 + seed_offset, kind="gt")
+    tr = syn.trajectory(30, seed=400 + seed_offset, width=W, height=H, f=F)
+    te = syn.trajectory(10, seed=500 + seed_offset, width=W, height=H, f=F)
+    trc, trd = render_targets(gt, tr)
+    tec, ted = render_targets(gt, te)
+    out = compare(trc, trd, tr, tec, ted, te, capacity=4_000_000, target_psnr=30.0)
+    out["setup"] = ("empty map, 1200x680 frames of a 1M-Gaussian room scene; prior trained on 30 frames "
+                    "(40 iterations each), compared on 10 other frames; cap 100 iterations per frame")
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -258,6 +279,12 @@ def run_ours(args):
     window = None
     if not args.no_window and pipe.extra is not None:
         window = window_measure(pipe, args.steps, args.warmup)
+    conv = None
+    if not args.no_convergence and rank == 0:
+        try:
+            conv = convergence_measure()
+        except Exception as e:  # the comparison is reported, never fatal to the bench line
+            conv = {"error": f"{type(e).__name__}: {e}"}
 
     peaks = load_peaks()
     roof = pipe.roofline(peaks)
@@ -274,6 +301,7 @@ def run_ours(args):
         "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
         "kernels_ms_per_step": pipe.kernel_timer.summary(args.steps),
         "window": window,
+        "iters_to_psnr": conv,
     }
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(pipe)

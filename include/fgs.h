@@ -274,11 +274,13 @@ fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads, fgs_gauss
  *   seeds first then low, row-major, at most max_new.  New Gaussians (eq11):
  *   back-projected from depth_gt, log-scale log(alpha_{h|l} d / f) on all axes
  *   (f = (fx + fy)/2), identity rotation, rgb of the frame, logit init_logit;
- *   when `prior` is not NULL the learned prior replaces scale and logit unless its
- *   log-scale is further than prior_max_dev from the eq11 value (fgs_prior_infer).
+ *   when `prior` is not NULL the learned prior (fgs_prior_infer) sets the logit of
+ *   every high-frequency seed, and its log-scales unless one axis is further than
+ *   prior_max_dev from eq11's; low-frequency seeds keep eq11.
  * Appends at g->d_n ? *g->d_n : g->n and increments *g->d_n when set.
  * out: mask (uint8 per pixel: bit0 M_h, bit1 M_l, bit2 M_m, bit3 seeded),
- *   energy (E, nullable), *d_num_new, *d_threshold (bin t), appended Gaussians.
+ *   energy (E, nullable), *d_num_new, *d_threshold (bin t), appended Gaussians,
+ *   seed_xy (nullable, [max_new][2] int32: pixel of the i-th appended Gaussian).
  * ws: fgs_fourier_seed_workspace_size(W, H, max_new) bytes, 256-byte aligned.
  * err: UNSUPPORTED when W or H has a prime factor above 17 (the FFT's radices). */
 typedef struct {
@@ -306,7 +308,8 @@ fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_gt, const fl
                             const fgs_camera *cam, const fgs_seed_params *params,
                             const fgs_mlp *prior, uint8_t *mask, float *energy,
                             fgs_gaussians *g, int32_t *d_num_new, int32_t *d_threshold,
-                            void *ws, size_t ws_bytes, int32_t *d_status, void *stream);
+                            int32_t *seed_xy, void *ws, size_t ws_bytes, int32_t *d_status,
+                            void *stream);
 size_t fgs_fourier_seed_workspace_size(int32_t width, int32_t height, int32_t max_new);
 
 /* ---------------------------------------------------------------------------------

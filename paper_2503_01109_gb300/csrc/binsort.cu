@@ -8,7 +8,7 @@
 // within a tile the pairs keep their emission order, which is depth then id.
 //
 // The radix sort is LSD, 8-bit digits, reduce-then-scan: an upsweep histogram per
-// block chunk, one exclusive scan of the digit-major counts, and a downsweep that
+// block chunk, a per-digit scan of the blocks' counts, and a downsweep that
 // ranks 2048-item tiles stably with warp match-any, reorders them in shared memory
 // and writes each digit run coalesced.  Item counts may live on the device (the
 // pair count), so the whole binning can be captured in a CUDA graph.
@@ -50,11 +50,19 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
   uint32_t lo, hi;
   block_chunk(count, gridDim.x, blockIdx.x, lo, hi);
   const int lane = threadIdx.x & 31;
-  for (uint32_t i0 = lo; i0 < hi; i0 += kSortThreads) {
-    const uint32_t i = i0 + threadIdx.x;
-    const int d = i < hi ? (int)((keys[i] >> shift) & 255u) : 256;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (d < 256 && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][d], (uint32_t)__popc(peers));
+  // kSortItems keys per thread in flight, warp-striped like the downsweep
+  for (uint32_t tile = lo; tile < hi; tile += kSortTile) {
+    int d[kSortItems];
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const uint32_t i = tile + warp * (32 * kSortItems) + it * 32 + lane;
+      d[it] = i < hi ? (int)((keys[i] >> shift) & 255u) : 256;
+    }
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const uint32_t peers = __match_any_sync(0xffffffffu, d[it]);
+      if (d[it] < 256 && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][d[it]], (uint32_t)__popc(peers));
+    }
   }
   __syncthreads();
   if (threadIdx.x < 256) {

@@ -549,7 +549,8 @@ extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_g
                                        const float *r_depth, const float *r_alpha, const fgs_camera *cam,
                                        const fgs_seed_params *prm, const fgs_mlp *prior, uint8_t *mask,
                                        float *energy, fgs_gaussians *g, int32_t *d_num_new, int32_t *d_threshold,
-                                       void *ws, size_t ws_bytes, int32_t *d_status, void *stream) {
+                                       int32_t *seed_xy, void *ws, size_t ws_bytes, int32_t *d_status,
+                                       void *stream) {
   FGS_CHECK_ARG(rgb_gt && depth_gt && cam && prm && mask && d_num_new && d_threshold,
                 "fgs_fourier_seed: NULL argument");
   FGS_CHECK_ARG(!r_alpha || (r_color && r_depth), "fgs_fourier_seed: r_alpha needs r_color and r_depth");
@@ -617,7 +618,7 @@ extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_g
   a.bsum_hi = w.bsum_hi;
   a.bsum_lo = w.bsum_lo;
   a.base = w.base;
-  a.seed_xy = w.seed_xy;
+  a.seed_xy = seed_xy ? seed_xy : w.seed_xy;
   a.seed_hi = w.seed_hi;
   const int nb = (int)((HW + kSeedBlock - 1) / kSeedBlock);
   k_seed_count<<<nb, kSeedBlock, 0, st>>>(a);
@@ -626,7 +627,7 @@ extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_g
   count_launch(3);
   FGS_CHECK_LAUNCH("fgs_fourier_seed seeds");
   if (prior) {
-    return prior_apply_to_seeds(prior, rgb_gt, depth_gt, W, H, w.seed_xy, w.seed_hi, w.base, prm->max_new,
+    return prior_apply_to_seeds(prior, rgb_gt, depth_gt, W, H, a.seed_xy, w.seed_hi, w.base, prm->max_new,
                                 prm->alpha_h, prm->alpha_l, cam->fx, cam->fy, prm->prior_max_dev, w.prior,
                                 w.prior_bytes, gauss_grads(g), st);
   }

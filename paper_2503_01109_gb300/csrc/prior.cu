@@ -478,26 +478,28 @@ __global__ void k_mlp_adam(fgs_mlp_master ms, const float *__restrict__ grad, fg
   if (fcopy) *fcopy = val;
 }
 
-// Learned prior on freshly written seeds: features, inference, then per seed the
-// eq11 fallback test |pred log-scale - eq11 log-scale| <= max_dev on every axis.
+// Learned prior on freshly written high-frequency seeds: features, inference, then per seed the
+// predicted opacity logit, and the predicted log-scales unless one axis lies
+// further than max_dev from eq11's log-scale (then eq11's radius stays: eq11 is
+// the judge of the scale; it says nothing about opacity).
 __global__ void k_apply_prior(const float *__restrict__ pred, const int32_t *__restrict__ xy,
                               const uint8_t *__restrict__ seed_hi, const int64_t *__restrict__ base,
                               const float *__restrict__ depth, int W, float alpha_h, float alpha_l, float f,
                               float max_dev, GaussGrads g) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= base[1]) return;
+  if (s >= base[1] || !seed_hi[s]) return;  // the prior initialises high-frequency seeds only
   const float d = depth[(int64_t)xy[2 * s + 1] * W + xy[2 * s]];
   const float ls = logf((seed_hi[s] ? alpha_h : alpha_l) * d / f);
   const float *p = pred + 4 * s;
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < 3; ++k) ok = ok && fabsf(p[k] - ls) <= max_dev;
-  if (!ok) return;
   const int64_t i = base[0] + s, c = g.cap;
+  g.logits[i] = p[3];
+  if (!ok) return;
   g.log_scales[i] = p[0];
   g.log_scales[c + i] = p[1];
   g.log_scales[2 * c + i] = p[2];
-  g.logits[i] = p[3];
 }
 
 size_t prior_apply_workspace_size(int64_t max_new) {
@@ -550,9 +552,9 @@ extern "C" size_t fgs_prior_train_workspace_size(int64_t n) {
 
 extern "C" fgs_status fgs_prior_features(const float *rgb, const float *depth, int32_t width, int32_t height,
                                          const int32_t *seed_xy, int64_t n, uint16_t *features, void *stream) {
-  FGS_CHECK_ARG(rgb && depth && seed_xy && features && width > 0 && height > 0 && n >= 0,
-                "fgs_prior_features: bad argument");
+  FGS_CHECK_ARG(n >= 0, "fgs_prior_features: n < 0");
   if (n == 0) return FGS_OK;
+  FGS_CHECK_ARG(rgb && depth && seed_xy && features && width > 0 && height > 0, "fgs_prior_features: bad argument");
   k_features<<<(unsigned)std::min<int64_t>(n, 8 * num_sms()), 256, 0, as_stream(stream)>>>(
       rgb, depth, width, height, seed_xy, n, nullptr, features);
   count_launch();
@@ -562,8 +564,9 @@ extern "C" fgs_status fgs_prior_features(const float *rgb, const float *depth, i
 
 extern "C" fgs_status fgs_prior_infer(const fgs_mlp *mlp, const uint16_t *features, int64_t n, float *out,
                                       void *stream) {
-  FGS_CHECK_ARG(mlp_ok(mlp) && features && out && n >= 0, "fgs_prior_infer: bad argument");
+  FGS_CHECK_ARG(n >= 0, "fgs_prior_infer: n < 0");
   if (n == 0) return FGS_OK;
+  FGS_CHECK_ARG(mlp_ok(mlp) && features && out, "fgs_prior_infer: bad argument");
   fgs_status s = set_smem((const void *)k_infer, kInferSmem);
   if (s != FGS_OK) return s;
   k_infer<<<infer_grid(n), 32 * kInferWarps, kInferSmem, as_stream(stream)>>>(*mlp, features, n, nullptr, out);

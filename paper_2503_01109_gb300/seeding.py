@@ -26,6 +26,7 @@ class Seeder:
         self.mask = torch.zeros(H * W, dtype=torch.uint8, device=dev)
         self.energy = torch.zeros(H * W, dtype=torch.float32, device=dev)
         self.num_new = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.seed_xy = torch.zeros(max(self.params.max_new, 1), 2, dtype=torch.int32, device=dev)
         self.threshold = torch.zeros(1, dtype=torch.int32, device=dev)
 
     def seed_frame(self, color_gt, depth_gt, cam: dict, render_first: bool = True, first_frame: bool = False):
@@ -38,4 +39,5 @@ class Seeder:
         mlp = None if self.prior is None else self.prior.mlp_struct()
         fgs.fgs_fourier_seed(color_gt, depth_gt, None if first_frame else f.color, None if first_frame else f.depth,
                              None if first_frame else f.alpha, cam, self.params, mlp, self.mask, self.energy, m.g,
-                             self.num_new, self.threshold, self.ws, m.status, use_device_count=True)
+                             self.num_new, self.threshold, self.ws, m.status, use_device_count=True,
+                             seed_xy=self.seed_xy)
