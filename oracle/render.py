@@ -51,7 +51,10 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        # no contraction into fused multiply-adds: the float32 decisions must round
+        # every operation separately (aarch64 GCC fuses by default)
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC,
+                               "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -64,10 +67,10 @@ def lib():
             L = ctypes.CDLL(path)
             P = ctypes.c_void_p
             i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
-            L.or_project.argtypes = [i64, P, P, P, P, P, P, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]
-            L.or_count_pairs.argtypes = [i32, i64, P, P]
+            L.or_project.argtypes = [i64, P, P, P, P, P, P, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P]
+            L.or_count_pairs.argtypes = [i32, i64, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.or_count_pairs.restype = i64
-            L.or_bin_sort.argtypes = [i32, i64, P, P, P, P, P, P, P, P]
+            L.or_bin_sort.argtypes = [i32, i64, P, P, P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P]
             L.or_bin_sort.restype = i64
             L.or_render_fwd.argtypes = [i64, P, P, P, P, P, P, P, P, ctypes.c_int, ctypes.c_int, P, P,
                                         i32, P, P, P, P, P, P]
@@ -128,27 +131,37 @@ def project(scene_aos: dict, cam: dict, tile_w: int = 16, tile_h: int = 16) -> d
     """EWA projection of every Gaussian into one view (Sec. III, C = R S S^T R^T).
 
     Returns mean2d[n][2], conic[n][3] (inverse of the dilated 2D covariance),
-    depth[n] (camera z), opacity[n] (sigmoid of the logit), radius[n] (0 = culled)
-    and rect[n][4] (inclusive tile bounds of the 3-sigma box; x0 > x1 = none)."""
+    depth[n] (camera z), opacity[n] (sigmoid of the logit), radius[n] (0 = culled),
+    rect[n][4] (inclusive tile bounds of the 3-sigma box; x0 > x1 = none) and
+    thr[n] (support threshold 2 ln(255 o) + margin; tiles where the splat's
+    Mahalanobis form exceeds it everywhere cannot reach alpha 1/255)."""
     n = scene_aos["means"].shape[0]
     out = {
         "mean2d": np.zeros((n, 2)), "conic": np.zeros((n, 3)), "depth": np.zeros(n),
         "opacity": np.zeros(n), "radius": np.zeros(n, np.int32), "rect": np.zeros((n, 4), np.int32),
+        "thr": np.zeros(n),
     }
     cv = cam_vec(cam)
     lib().or_project(n, _p(scene_aos["means"]), _p(scene_aos["log_scales"]), _p(scene_aos["quats"]),
                      _p(scene_aos["logits"]), _p(cv), _p(KCONST), tile_w, tile_h, _p(out["mean2d"]),
                      _p(out["conic"]), _p(out["depth"]), _p(out["opacity"]), _p(out["radius"]),
-                     _p(out["rect"]))
+                     _p(out["rect"]), _p(out["thr"]))
     return out
 
 
+def support_f64(splats: dict) -> np.ndarray:
+    """[n][6] double (mx, my, a, b, c, thr) of one view's FP64 splats."""
+    return np.ascontiguousarray(np.concatenate([splats["mean2d"], splats["conic"], splats["thr"][:, None]], 1))
+
+
 def bin_sort(cams: list, tile_w: int, tile_h: int, depth_f32: np.ndarray, radius: np.ndarray,
-             rect: np.ndarray):
+             rect: np.ndarray, supp: np.ndarray | None = None):
     """Sorted (tile, Gaussian) lists of a view set.
 
-    depth_f32[v][n] float32, radius[v][n], rect[v][n][4].  Order: global tile,
-    float32 depth bits, id.  Returns (tile[P] uint32, id[P] int32, ranges[T][2])."""
+    depth_f32[v][n] float32, radius[v][n], rect[v][n][4], supp[v][n][6] (mx, my, a,
+    b, c, thr; float32 -> the support test in float32, float64 -> in double; None:
+    the whole rect).  Order: global tile, float32 depth bits, id.  Returns
+    (tile[P] uint32, id[P] int32, ranges[T][2])."""
     V = len(cams)
     n = depth_f32.shape[1]
     tx = np.array([tiles_of(c, tile_w, tile_h)[0] for c in cams], np.int32)
@@ -156,12 +169,17 @@ def bin_sort(cams: list, tile_w: int, tile_h: int, depth_f32: np.ndarray, radius
     depth_f32 = np.ascontiguousarray(depth_f32, np.float32)
     radius = np.ascontiguousarray(radius, np.int32)
     rect = np.ascontiguousarray(rect, np.int32)
-    P = lib().or_count_pairs(V, n, _p(radius), _p(rect))
+    sp, f32 = None, 0
+    if supp is not None:
+        f32 = 1 if supp.dtype == np.float32 else 0
+        supp = np.ascontiguousarray(supp, np.float32 if f32 else np.float64)
+        sp = _p(supp)
+    P = lib().or_count_pairs(V, n, _p(radius), _p(rect), sp, f32, tile_w, tile_h)
     tiles = np.zeros(max(P, 1), np.uint32)
     ids = np.zeros(max(P, 1), np.int32)
     ranges = np.zeros((int((tx * ty).sum()), 2), np.int32)
-    P2 = lib().or_bin_sort(V, n, _p(tx), _p(ty), _p(depth_f32), _p(radius), _p(rect), _p(tiles),
-                           _p(ids), _p(ranges))
+    P2 = lib().or_bin_sort(V, n, _p(tx), _p(ty), _p(depth_f32), _p(radius), _p(rect), sp, f32, tile_w, tile_h,
+                           _p(tiles), _p(ids), _p(ranges))
     assert P2 == P
     return tiles[:P], ids[:P], ranges
 
@@ -286,11 +304,18 @@ def adam(p, g, m, v, lr, b1=0.9, b2=0.999, eps=1e-15, t=1):
 
 def splats_from_gpu(splat: np.ndarray, radius: np.ndarray, rect: np.ndarray) -> dict:
     """Teacher forcing: a view's float32 splat records [n][8] (mean2d, conic,
-    opacity, depth) and integer support, widened to float64."""
+    opacity, depth, support threshold) and integer support, widened to float64."""
     s = np.asarray(splat, np.float64)
     return {"mean2d": np.ascontiguousarray(s[:, 0:2]), "conic": np.ascontiguousarray(s[:, 2:5]),
             "opacity": np.ascontiguousarray(s[:, 5]), "depth": np.ascontiguousarray(s[:, 6]),
-            "radius": np.asarray(radius, np.int32), "rect": np.asarray(rect, np.int32)}
+            "thr": np.ascontiguousarray(s[:, 7]), "radius": np.asarray(radius, np.int32),
+            "rect": np.asarray(rect, np.int32)}
+
+
+def support_f32(splat: np.ndarray) -> np.ndarray:
+    """[n][6] float32 (mx, my, a, b, c, thr) straight from a view's GPU records."""
+    s = np.asarray(splat, np.float32)
+    return np.ascontiguousarray(s[:, [0, 1, 2, 3, 4, 7]])
 
 
 def render_views(scene: dict, cams: list, tile_w=16, tile_h=16) -> dict:
@@ -305,7 +330,8 @@ def render_views(scene: dict, cams: list, tile_w=16, tile_h=16) -> dict:
         depth32.append(pr["depth"].astype(np.float32))
         radius.append(pr["radius"])
         rect.append(pr["rect"])
-    tiles, ids, ranges = bin_sort(cams, tile_w, tile_h, np.stack(depth32), np.stack(radius), np.stack(rect))
+    tiles, ids, ranges = bin_sort(cams, tile_w, tile_h, np.stack(depth32), np.stack(radius), np.stack(rect),
+                                  np.stack([support_f64(p) for p in projs]))
     outs, base = [], 0
     for cam, pr in zip(cams, projs):
         outs.append(render_fwd(pr, sa["rgb"], cam, ids, ranges, base, tile_w, tile_h))

@@ -19,7 +19,8 @@
  *   means[n][3], log_scales[n][3], quats[n][4] (w,x,y,z), logits[n], rgb[n][3]
  *   camera: double cam[19] = w, h, fx, fy, cx, cy, R[9] row-major, t[3], znear
  *   splats of one view: mean2d[n][2], conic[n][3], depth[n], opacity[n],
- *   radius[n] (0 = culled), rect[n][4] = tile x0, y0, x1, y1 (x0 > x1: none)
+ *   radius[n] (0 = culled), rect[n][4] = tile x0, y0, x1, y1 (x0 > x1: none),
+ *   thr[n] (support threshold, see or_project)
  */
 #include <math.h>
 #include <stdint.h>
@@ -131,11 +132,16 @@ static void project_one(const double *mu, const double *ls, const double *q, dou
   o->visible = 1;
 }
 
+/* Support threshold of a splat: alpha = o exp(-q/2) reaches 1/255 only where
+ * q <= 2 ln(255 o); plus a margin above any float32 rounding of that test.  A
+ * splat with 255 o <= 1 blends nowhere (-1). */
+#define SUPPORT_MARGIN 0.01
+
 /* Projection of n Gaussians into one view; rect uses tile_w x tile_h tiles. */
 void or_project(int64_t n, const double *means, const double *log_scales, const double *quats,
                 const double *logits, const double *cam, const double *kconst, int tile_w,
                 int tile_h, double *mean2d, double *conic, double *depth, double *opacity,
-                int32_t *radius, int32_t *rect) {
+                int32_t *radius, int32_t *rect, double *thr) {
   OConst k;
   unpack_const(kconst, &k);
   const int W = (int)cam[0], H = (int)cam[1];
@@ -154,6 +160,7 @@ void or_project(int64_t n, const double *means, const double *log_scales, const 
     int32_t *rc = rect + 4 * i;
     rc[0] = 1; rc[1] = 1; rc[2] = 0; rc[3] = 0;
     radius[i] = 0;
+    thr[i] = 255.0 * o.opacity > 1.0 ? 2.0 * log(255.0 * o.opacity) + SUPPORT_MARGIN : -1.0;
     if (!o.visible) continue;
     double mid = 0.5 * (o.a + o.c);
     double lam = mid + sqrt(fmax(0.0, mid * mid - o.det));
@@ -168,14 +175,70 @@ void or_project(int64_t n, const double *means, const double *log_scales, const 
     if (y0 < 0) y0 = 0;
     if (x1 > tiles_x - 1) x1 = tiles_x - 1;
     if (y1 > tiles_y - 1) y1 = tiles_y - 1;
-    if (x0 <= x1 && y0 <= y1) {
+    if (x0 <= x1 && y0 <= y1 && thr[i] >= 0) {
       rc[0] = (int32_t)x0; rc[1] = (int32_t)y0; rc[2] = (int32_t)x1; rc[3] = (int32_t)y1;
     }
   }
 }
 
 /* ---------------------------------------------------------------------------------
- * Binning: every (tile, Gaussian) pair whose tile lies in the Gaussian's rect,
+ * Opacity-aware support of a splat on a tile: the minimum over the tile's pixel
+ * centres of q(d) = a dx^2 + 2 b dx dy + c dy^2 (d = pixel - mean2d) is at most thr.
+ * The minimum of this convex form over a rectangle is 0 when the mean lies inside,
+ * else it lies on an edge, where it is a 1-D quadratic minimised at
+ * dy = -b dx / c (vertical edges) or dx = -b dy / a (horizontal edges), clamped.
+ * support_f32 takes every step in float32 (teacher-forced parity with the
+ * kernels); support_f64 is the same test in double. */
+static float support_q32(float a, float b, float c, float dx, float dy) {
+  return (a * (dx * dx) + 2.f * (b * (dx * dy))) + c * (dy * dy);
+}
+
+static int support_f32(float mx, float my, float a, float b, float c, float thr, int tx, int ty, int tw, int th) {
+  float x0 = (float)(tx * tw) - mx, x1 = (float)(tx * tw + tw - 1) - mx;
+  float y0 = (float)(ty * th) - my, y1 = (float)(ty * th + th - 1) - my;
+  if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return 1;
+  float sx = -b / a, sy = -b / c;   /* dx on a horizontal edge = sx dy, dy on a vertical one = sy dx */
+  float q0 = support_q32(a, b, c, x0, fminf(fmaxf(sy * x0, y0), y1));
+  float q1 = support_q32(a, b, c, x1, fminf(fmaxf(sy * x1, y0), y1));
+  float q2 = support_q32(a, b, c, fminf(fmaxf(sx * y0, x0), x1), y0);
+  float q3 = support_q32(a, b, c, fminf(fmaxf(sx * y1, x0), x1), y1);
+  return fminf(fminf(q0, q1), fminf(q2, q3)) <= thr;
+}
+
+static int support_f64(double mx, double my, double a, double b, double c, double thr, int tx, int ty, int tw,
+                       int th) {
+  double x0 = tx * tw - mx, x1 = tx * tw + tw - 1 - mx, y0 = ty * th - my, y1 = ty * th + th - 1 - my;
+  if (x0 <= 0 && x1 >= 0 && y0 <= 0 && y1 >= 0) return 1;
+  double best = 1e300;
+  for (int e = 0; e < 4; ++e) {
+    double dx, dy;
+    if (e < 2) {
+      dx = e == 0 ? x0 : x1;
+      dy = clampd(-b * dx / c, y0, y1);
+    } else {
+      dy = e == 2 ? y0 : y1;
+      dx = clampd(-b * dy / a, x0, x1);
+    }
+    double q = a * dx * dx + 2 * b * dx * dy + c * dy * dy;
+    if (q < best) best = q;
+  }
+  return best <= thr;
+}
+
+/* supp: per record mx, my, a, b, c, thr -- float32 [v][n][6] (supp_f32 = 1) or
+ * double (supp_f32 = 0); NULL = the whole rect is the support. */
+static int in_support(const void *supp, int supp_f32, int64_t rec, int tx, int ty, int tw, int th) {
+  if (!supp) return 1;
+  if (supp_f32) {
+    const float *s = (const float *)supp + 6 * rec;
+    return support_f32(s[0], s[1], s[2], s[3], s[4], s[5], tx, ty, tw, th);
+  }
+  const double *s = (const double *)supp + 6 * rec;
+  return support_f64(s[0], s[1], s[2], s[3], s[4], s[5], tx, ty, tw, th);
+}
+
+/* ---------------------------------------------------------------------------------
+ * Binning: every (tile, Gaussian) pair whose tile lies in the Gaussian's rect and support,
  * ordered by (global tile, float32 depth bits, id).  Depth order is the
  * front-to-back order eq1's product runs over.  depth_f32 is the float32 depth
  * the kernels key on; it is given, so the order is a pure integer question. */
@@ -194,13 +257,16 @@ static int pair_cmp(const void *pa, const void *pb) {
 }
 
 /* Counts the pairs of a view set.  rect[v][n][4], radius[v][n]. */
-int64_t or_count_pairs(int32_t n_views, int64_t n, const int32_t *radius, const int32_t *rect) {
+int64_t or_count_pairs(int32_t n_views, int64_t n, const int32_t *radius, const int32_t *rect,
+                       const void *supp, int supp_f32, int tile_w, int tile_h) {
   int64_t total = 0;
   for (int32_t v = 0; v < n_views; ++v)
     for (int64_t i = 0; i < n; ++i) {
       const int32_t *r = rect + 4 * (v * n + i);
       if (radius[v * n + i] <= 0 || r[0] > r[2] || r[1] > r[3]) continue;
-      total += (int64_t)(r[2] - r[0] + 1) * (r[3] - r[1] + 1);
+      for (int32_t ty = r[1]; ty <= r[3]; ++ty)
+        for (int32_t tx = r[0]; tx <= r[2]; ++tx)
+          total += in_support(supp, supp_f32, v * n + i, tx, ty, tile_w, tile_h);
     }
   return total;
 }
@@ -209,8 +275,9 @@ int64_t or_count_pairs(int32_t n_views, int64_t n, const int32_t *radius, const 
  * (ranges[2*t], ranges[2*t+1]).  Returns the pair count. */
 int64_t or_bin_sort(int32_t n_views, int64_t n, const int32_t *tiles_x, const int32_t *tiles_y,
                     const float *depth_f32, const int32_t *radius, const int32_t *rect,
+                    const void *supp, int supp_f32, int tile_w, int tile_h,
                     uint32_t *out_tile, int32_t *out_id, int32_t *ranges) {
-  int64_t P = or_count_pairs(n_views, n, radius, rect);
+  int64_t P = or_count_pairs(n_views, n, radius, rect, supp, supp_f32, tile_w, tile_h);
   OPair *pairs = (OPair *)malloc(sizeof(OPair) * (size_t)(P > 0 ? P : 1));
   int64_t k = 0;
   uint32_t tile_base = 0;
@@ -222,6 +289,7 @@ int64_t or_bin_sort(int32_t n_views, int64_t n, const int32_t *tiles_x, const in
       memcpy(&dbits, &depth_f32[v * n + i], 4);
       for (int32_t ty = r[1]; ty <= r[3]; ++ty)
         for (int32_t tx = r[0]; tx <= r[2]; ++tx) {
+          if (!in_support(supp, supp_f32, v * n + i, tx, ty, tile_w, tile_h)) continue;
           pairs[k].tile = tile_base + (uint32_t)(ty * tiles_x[v] + tx);
           pairs[k].dbits = dbits;
           pairs[k].id = (int32_t)i;

@@ -2,8 +2,9 @@
 //
 // The required order of every tile's list is (float32 depth bits, Gaussian id).
 // Instead of radix-sorting 64-bit (tile | depth) keys of every (tile, Gaussian)
-// pair, the records are sorted by depth ONCE (n_views * n keys, stable, so equal
-// depths stay in id order), pairs are emitted in that order, and a stable sort on
+// pair, the visible records are compacted in record order and sorted by depth
+// ONCE (stable, so equal depths stay in id order), pairs are emitted in that
+// order, and a stable sort on
 // the tile index alone (a few bits, one or two 8-bit passes) finishes the job:
 // within a tile the pairs keep their emission order, which is depth then id.
 //
@@ -228,44 +229,136 @@ static int sort_blocks(int64_t cap) {
 }
 
 // ---------------------------------------------------------------------------------
-// record keys for the depth sort: float32 depth bits of a record with tiles, else
-// 0xFFFFFFFF (sorted last; such records emit nothing)
+// Visible records (radius > 0 and at least one tile) are compacted in record
+// order before the depth sort, so the sort touches only them: a block count, a
+// scan of the block counts, and an ordered scatter of (depth bits, record).
 
-__global__ void k_depth_keys(const float4 *__restrict__ splat, const int32_t *__restrict__ radius,
-                             const uint2 *__restrict__ rect, int64_t n, int64_t stride, int n_views,
-                             uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j >= (int64_t)n_views * n) return;
-  const int64_t v = j / n, i = j - v * n;
-  const int64_t r = v * stride + i;
-  uint32_t key = 0xFFFFFFFFu;
-  if (radius[r] > 0) {
-    const uint2 rc = rect[r];
-    if ((rc.x & 0xFFFFu) <= (rc.y & 0xFFFFu) && (rc.x >> 16) <= (rc.y >> 16))
-      key = __float_as_uint(splat[2 * r + 1].z);
-  }
-  keys[j] = key;
-  vals[j] = (uint32_t)r;
-}
-
-__device__ __forceinline__ uint32_t rect_tiles(uint2 rc) {
-  const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu, y1 = rc.y >> 16;
-  if (x0 > x1 || y0 > y1) return 0u;
-  return (x1 - x0 + 1u) * (y1 - y0 + 1u);
-}
-
-// Tiles per sorted record, then per-block sums for the scan.
 constexpr int kScanBlock = 1024;
 
-__global__ void __launch_bounds__(kScanBlock) k_counts_blocksum(const uint32_t *__restrict__ skeys,
+__device__ __forceinline__ bool record_visible(const int32_t *__restrict__ radius, const uint2 *__restrict__ rect,
+                                               int64_t r) {
+  if (radius[r] <= 0) return false;
+  const uint2 rc = rect[r];
+  return (rc.x & 0xFFFFu) <= (rc.y & 0xFFFFu) && (rc.x >> 16) <= (rc.y >> 16);
+}
+
+// record index of compact slot j (j < n_views * n): view-major, ids ascending
+__device__ __forceinline__ int64_t record_of(int64_t j, int64_t n, int64_t stride) {
+  const int64_t v = j / n;
+  return v * stride + (j - v * n);
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_vis_count(const int32_t *__restrict__ radius,
+                                                          const uint2 *__restrict__ rect, int64_t n, int64_t stride,
+                                                          int64_t R, uint32_t *__restrict__ bsum) {
+  __shared__ uint32_t red[kScanBlock / 32];
+  const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+  const bool vis = j < R && record_visible(radius, rect, record_of(j, n, stride));
+  const uint32_t b = __ballot_sync(0xffffffffu, vis);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t t = red[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of nb block counts in place by one CTA; *total = their sum.
+__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *__restrict__ bsum, int nb, int64_t *total) {
+  __shared__ unsigned long long part[1024];
+  const int per = (nb + 1023) / 1024;
+  const int lo = threadIdx.x * per, hi = min(nb, lo + per);
+  unsigned long long s = 0;
+  for (int i = lo; i < hi; ++i) s += bsum[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const unsigned long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned long long run = part[threadIdx.x] - s;
+  for (int i = lo; i < hi; ++i) {
+    const uint32_t v = bsum[i];
+    bsum[i] = (uint32_t)run;
+    run += v;
+  }
+  if (threadIdx.x == 1023) *total = (int64_t)part[1023];
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_vis_scatter(const float4 *__restrict__ splat,
+                                                            const int32_t *__restrict__ radius,
+                                                            const uint2 *__restrict__ rect, int64_t n, int64_t stride,
+                                                            int64_t R, const uint32_t *__restrict__ bsum,
+                                                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+  __shared__ uint32_t wsum[kScanBlock / 32];
+  const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t r = j < R ? record_of(j, n, stride) : 0;
+  const bool vis = j < R && record_visible(radius, rect, r);
+  const uint32_t b = __ballot_sync(0xffffffffu, vis);
+  if (lane == 0) wsum[warp] = __popc(b);
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = wsum[lane];
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    wsum[lane] = wi - w;
+  }
+  __syncthreads();
+  if (!vis) return;
+  const uint32_t pos = bsum[blockIdx.x] + wsum[warp] + __popc(b & ((1u << lane) - 1u));
+  keys[pos] = __float_as_uint(splat[2 * r + 1].z);  // depth > 0: its bits order like the value
+  vals[pos] = (uint32_t)r;
+}
+
+
+// Tiles per sorted visible record (those of its box that its opacity-aware
+// ellipse reaches), then per-block sums for the scan.  A warp counts its 32
+// records one after the other, its lanes testing 32 of the record's tiles at a
+// time, so large footprints do not serialise one thread.
+__global__ void __launch_bounds__(kScanBlock) k_counts_blocksum(const float4 *__restrict__ splat,
                                                                 const uint32_t *__restrict__ svals,
-                                                                const uint2 *__restrict__ rect, int64_t R,
+                                                                const uint2 *__restrict__ rect,
+                                                                const int64_t *__restrict__ d_vis, int tw, int th,
                                                                 uint32_t *__restrict__ cnt,
                                                                 uint32_t *__restrict__ bsum) {
   __shared__ uint32_t red[kScanBlock / 32];
   const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+  const int64_t R = *d_vis;
+  const int lane = threadIdx.x & 31;
+  const uint32_t my_rec = j < R ? svals[j] : 0u;
   uint32_t c = 0;
-  if (j < R && skeys[j] != 0xFFFFFFFFu) c = rect_tiles(rect[svals[j]]);
+  uint32_t pending = __ballot_sync(0xffffffffu, j < R);
+  while (pending) {
+    const int src = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const uint32_t rec = __shfl_sync(0xffffffffu, my_rec, src);
+    const uint2 rc = rect[rec];
+    const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu, y1 = rc.y >> 16;
+    uint32_t n = 0;
+    if (x0 <= x1 && y0 <= y1) {
+      const SupportSplat sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
+      const uint32_t w = x1 - x0 + 1u, box = w * (y1 - y0 + 1u);
+      for (uint32_t q0 = 0; q0 < box; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        bool keep = false;
+        if (q < box) {
+          const uint32_t dy = q / w, dx = q - dy * w;
+          keep = tile_in_support(sp, (int)(x0 + dx), (int)(y0 + dy), tw, th);
+        }
+        n += __popc(__ballot_sync(0xffffffffu, keep));
+      }
+    }
+    if (lane == src) c = n;
+  }
   if (j < R) cnt[j] = c;
   uint32_t s = c;
 #pragma unroll
@@ -316,15 +409,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_bsum(uint32_t *__restrict
 // Emits the (tile, id) pairs of every sorted record at its scanned offset.  A
 // warp cooperates on one record at a time so that large footprints do not
 // serialise a single thread.
-__global__ void __launch_bounds__(kScanBlock) k_emit(const uint32_t *__restrict__ skeys,
+__global__ void __launch_bounds__(kScanBlock) k_emit(const float4 *__restrict__ splat, int tw, int th,
                                                      const uint32_t *__restrict__ svals,
                                                      const uint2 *__restrict__ rect,
                                                      const uint32_t *__restrict__ cnt,
-                                                     const uint32_t *__restrict__ bsum, int64_t R,
-                                                     int64_t stride, DevViews vs, const int64_t *d_sort_count,
-                                                     uint32_t *__restrict__ tile_keys, uint32_t *__restrict__ ids) {
+                                                     const uint32_t *__restrict__ bsum,
+                                                     const int64_t *__restrict__ d_vis, int64_t stride, DevViews vs,
+                                                     const int64_t *d_sort_count, uint32_t *__restrict__ tile_keys,
+                                                     uint32_t *__restrict__ ids) {
   __shared__ uint32_t warp_sum[kScanBlock / 32];
   const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+  const int64_t R = *d_vis;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t c = j < R ? cnt[j] : 0u;
   // block-local exclusive scan of c
@@ -359,14 +454,31 @@ __global__ void __launch_bounds__(kScanBlock) k_emit(const uint32_t *__restrict_
     const uint32_t rec = __shfl_sync(0xffffffffu, j < R ? svals[j] : 0u, src);
     const uint2 rc = rect[rec];
     const uint32_t v = (uint32_t)(rec / stride), id = (uint32_t)(rec - (uint64_t)v * stride);
-    const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu;
-    const uint32_t w = x1 - x0 + 1u;
+    const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu, y1 = rc.y >> 16;
+    const uint32_t w = x1 - x0 + 1u, box = w * (y1 - y0 + 1u);
     const uint32_t tb = (uint32_t)vs.cam[v].tile_base, tx = (uint32_t)vs.cam[v].tiles_x;
-    for (uint32_t q = lane; q < rc_cnt; q += 32) {
-      const uint32_t dy = q / w, dx = q - dy * w;
-      tile_keys[rc_off + q] = tb + (y0 + dy) * tx + (x0 + dx);
-      ids[rc_off + q] = id;
+    const SupportSplat sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
+    // the box's tiles in row-major order, 32 candidates per step; the ones the
+    // ellipse reaches are written at consecutive positions (rc_cnt in total)
+    uint32_t out = rc_off;
+    for (uint32_t q0 = 0; q0 < box; q0 += 32) {
+      const uint32_t q = q0 + lane;
+      bool keep = false;
+      uint32_t t = 0;
+      if (q < box) {
+        const uint32_t dy = q / w, dx = q - dy * w;
+        keep = tile_in_support(sp, (int)(x0 + dx), (int)(y0 + dy), tw, th);
+        t = tb + (y0 + dy) * tx + (x0 + dx);
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const uint32_t pos = out + __popc(m & ((1u << lane) - 1u));
+        tile_keys[pos] = t;
+        ids[pos] = id;
+      }
+      out += __popc(m);
     }
+    (void)rc_cnt;
   }
 }
 
@@ -391,6 +503,7 @@ struct BinWs {
   uint32_t *counts;                 // 256 * kSortMaxBlocks
   uint32_t *digit_total;            // 256
   int64_t *sort_count;              // 1
+  int64_t *vis_count;               // 1
   size_t bytes;
 };
 
@@ -415,6 +528,7 @@ static BinWs carve(void *base, int64_t R, int64_t cap) {
   w.counts = (uint32_t *)take((size_t)256 * kSortMaxBlocks * 4);
   w.digit_total = (uint32_t *)take(256 * 4);
   w.sort_count = (int64_t *)take(8);
+  w.vis_count = (int64_t *)take(8);
   w.bytes = off;
   return w;
 }
@@ -460,25 +574,27 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   }
   const float4 *splat = reinterpret_cast<const float4 *>(proj->splat);
   const uint2 *rect = reinterpret_cast<const uint2 *>(proj->rect);
-  {
-    const int th = 256;
-    k_depth_keys<<<(unsigned)((R + th - 1) / th), th, 0, st>>>(splat, proj->radius, rect, n, proj->stride,
-                                                              n_views, w.dk0, w.dv0);
-    count_launch();
-  }
-  // depth sort: 4 passes, result back in (dk0, dv0)
-  fgs_status s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, nullptr, R, R, 32, sort_blocks(R), w.counts, w.digit_total, st);
-  if (s != FGS_OK) return s;
   const int64_t nb = (R + kScanBlock - 1) / kScanBlock;
-  k_counts_blocksum<<<(unsigned)nb, kScanBlock, 0, st>>>(w.dk0, w.dv0, rect, R, w.cnt, w.bsum);
+  // ordered compaction of the visible records, then the depth sort over them
+  // (4 passes, stable: equal depths keep record order = id order within a view)
+  k_vis_count<<<(unsigned)nb, kScanBlock, 0, st>>>(proj->radius, rect, n, proj->stride, R, w.bsum);
+  k_scan_blocks<<<1, 1024, 0, st>>>(w.bsum, (int)nb, w.vis_count);
+  k_vis_scatter<<<(unsigned)nb, kScanBlock, 0, st>>>(splat, proj->radius, rect, n, proj->stride, R, w.bsum, w.dk0,
+                                                     w.dv0);
+  count_launch(3);
+  fgs_status s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, w.vis_count, 0, R, 32, sort_blocks(R), w.counts,
+                            w.digit_total, st);
+  if (s != FGS_OK) return s;
+  k_counts_blocksum<<<(unsigned)nb, kScanBlock, 0, st>>>(splat, w.dv0, rect, w.vis_count, tiling.tile_w,
+                                                         tiling.tile_h, w.cnt, w.bsum);
   k_scan_bsum<<<1, kScanThreads, 0, st>>>(w.bsum, (int)nb, d_num_pairs, pair_capacity, d_status, w.sort_count);
   // emit into the buffer the tile sort ends in the caller's arrays
   const int tbits = std::max(1, bits_for(vs.total_tiles));
   const int passes = (tbits + 7) / 8;
   uint32_t *ek = (passes & 1) ? w.tk1 : tile_keys;
   uint32_t *ev = (passes & 1) ? w.tv1 : reinterpret_cast<uint32_t *>(ids);
-  k_emit<<<(unsigned)nb, kScanBlock, 0, st>>>(w.dk0, w.dv0, rect, w.cnt, w.bsum, R, proj->stride, vs,
-                                              w.sort_count, ek, ev);
+  k_emit<<<(unsigned)nb, kScanBlock, 0, st>>>(splat, tiling.tile_w, tiling.tile_h, w.dv0, rect, w.cnt, w.bsum,
+                                              w.vis_count, proj->stride, vs, w.sort_count, ek, ev);
   count_launch(3);
   FGS_CHECK_LAUNCH("fgs_bin_sort emit");
   s = radix_sort(ek, ev, (passes & 1) ? tile_keys : w.tk1, (passes & 1) ? reinterpret_cast<uint32_t *>(ids) : w.tv1,

@@ -123,11 +123,15 @@ __global__ void k_project(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_
     y0 = fmaxf(y0, 0.f);
     x1 = fminf(x1, (float)(cm.tiles_x - 1));
     y1 = fminf(y1, (float)(cm.tiles_y - 1));
+    // opacity-aware support: alpha = o exp(-q/2) >= 1/255 needs q <= 2 ln(255 o);
+    // a splat with o <= 1/255 can blend nowhere
+    const float lo = 255.0f * L.o;
+    const float thr = lo > 1.0f ? 2.0f * logf(lo) + kSupportMargin : -1.0f;
     uint2 rc = make_uint2(1u | (1u << 16), 0u);
-    if (x0 <= x1 && y0 <= y1)
+    if (x0 <= x1 && y0 <= y1 && thr >= 0.f)
       rc = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
     splat[2 * r] = make_float4(mx, my, ca, cb);
-    splat[2 * r + 1] = make_float4(cc, L.o, V.p[2], 0.f);
+    splat[2 * r + 1] = make_float4(cc, L.o, V.p[2], thr);
     radius[r] = rad;
     rect[r] = rc;
   }

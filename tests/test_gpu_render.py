@@ -68,7 +68,8 @@ def test_bin_sort_bit_exact(cuda_device, W, H, tw, th, bd, n, views):
     depth = np.stack([m.proj.splat[v, :n, 6].cpu().numpy() for v in range(views)]).astype(np.float32)
     radius = np.stack([m.proj.radius[v, :n].cpu().numpy() for v in range(views)])
     rect = np.stack([m.proj.rect[v, :n].cpu().numpy().view(np.uint16).astype(np.int32) for v in range(views)])
-    rt, rids, rranges = orr.bin_sort(cams, tw, th, depth, radius, rect)
+    supp = np.stack([orr.support_f32(m.proj.splat[v, :n].cpu().numpy()) for v in range(views)])
+    rt, rids, rranges = orr.bin_sort(cams, tw, th, depth, radius, rect, supp)
     assert len(tk) == len(rt)
     assert np.array_equal(tk, rt)
     assert np.array_equal(ids, rids)
