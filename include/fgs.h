@@ -96,7 +96,7 @@ typedef struct {
 typedef struct {
   int64_t stride;   /* records per view (>= the Gaussians' n)                          */
   float *splat;     /* [n_views][stride][8]: mean2d.x, mean2d.y, conic a, b, c,       */
-                    /*   opacity, depth (camera z), unused                              */
+                    /*   opacity, depth (camera z), support threshold (fgs_project)     */
   int32_t *radius;  /* [n_views][stride]  ceil(3 sqrt(lambda_max)); 0 = culled          */
   uint16_t *rect;   /* [n_views][stride][4] inclusive tile bounds x0, y0, x1, y1        */
                     /*   (x0 > x1 = touches no tile)                                    */
@@ -114,8 +114,12 @@ typedef struct {
  *   Sigma' = J R_cam C R_cam^T J^T + 0.3 I, J the perspective Jacobian at p with
  *   x/z, y/z clamped to +-1.3 tan(half field of view).  conic = Sigma'^-1.
  *   mean2d = (fx x/z + cx, fy y/z + cy); radius = ceil(3 sqrt(lambda_max(Sigma')));
- *   rect = tiles whose pixel-centre box meets [mean2d -+ 3 sqrt(diag Sigma')].
- *   opacity = sigmoid(logit).
+ *   opacity = sigmoid(logit); support threshold thr = 2 ln(255 opacity) + 0.01
+ *   (alpha = opacity e^(-q/2) can reach 1/255 only where the Mahalanobis form
+ *   q <= thr; -1 when 255 opacity <= 1); rect = tiles whose pixel-centre box
+ *   meets [mean2d -+ min(3, sqrt(thr)) sqrt(diag Sigma')] (empty if thr < 0).
+ *   The splat record's last slot holds thr; fgs_bin_sort further drops the
+ *   tiles of the rect on which q exceeds thr at every pixel centre.
  * in : g (n Gaussians), cams[n_views] (host), tiling.
  * out: out->splat/radius/rect for n_views x g->n records (stride out->stride >= n).
  * err: INVALID_ARGUMENT for n_views outside 1..FGS_MAX_VIEWS, bad tiling, NULLs. */
@@ -128,7 +132,8 @@ int64_t fgs_num_tiles(const fgs_camera *cams, int32_t n_views, fgs_tiling tiling
 /* ---------------------------------------------------------------------------------
  * fgs_bin_sort -- tile binning and depth ordering of the splats that eq1 blends
  * front to back.  Produces, for every global tile, the list of Gaussians whose
- * rect contains the tile, ordered by (float32 depth bits, Gaussian id).
+ * rect contains the tile and whose support ellipse {q <= thr} meets one of the
+ * tile's pixel centres, ordered by (float32 depth bits, Gaussian id).
  *   tile_keys[k], ids[k] for k < *d_num_pairs: global tile index and Gaussian id,
  *   sorted by (tile, depth, id).  tile_ranges[2*t], [2*t+1] = [start, end) of tile t
  *   (0, 0 for an empty tile).
@@ -391,6 +396,8 @@ int64_t fgs_launch_count(void);
 /* cudaMemsetAsync of `bytes` bytes at device pointer dst on the stream (used to
  * clear gradient planes and loss accumulators between mapping iterations). */
 fgs_status fgs_memset_async(void *dst, int32_t value, size_t bytes, void *stream);
+/* cudaMemcpyAsync of `bytes` bytes (any direction the pointers imply) on the stream. */
+fgs_status fgs_memcpy_async(void *dst, const void *src, size_t bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -165,8 +165,11 @@ void or_project(int64_t n, const double *means, const double *log_scales, const 
     double mid = 0.5 * (o.a + o.c);
     double lam = mid + sqrt(fmax(0.0, mid * mid - o.det));
     radius[i] = (int32_t)ceil(k.support_sigma * sqrt(lam));
-    /* tiles whose pixel-centre box [tx*TW, tx*TW+TW-1] meets the 3-sigma box */
-    double ex = k.support_sigma * sqrt(o.a), ey = k.support_sigma * sqrt(o.c);
+    /* tiles whose pixel-centre box [tx*TW, tx*TW+TW-1] meets the 3-sigma box cut
+     * to the bounding box of the support ellipse {q <= thr}: half-widths
+     * sqrt(thr a), sqrt(thr c) with (a, c) the diagonal of the 2D covariance */
+    double kk = fmin(k.support_sigma, sqrt(fmax(thr[i], 0.0)));
+    double ex = kk * sqrt(o.a), ey = kk * sqrt(o.c);
     double x0 = ceil((o.mean2d[0] - ex - (tile_w - 1)) / tile_w);
     double x1 = floor((o.mean2d[0] + ex) / tile_w);
     double y0 = ceil((o.mean2d[1] - ey - (tile_h - 1)) / tile_h);

@@ -108,6 +108,16 @@ fgs_status fgs_memset_async(void *dst, int32_t value, size_t bytes, void *stream
   return FGS_OK;
 }
 
+fgs_status fgs_memcpy_async(void *dst, const void *src, size_t bytes, void *stream) {
+  if (bytes == 0) return FGS_OK;
+  if (dst == nullptr || src == nullptr) {
+    fgs::set_error("fgs_memcpy_async: NULL pointer");
+    return FGS_ERR_INVALID_ARGUMENT;
+  }
+  FGS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, fgs::as_stream(stream)), "fgs_memcpy_async");
+  return FGS_OK;
+}
+
 int64_t fgs_num_tiles(const fgs_camera *cams, int32_t n_views, fgs_tiling tiling) {
   if (!fgs::tiling_ok(tiling)) return -1;
   fgs::DevViews vs;

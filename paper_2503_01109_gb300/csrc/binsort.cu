@@ -320,6 +320,48 @@ __global__ void __launch_bounds__(kScanBlock) k_vis_scatter(const float4 *__rest
 }
 
 
+// A visible record prepared by its own lane (box and support), so that a warp
+// walking its 32 records one after the other only broadcasts them.
+struct PreparedRecord {
+  uint32_t rec, x0, y0, x1, y1;
+  SupportSplat sp;
+};
+
+__device__ __forceinline__ PreparedRecord prepare_record(const float4 *__restrict__ splat,
+                                                         const uint2 *__restrict__ rect, uint32_t rec, bool valid) {
+  PreparedRecord p{};
+  if (!valid) {
+    p.x0 = 1;  // empty box
+    return p;
+  }
+  const uint2 rc = rect[rec];
+  p.rec = rec;
+  p.x0 = rc.x & 0xFFFFu;
+  p.y0 = rc.x >> 16;
+  p.x1 = rc.y & 0xFFFFu;
+  p.y1 = rc.y >> 16;
+  p.sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
+  return p;
+}
+
+__device__ __forceinline__ PreparedRecord shfl_record(const PreparedRecord &p, int src) {
+  PreparedRecord q;
+  q.rec = __shfl_sync(0xffffffffu, p.rec, src);
+  q.x0 = __shfl_sync(0xffffffffu, p.x0, src);
+  q.y0 = __shfl_sync(0xffffffffu, p.y0, src);
+  q.x1 = __shfl_sync(0xffffffffu, p.x1, src);
+  q.y1 = __shfl_sync(0xffffffffu, p.y1, src);
+  q.sp.mx = __shfl_sync(0xffffffffu, p.sp.mx, src);
+  q.sp.my = __shfl_sync(0xffffffffu, p.sp.my, src);
+  q.sp.a = __shfl_sync(0xffffffffu, p.sp.a, src);
+  q.sp.b = __shfl_sync(0xffffffffu, p.sp.b, src);
+  q.sp.c = __shfl_sync(0xffffffffu, p.sp.c, src);
+  q.sp.thr = __shfl_sync(0xffffffffu, p.sp.thr, src);
+  q.sp.sx = __shfl_sync(0xffffffffu, p.sp.sx, src);
+  q.sp.sy = __shfl_sync(0xffffffffu, p.sp.sy, src);
+  return q;
+}
+
 // Tiles per sorted visible record (those of its box that its opacity-aware
 // ellipse reaches), then per-block sums for the scan.  A warp counts its 32
 // records one after the other, its lanes testing 32 of the record's tiles at a
@@ -334,18 +376,17 @@ __global__ void __launch_bounds__(kScanBlock) k_counts_blocksum(const float4 *__
   const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
   const int64_t R = *d_vis;
   const int lane = threadIdx.x & 31;
-  const uint32_t my_rec = j < R ? svals[j] : 0u;
+  const PreparedRecord mine = prepare_record(splat, rect, j < R ? svals[j] : 0u, j < R);
   uint32_t c = 0;
-  uint32_t pending = __ballot_sync(0xffffffffu, j < R);
+  uint32_t pending = __ballot_sync(0xffffffffu, j < R && mine.x0 <= mine.x1 && mine.y0 <= mine.y1);
   while (pending) {
     const int src = __ffs(pending) - 1;
     pending &= pending - 1;
-    const uint32_t rec = __shfl_sync(0xffffffffu, my_rec, src);
-    const uint2 rc = rect[rec];
-    const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu, y1 = rc.y >> 16;
+    const PreparedRecord pr = shfl_record(mine, src);
+    const uint32_t x0 = pr.x0, y0 = pr.y0, x1 = pr.x1, y1 = pr.y1;
+    const SupportSplat &sp = pr.sp;
     uint32_t n = 0;
-    if (x0 <= x1 && y0 <= y1) {
-      const SupportSplat sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
+    {
       const uint32_t w = x1 - x0 + 1u, box = w * (y1 - y0 + 1u);
       for (uint32_t q0 = 0; q0 < box; q0 += 32) {
         const uint32_t q = q0 + lane;
@@ -445,19 +486,21 @@ __global__ void __launch_bounds__(kScanBlock) k_emit(const float4 *__restrict__ 
   const uint32_t off = bsum[blockIdx.x] + warp_sum[warp] + (incl - c);
   const int64_t sort_count = *d_sort_count;  // 0 on overflow: emit nothing
   // warp-cooperative emission: each lane's record in turn
-  uint32_t pending = __ballot_sync(0xffffffffu, c > 0 && sort_count > 0);
+  const bool has = c > 0 && sort_count > 0;
+  const PreparedRecord mine = prepare_record(splat, rect, has ? svals[j] : 0u, has);
+  uint32_t pending = __ballot_sync(0xffffffffu, has);
   while (pending) {
     const int src = __ffs(pending) - 1;
     pending &= pending - 1;
     const uint32_t rc_off = __shfl_sync(0xffffffffu, off, src);
     const uint32_t rc_cnt = __shfl_sync(0xffffffffu, c, src);
-    const uint32_t rec = __shfl_sync(0xffffffffu, j < R ? svals[j] : 0u, src);
-    const uint2 rc = rect[rec];
+    const PreparedRecord pr = shfl_record(mine, src);
+    const uint32_t rec = pr.rec;
     const uint32_t v = (uint32_t)(rec / stride), id = (uint32_t)(rec - (uint64_t)v * stride);
-    const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu, y1 = rc.y >> 16;
-    const uint32_t w = x1 - x0 + 1u, box = w * (y1 - y0 + 1u);
+    const uint32_t x0 = pr.x0, y0 = pr.y0, x1 = pr.x1;
+    const uint32_t w = x1 - x0 + 1u, box = w * (pr.y1 - y0 + 1u);
     const uint32_t tb = (uint32_t)vs.cam[v].tile_base, tx = (uint32_t)vs.cam[v].tiles_x;
-    const SupportSplat sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
+    const SupportSplat &sp = pr.sp;
     // the box's tiles in row-major order, 32 candidates per step; the ones the
     // ellipse reaches are written at consecutive positions (rc_cnt in total)
     uint32_t out = rc_off;

@@ -114,7 +114,13 @@ __global__ void k_project(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_
     const float mid = 0.5f * (V.a + V.c);
     const float lam = mid + sqrtf(fmaxf(0.0f, mid * mid - V.det));
     const int rad = (int)ceilf(kSupportSigma * sqrtf(lam));
-    const float ex = kSupportSigma * sqrtf(V.a), ey = kSupportSigma * sqrtf(V.c);
+    // opacity-aware support: alpha = o exp(-q/2) >= 1/255 needs q <= 2 ln(255 o);
+    // a splat with o <= 1/255 can blend nowhere.  The box is the 3-sigma box cut
+    // to the bounding box of that ellipse (half-widths sqrt(thr Sigma'_xx), ...).
+    const float lo = 255.0f * L.o;
+    const float thr = lo > 1.0f ? 2.0f * logf(lo) + kSupportMargin : -1.0f;
+    const float k = fminf(kSupportSigma, sqrtf(fmaxf(thr, 0.f)));
+    const float ex = k * sqrtf(V.a), ey = k * sqrtf(V.c);
     float x0 = ceilf((mx - ex - (float)(tw - 1)) / (float)tw);
     float x1 = floorf((mx + ex) / (float)tw);
     float y0 = ceilf((my - ey - (float)(th - 1)) / (float)th);
@@ -123,10 +129,6 @@ __global__ void k_project(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_
     y0 = fmaxf(y0, 0.f);
     x1 = fminf(x1, (float)(cm.tiles_x - 1));
     y1 = fminf(y1, (float)(cm.tiles_y - 1));
-    // opacity-aware support: alpha = o exp(-q/2) >= 1/255 needs q <= 2 ln(255 o);
-    // a splat with o <= 1/255 can blend nowhere
-    const float lo = 255.0f * L.o;
-    const float thr = lo > 1.0f ? 2.0f * logf(lo) + kSupportMargin : -1.0f;
     uint2 rc = make_uint2(1u | (1u << 16), 0u);
     if (x0 <= x1 && y0 <= y1 && thr >= 0.f)
       rc = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));

@@ -102,6 +102,7 @@ _SIGS = {
     "fgs_version": ([], c_int32),
     "fgs_launch_count": ([], c_int64),
     "fgs_memset_async": ([c_void_p, c_int32, c_size_t, c_void_p], c_int32),
+    "fgs_memcpy_async": ([c_void_p, c_void_p, c_size_t, c_void_p], c_int32),
 }
 _OPTIONAL = {
     "fgs_fourier_seed": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -400,6 +401,11 @@ def fgs_adam(g: GaussianMap, grads: GaussianMap, m: GaussianMap, v: GaussianMap,
 
 def fgs_memset_async(t: torch.Tensor, value: int = 0):
     _check(lib().fgs_memset_async(_ptr(t), int(value), t.numel() * t.element_size(), _stream()), "fgs_memset_async")
+
+
+def fgs_memcpy_async(dst: torch.Tensor, src: torch.Tensor):
+    n = min(dst.numel() * dst.element_size(), src.numel() * src.element_size())
+    _check(lib().fgs_memcpy_async(_ptr(dst), _ptr(src), n, _stream()), "fgs_memcpy_async")
 
 
 def ws_tensor(nbytes: int, device="cuda") -> torch.Tensor:

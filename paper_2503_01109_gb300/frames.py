@@ -77,7 +77,7 @@ class TimedMapper(Mapper):
             fgs.fgs_render_fwd(self.proj, self.g, self.cams, self.til, self.ids, self.ranges, self.frame, self.status)
         if self.timer.on:
             snap = torch.empty_like(self.frame.n_contrib)
-            snap.copy_(self.frame.n_contrib)   # device copy (copy engine), summed after timing
+            fgs.fgs_memcpy_async(snap, self.frame.n_contrib)   # copy engine; summed after timing
             self.nc_snap.append((self._in_iteration, snap))
 
     def backward(self, dC, dD, dA=None):
