@@ -215,6 +215,23 @@ def convergence_measure(seed_offset: int = 0):
     return out
 
 
+def aggregate(ms_local: float, units_local: float, world: int, dist=None):
+    """Whole-job throughput of N independent replicas: the slowest rank's time
+    and the units all ranks processed (max / sum over ranks; no data exchange)."""
+    if world <= 1 or dist is None:
+        return ms_local, units_local / (ms_local / 1e3)
+    import torch
+    t = torch.tensor([ms_local, units_local], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t = t.cuda()
+    mx = t[:1].clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    tot = t[1:].clone()
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    ms = float(mx.item())
+    return ms, float(tot.item()) / (ms / 1e3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -260,21 +277,15 @@ def run_ours(args):
     pipe.kernel_timer.disable()
     pipe.check()
     clocks = clk.summary()
-    ms_t = torch.tensor([ms], device=device)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max, value = aggregate(ms, iters_per_step * args.steps, world, dist if world > 1 else None)
     total_iters = iters_per_step * args.steps * world
-    value = total_iters / (ms_max / 1e3)
 
     e2e = None
     if not args.no_e2e:
         e2e = pipe.e2e_measure(args.warmup, args.steps, step)
-        e2e_t = torch.tensor([e2e["ms"]], device=device)
-        if world > 1:
-            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-        e2e = {"value": total_iters / (float(e2e_t.item()) / 1e3), "unit": "iters/s",
-               "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
+        _, e2e_value = aggregate(e2e["ms"], iters_per_step * args.steps, world, dist if world > 1 else None)
+        e2e = {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": e2e["h2d"],
+               "d2h_bytes_per_step": e2e["d2h"]}
 
     window = None
     if not args.no_window and pipe.extra is not None:
@@ -287,7 +298,7 @@ def run_ours(args):
             conv = {"error": f"{type(e).__name__}: {e}"}
 
     peaks = load_peaks()
-    roof = pipe.roofline(peaks)
+    roof = pipe.roofline(peaks, os.path.join(ROOT, "profiles"))
     out = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -39,8 +39,10 @@ KCONST = np.array([0.2, DILATION, ALPHA_MAX, ALPHA_MIN, T_MIN, JAC_CLAMP, SUPPOR
                   dtype=np.float64)
 # decision bands: relative band on alpha vs its thresholds, relative band on T vs
 # T_MIN, absolute band on power vs 0.  A float32 evaluation of the same decision
-# can land on the other side only inside these bands.
-BAND = np.array([2e-5, 2e-4, 1e-6], dtype=np.float64)
+# can land on the other side only inside these bands: on the same float32 splat
+# values alpha's relative error is ~1e-6 (rounded power, exp2 approximation) and
+# T's ~1e-5 after ~100 rounded products; the bands keep a factor ~5 above that.
+BAND = np.array([5e-6, 5e-5, 1e-6], dtype=np.float64)
 
 _lock = threading.Lock()
 _lib = None

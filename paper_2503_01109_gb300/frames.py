@@ -12,6 +12,10 @@ library (colour, and depth normalised by the rendered opacity where it exceeds
 """
 from __future__ import annotations
 
+import hashlib
+import os
+import re
+
 import numpy as np
 import torch
 
@@ -213,14 +217,43 @@ class FramePipeline:
 
     # ------------------------------------------------------------------------------
     # roofline of the dominant kernel
-    FLOP_FWD_PAIR = 27  # per evaluated (pixel, splat): see the design doc
+    # FP32 operations per blended (pixel, splat) pair, counted from the kernels'
+    # arithmetic: forward = power 8, exp 2, alpha 2, compare 1, T update 2, five
+    # accumulations 10, misc 2; adjoint = recompute 12, T recovery 2, dalpha 20,
+    # suffix sums 10, ten gradient terms 24.
+    FLOP_FWD_PAIR = 27
     FLOP_BWD_PAIR = 68
 
     def contributor_work(self, iterations_only: bool = False):
         """Sum over pixels of contributor counts, one entry per timed render."""
         return [int(s.sum().item()) for it, s in self.mapper.nc_snap if it or not iterations_only]
 
-    def roofline(self, peaks: dict):
+    @staticmethod
+    def kernel_source_hash(kernel: str) -> str:
+        """sha256 of the sources a kernel is built from (changes invalidate its ncu figures)."""
+        here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+        files = {"render_bwd": ["common.cuh", "render_tile.cuh", "render.cu"],
+                 "render_fwd": ["common.cuh", "render_tile.cuh", "render.cu"]}[kernel]
+        h = hashlib.sha256()
+        for f in files:
+            h.update(open(os.path.join(here, f), "rb").read())
+        return h.hexdigest()[:16]
+
+    @staticmethod
+    def profiled_traffic(kernel: str, profiles_dir: str):
+        """DRAM bytes per launch from the committed ncu summary of `kernel`, if its
+        source hash matches the current sources; else None."""
+        path = os.path.join(profiles_dir, f"{kernel}_room1M_1200x680.md")
+        try:
+            text = open(path).read()
+        except OSError:
+            return None
+        m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+);\s*source_sha256:\s*([0-9a-f]+)", text)
+        if not m or m.group(2) != FramePipeline.kernel_source_hash(kernel):
+            return None
+        return float(m.group(1))
+
+    def roofline(self, peaks: dict, profiles_dir: str | None = None):
         t = self.kernel_timer
         totals = {k: sum(t.durations(k)) for k in t.events}
         if not totals:
@@ -241,8 +274,10 @@ class FramePipeline:
         achieved = float(np.mean(flops / secs)) / 1e12
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 FLOP x max SM clock
+        traffic = self.profiled_traffic(name, profiles_dir) if profiles_dir else None
         return {"kernel": name, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)",
                 "share_of_step": round(totals[name] / sum(totals.values()), 3),
                 "avg_launch_ms": round(float(np.mean(durs)), 4)}
