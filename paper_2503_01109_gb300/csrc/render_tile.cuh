@@ -155,22 +155,48 @@ struct RenderBwdArgs {
   float *grad_rgb;   // [3][cap]
 };
 
-// Sum of 16 per-lane values over the warp by recursive halving: at each of the
-// five butterfly steps a lane keeps half of its values and adds the partner's
-// copies of them, so all 16 totals take 16 shuffles.  On return v[0] holds the
-// total of field (lane >> 1) (lanes 2f and 2f+1 hold the same total).
-__device__ __forceinline__ void warp_sum16(float (&v)[16], int lane) {
+// Sum of 10 per-lane values over the warp by recursive halving: at each
+// butterfly step a lane keeps half of its values (the list padded to an even
+// length with a zero) and adds the partner's copies of them, 10 -> 5 -> 3 -> 2 -> 1,
+// twelve shuffles in all.  On return v[0] holds the warp total of field
+// warp_sum10_field(lane), or of a padding slot where that is negative.
+__device__ __forceinline__ void warp_sum10(float (&v)[10], int lane) {
+  const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2;
 #pragma unroll
-  for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
-    const bool up = lane & bit;
+  for (int i = 0; i < 5; ++i) {
+    const float send = u16 ? v[i] : v[i + 5];
+    const float keep = u16 ? v[i + 5] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  v[5] = 0.f;
 #pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const float send = up ? v[i] : v[i + half];
-      const float keep = up ? v[i + half] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
-    }
+  for (int i = 0; i < 3; ++i) {
+    const float send = u8 ? v[i] : v[i + 3];
+    const float keep = u8 ? v[i + 3] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  v[3] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = u4 ? v[i] : v[i + 2];
+    const float keep = u4 ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const float send = u2 ? v[0] : v[1];
+    const float keep = u2 ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
   }
   v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Field whose warp total warp_sum10() leaves in `lane`, or -1 for a padding slot.
+__host__ __device__ __forceinline__ int warp_sum10_field(int lane) {
+  const int lc = (lane >> 1) & 1;
+  const int lb = ((lane >> 2) & 1) * 2 + lc;
+  const int la = ((lane >> 3) & 1) * 3 + lb;
+  if (lb >= 3 || la >= 5) return -1;
+  return ((lane >> 4) & 1) * 5 + la;
 }
 
 // Adjoint of global tile t by the whole CTA; `smem` holds TileSmem<BATCH>::bwd bytes.
@@ -195,8 +221,11 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
   const float4 *sp = a.splat + 2 * (int64_t)v * a.stride;
   const int64_t HW = (int64_t)cm.W * cm.H;
   const float *dc = a.dC + 3 * cm.pix_base;
-  float T[PX], gc0[PX], gc1[PX], gc2[PX], gd[PX], ga[PX];
-  float S0[PX], S1[PX], S2[PX], Sd[PX], Sa[PX];  // sums of gamma alpha T behind the current splat
+  // Per pixel: T (recovered front to back from T_final), the upstream gradient
+  // g = (dL/dC, dL/dD, dL/dA), and U = sum over the splats behind the current one
+  // of w_j (g . gamma_j), gamma_j = (colour_j, depth_j, 1): the term of dL/dalpha
+  // that the splats behind contribute, carried as one scalar.
+  float T[PX], gc0[PX], gc1[PX], gc2[PX], gd[PX], ga[PX], U[PX];
   int last[PX];
   int my_max = 0;
 #pragma unroll
@@ -204,8 +233,7 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
     const int py = py0 + q;
     T[q] = 1.f;
     last[q] = 0;
-    gc0[q] = gc1[q] = gc2[q] = gd[q] = ga[q] = 0.f;
-    S0[q] = S1[q] = S2[q] = Sd[q] = Sa[q] = 0.f;
+    gc0[q] = gc1[q] = gc2[q] = gd[q] = ga[q] = U[q] = 0.f;
     if (px < cm.W && py < cm.H) {
       const int64_t pix = (int64_t)py * cm.W + px;
       T[q] = a.t_final[cm.pix_base + pix];
@@ -224,6 +252,7 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
   const int lane = threadIdx.x & 31;
+  const int my_field = (lane & 1) ? -1 : warp_sum10_field(lane);
   if (lane == 0 && my_max > 0) atomicMax(&s_max_last, my_max);
   __syncthreads();
   const int max_last = s_max_last;
@@ -245,9 +274,15 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
       const int j = start + k;
       const float4 g0 = s_g0[k], g1 = s_g1[k];
       const float4 c = s_rgb[k];
-      float acc[16];
+      // Sums over this thread's pixels.  The power's derivatives are linear in
+      // e = dL/dalpha * G with coefficients (dx, dy, dx^2, dx dy, dy^2) and the
+      // splat's conic and opacity, so the pixels accumulate those moments and the
+      // flush below applies the per-splat factors once:
+      //   0..4: sum e dx, e dy, e dx^2, e dx dy, e dy^2;  5: sum e (= dL/dopacity);
+      //   6: sum dL/dD w;  7..9: sum dL/dC w.
+      float acc[NF];
 #pragma unroll
-      for (int f = 0; f < 16; ++f) acc[f] = 0.f;
+      for (int f = 0; f < NF; ++f) acc[f] = 0.f;
       bool contrib = false;
 #pragma unroll
       for (int q = 0; q < PX; ++q) {
@@ -264,37 +299,42 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
         T[q] *= rom;  // transmittance in front of this splat
         const float w = alpha * T[q];
         const float dot_gam = gc0[q] * c.x + gc1[q] * c.y + gc2[q] * c.z + gd[q] * g1.z + ga[q];
-        const float dot_S = gc0[q] * S0[q] + gc1[q] * S1[q] + gc2[q] * S2[q] + gd[q] * Sd[q] + ga[q] * Sa[q];
-        const float dalpha = T[q] * dot_gam - dot_S * rom;
-        S0[q] += c.x * w;
-        S1[q] += c.y * w;
-        S2[q] += c.z * w;
-        Sd[q] += g1.z * w;
-        Sa[q] += w;
+        const float dalpha = T[q] * dot_gam - U[q] * rom;
+        U[q] += w * dot_gam;
         acc[6] += gd[q] * w;
         acc[7] += gc0[q] * w;
         acc[8] += gc1[q] * w;
         acc[9] += gc2[q] * w;
-        if (raw < kAlphaMax) {
-          const float dp = dalpha * alpha;  // d alpha / d power = alpha (unclamped)
-          acc[0] -= dp * (g0.z * dx + g0.w * dy);
-          acc[1] -= dp * (g0.w * dx + g1.x * dy);
-          acc[2] -= 0.5f * dp * dx * dx;
-          acc[3] -= dp * dx * dy;
-          acc[4] -= 0.5f * dp * dy * dy;
-          acc[5] += dalpha * G;
+        if (raw < kAlphaMax) {  // d alpha / d power = alpha (unclamped)
+          const float e = dalpha * G;
+          const float ex = e * dx, ey = e * dy;
+          acc[0] += ex;
+          acc[1] += ey;
+          acc[2] += ex * dx;
+          acc[3] += ex * dy;
+          acc[4] += ey * dy;
+          acc[5] += e;
         }
       }
       if (__ballot_sync(0xffffffffu, contrib)) {
-        warp_sum16(acc, lane);
-        const int f = lane >> 1;
-        if ((lane & 1) == 0 && f < NF) atomicAdd(&s_acc[k][f], acc[0]);
+        warp_sum10(acc, lane);
+        if (my_field >= 0) atomicAdd(&s_acc[k][my_field], acc[0]);
       }
     }
     __syncthreads();
+    // dL/dmean = -o (A m), dL/d(a, b, c) = -o (m_xx / 2, m_xy, m_yy / 2) with A the
+    // conic [[a, b], [b, c]] and m the moments above; dL/dopacity = sum e.
     for (int e = threadIdx.x; e < cnt * NF; e += NT) {
       const int k = e / NF, f = e - k * NF;
-      const float val = s_acc[k][f];
+      float val = s_acc[k][f];
+      if (f < 5) {
+        const float4 g0 = s_g0[k];
+        const float cc = s_g1[k].x, o = s_g1[k].y;
+        if (f == 0) val = -o * (g0.z * val + g0.w * s_acc[k][1]);
+        else if (f == 1) val = -o * (g0.w * s_acc[k][0] + cc * val);
+        else if (f == 3) val = -o * val;
+        else val = -0.5f * o * val;
+      }
       if (val != 0.f) {
         const int id = s_id[k];
         if (f < 7)
