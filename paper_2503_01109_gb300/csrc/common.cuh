@@ -117,15 +117,34 @@ __device__ __forceinline__ int view_of_tile(const DevViews &vs, int t) {
   return v;
 }
 
-// Alpha of one (pixel, splat) evaluation, written with explicit rounding
-// intrinsics so that the forward and the backward kernels take bit-identical
-// skip / stop decisions.  Returns power; sets G = exp(power), alpha.
-__device__ __forceinline__ float splat_power(float mx, float my, float ca, float cb, float cc,
-                                             float px, float py, float &dx, float &dy) {
+// The blend evaluates each (pixel, splat) pair in the base-2 domain: the
+// staged copy of a splat carries its conic scaled by -log2(e)/2 (a, c) and
+// -log2(e) (b), so that power * log2(e) is one quadratic form and G = exp(power)
+// is one ex2.  Explicit rounding intrinsics make the forward and the adjoint
+// kernels take bit-identical skip decisions and alphas.
+constexpr float kLog2e = 1.44269504088896341f;
+constexpr float kLn2 = 0.693147180559945309f;
+
+__device__ __forceinline__ float4 stage_g0(float4 r0) {  // (mx, my, a, b) -> (mx, my, A, B)
+  return make_float4(r0.x, r0.y, __fmul_rn(-0.5f * kLog2e, r0.z), __fmul_rn(-kLog2e, r0.w));
+}
+__device__ __forceinline__ float4 stage_g1(float4 r1) {  // (c, o, z, thr) -> (C, o, z, thr)
+  return make_float4(__fmul_rn(-0.5f * kLog2e, r1.x), r1.y, r1.z, r1.w);
+}
+
+// power * log2(e) at pixel (px, py) for a staged conic (A, B, C); dx = mx - px, dy = my - py.
+__device__ __forceinline__ float splat_power2(float mx, float my, float A, float B, float C, float px, float py,
+                                              float &dx, float &dy) {
   dx = __fsub_rn(mx, px);
   dy = __fsub_rn(my, py);
-  float q = __fmaf_rn(ca, __fmul_rn(dx, dx), __fmul_rn(cc, __fmul_rn(dy, dy)));
-  return __fmaf_rn(-0.5f, q, -__fmul_rn(__fmul_rn(cb, dx), dy));
+  const float t = __fmul_rn(__fmul_rn(B, dx), dy);
+  return __fmaf_rn(A, __fmul_rn(dx, dx), __fmaf_rn(C, __fmul_rn(dy, dy), t));
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // Margin added to the opacity-aware support threshold 2 ln(255 o): it exceeds

@@ -80,46 +80,74 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int t, char
     for (int j = threadIdx.x; j < BATCH; j += NT) {
       if (base + j < n) {
         const int id = a.ids[range.x + base + j];
-        s_g0[j] = sp[2 * (int64_t)id];
-        s_g1[j] = sp[2 * (int64_t)id + 1];
+        s_g0[j] = stage_g0(sp[2 * (int64_t)id]);
+        s_g1[j] = stage_g1(sp[2 * (int64_t)id + 1]);
         s_rgb[j] = make_float4(a.rgb[id], a.rgb[a.cap + id], a.rgb[2 * a.cap + id], 0.f);
       }
     }
     __syncthreads();
     if (!all_done) {
       const int cnt = min(BATCH, n - base);
-      for (int k = 0; k < cnt; ++k) {
-        const float4 g0 = s_g0[k], g1 = s_g1[k];
-        bool any_live = false;
-#pragma unroll
-        for (int q = 0; q < PX; ++q) {
-          if (done[q]) continue;
-          any_live = true;
+      if constexpr (PX == 1) {
+        // one pixel per thread: the thread leaves the batch when its pixel stops
+        const float fpy = (float)py0;
+        for (int k = 0; k < cnt; ++k) {
+          const float4 g0 = s_g0[k], g1 = s_g1[k];
           float dx, dy;
-          const float power = splat_power(g0.x, g0.y, g0.z, g0.w, g1.x, fpx, (float)(py0 + q), dx, dy);
-          if (power > 0.f) continue;
-          const float alpha = fminf(kAlphaMax, __fmul_rn(g1.y, __expf(power)));
+          const float power2 = splat_power2(g0.x, g0.y, g0.z, g0.w, g1.x, fpx, fpy, dx, dy);
+          if (power2 > 0.f) continue;
+          const float alpha = fminf(kAlphaMax, __fmul_rn(g1.y, ex2_approx(power2)));
           if (alpha < kAlphaMin) continue;
-          const float Tn = T[q] * (1.f - alpha);
+          const float Tn = T[0] * (1.f - alpha);
           if (Tn < kTMin) {
-            done[q] = true;
-            continue;
+            done[0] = true;
+            break;
           }
-          const float w = alpha * T[q];
+          const float w = alpha * T[0];
           const float4 c = s_rgb[k];
-          C0[q] += c.x * w;
-          C1[q] += c.y * w;
-          C2[q] += c.z * w;
-          D[q] += g1.z * w;
-          A[q] += w;
-          T[q] = Tn;
-          last[q] = base + k + 1;
+          C0[0] += c.x * w;
+          C1[0] += c.y * w;
+          C2[0] += c.z * w;
+          D[0] += g1.z * w;
+          A[0] += w;
+          T[0] = Tn;
+          last[0] = base + k + 1;
         }
-        if (!any_live) break;
-      }
-      all_done = true;
+        all_done = done[0];
+      } else {
+        for (int k = 0; k < cnt; ++k) {
+          const float4 g0 = s_g0[k], g1 = s_g1[k];
+          bool any_live = false;
 #pragma unroll
-      for (int q = 0; q < PX; ++q) all_done = all_done && done[q];
+          for (int q = 0; q < PX; ++q) {
+            if (done[q]) continue;
+            any_live = true;
+            float dx, dy;
+            const float power2 = splat_power2(g0.x, g0.y, g0.z, g0.w, g1.x, fpx, (float)(py0 + q), dx, dy);
+            if (power2 > 0.f) continue;
+            const float alpha = fminf(kAlphaMax, __fmul_rn(g1.y, ex2_approx(power2)));
+            if (alpha < kAlphaMin) continue;
+            const float Tn = T[q] * (1.f - alpha);
+            if (Tn < kTMin) {
+              done[q] = true;
+              continue;
+            }
+            const float w = alpha * T[q];
+            const float4 c = s_rgb[k];
+            C0[q] += c.x * w;
+            C1[q] += c.y * w;
+            C2[q] += c.z * w;
+            D[q] += g1.z * w;
+            A[q] += w;
+            T[q] = Tn;
+            last[q] = base + k + 1;
+          }
+          if (!any_live) break;
+        }
+        all_done = true;
+#pragma unroll
+        for (int q = 0; q < PX; ++q) all_done = all_done && done[q];
+      }
     }
   }
   const int64_t HW = (int64_t)cm.W * cm.H;
@@ -253,6 +281,7 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
   for (int o = 16; o > 0; o >>= 1) my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
   const int lane = threadIdx.x & 31;
   const int my_field = (lane & 1) ? -1 : warp_sum10_field(lane);
+  const int warp_last = my_max;  // no pixel of this warp blends a splat at or past it
   if (lane == 0 && my_max > 0) atomicMax(&s_max_last, my_max);
   __syncthreads();
   const int max_last = s_max_last;
@@ -263,14 +292,14 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
       if (j < cnt) {
         const int id = a.ids[range.x + start + j];
         s_id[j] = id;
-        s_g0[j] = sp[2 * (int64_t)id];
-        s_g1[j] = sp[2 * (int64_t)id + 1];
+        s_g0[j] = stage_g0(sp[2 * (int64_t)id]);
+        s_g1[j] = stage_g1(sp[2 * (int64_t)id + 1]);
         s_rgb[j] = make_float4(a.rgb[id], a.rgb[a.cap + id], a.rgb[2 * a.cap + id], 0.f);
       }
     }
     for (int e = threadIdx.x; e < BATCH * NF; e += NT) (&s_acc[0][0])[e] = 0.f;
     __syncthreads();
-    for (int k = cnt - 1; k >= 0; --k) {
+    for (int k = min(cnt, warp_last - start) - 1; k >= 0; --k) {
       const int j = start + k;
       const float4 g0 = s_g0[k], g1 = s_g1[k];
       const float4 c = s_rgb[k];
@@ -288,9 +317,9 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
       for (int q = 0; q < PX; ++q) {
         if (j >= last[q]) continue;
         float dx, dy;
-        const float power = splat_power(g0.x, g0.y, g0.z, g0.w, g1.x, fpx, (float)(py0 + q), dx, dy);
-        if (power > 0.f) continue;
-        const float G = __expf(power);
+        const float power2 = splat_power2(g0.x, g0.y, g0.z, g0.w, g1.x, fpx, (float)(py0 + q), dx, dy);
+        if (power2 > 0.f) continue;
+        const float G = ex2_approx(power2);
         const float raw = __fmul_rn(g1.y, G);
         const float alpha = fminf(kAlphaMax, raw);
         if (alpha < kAlphaMin) continue;
@@ -322,16 +351,18 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
       }
     }
     __syncthreads();
-    // dL/dmean = -o (A m), dL/d(a, b, c) = -o (m_xx / 2, m_xy, m_yy / 2) with A the
-    // conic [[a, b], [b, c]] and m the moments above; dL/dopacity = sum e.
+    // dL/dmean = -o (Q m), dL/d(a, b, c) = -o (m_xx / 2, m_xy, m_yy / 2) with Q the
+    // conic [[a, b], [b, c]] and m the moments above; dL/dopacity = sum e.  The
+    // staged conic is (A, B, C) = -log2(e) (a/2, b, c/2), so -o Q m =
+    // o ln2 (2A m_x + B m_y, B m_x + 2C m_y).
     for (int e = threadIdx.x; e < cnt * NF; e += NT) {
       const int k = e / NF, f = e - k * NF;
       float val = s_acc[k][f];
       if (f < 5) {
         const float4 g0 = s_g0[k];
-        const float cc = s_g1[k].x, o = s_g1[k].y;
-        if (f == 0) val = -o * (g0.z * val + g0.w * s_acc[k][1]);
-        else if (f == 1) val = -o * (g0.w * s_acc[k][0] + cc * val);
+        const float cC = s_g1[k].x, o = s_g1[k].y;
+        if (f == 0) val = o * kLn2 * (2.f * g0.z * val + g0.w * s_acc[k][1]);
+        else if (f == 1) val = o * kLn2 * (g0.w * s_acc[k][0] + 2.f * cC * val);
         else if (f == 3) val = -o * val;
         else val = -0.5f * o * val;
       }
