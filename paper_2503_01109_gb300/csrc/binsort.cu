@@ -10,7 +10,7 @@
 //
 // The radix sort is LSD, 8-bit digits, reduce-then-scan: an upsweep histogram per
 // block chunk, a per-digit scan of the blocks' counts, and a downsweep that
-// ranks 2048-item tiles stably with warp match-any, reorders them in shared memory
+// ranks 2048-item tiles stably with per-bit warp ballots, reorders them in shared memory
 // and writes each digit run coalesced.  Item counts may live on the device (the
 // pair count), so the whole binning can be captured in a CUDA graph.
 #include "common.cuh"
@@ -39,9 +39,49 @@ __device__ __forceinline__ void block_chunk(uint32_t count, uint32_t nb, uint32_
   hi = (uint32_t)(h < count ? h : count);
 }
 
+// Lanes of the warp whose digit (the low `nbits` bits of d) equals this lane's,
+// among the valid lanes: one ballot per digit bit, so the cost does not depend on
+// how many distinct digits the warp holds.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid, int nbits) {
+  uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    if (b < nbits) {
+      const bool bit = (d >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bal : ~bal;
+    }
+  }
+  return peers;
+}
+
+// Exclusive scan over the values of a 256-thread block (one per thread) with
+// warp shuffles; `total` receives the sum.  s_warp holds 8 words; the caller
+// synchronises before s_warp is written again.
+__device__ __forceinline__ uint32_t block_scan256(uint32_t x, uint32_t *s_warp, uint32_t &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < kSortThreads / 32; ++w) {
+    const uint32_t t = s_warp[w];
+    before += (w < warp) ? t : 0u;
+    all += t;
+  }
+  total = all;
+  return before + incl - x;
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
                                                                 const int64_t *d_count, int64_t host_count,
-                                                                int64_t cap, int shift,
+                                                                int64_t cap, int shift, int nbits,
                                                                 uint32_t *__restrict__ counts) {
   __shared__ uint32_t hist[kSortThreads / 32][256];
   const int warp = threadIdx.x >> 5;
@@ -53,25 +93,25 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
   const int lane = threadIdx.x & 31;
   // kSortItems keys per thread in flight, warp-striped like the downsweep
   for (uint32_t tile = lo; tile < hi; tile += kSortTile) {
-    int d[kSortItems];
+    uint32_t d[kSortItems];
+    bool valid[kSortItems];
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
       const uint32_t i = tile + warp * (32 * kSortItems) + it * 32 + lane;
-      d[it] = i < hi ? (int)((keys[i] >> shift) & 255u) : 256;
+      valid[it] = i < hi;
+      d[it] = valid[it] ? (keys[i] >> shift) & 255u : 0u;
     }
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-      const uint32_t peers = __match_any_sync(0xffffffffu, d[it]);
-      if (d[it] < 256 && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][d[it]], (uint32_t)__popc(peers));
+      const uint32_t peers = digit_peers(d[it], valid[it], nbits);
+      if (valid[it] && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][d[it]], (uint32_t)__popc(peers));
     }
   }
   __syncthreads();
-  if (threadIdx.x < 256) {
-    uint32_t s = 0;
+  uint32_t s = 0;
 #pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) s += hist[w][threadIdx.x];
-    counts[threadIdx.x * gridDim.x + blockIdx.x] = s;  // digit-major
-  }
+  for (int w = 0; w < kSortThreads / 32; ++w) s += hist[w][threadIdx.x];
+  counts[threadIdx.x * gridDim.x + blockIdx.x] = s;  // digit-major
 }
 
 // Per-digit exclusive scan over the blocks' counts (one CTA per digit, nb <= 1024),
@@ -108,13 +148,13 @@ __global__ void __launch_bounds__(kScanThreads) k_digit_scan(uint32_t *__restric
 __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const int64_t *d_count,
-    int64_t host_count, int64_t cap, int shift, const uint32_t *__restrict__ offsets,
+    int64_t host_count, int64_t cap, int shift, int nbits, const uint32_t *__restrict__ offsets,
     const uint32_t *__restrict__ digit_total) {
   constexpr int W = kSortThreads / 32;
-  __shared__ uint32_t s_whist[W][256];
-  __shared__ uint32_t s_base[256];
-  __shared__ uint32_t s_prefix[256];
-  __shared__ uint32_t s_total[256];
+  __shared__ uint32_t s_whist[W][256];  // per warp and digit: count, then the warp's offset in the tile's run
+  __shared__ uint32_t s_base[256];      // output position of this block's next item of each digit
+  __shared__ uint32_t s_prefix[256];    // start of each digit's run in the reordered tile
+  __shared__ uint32_t s_warp[W];
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -122,74 +162,57 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
   const uint32_t count = item_count(d_count, host_count, cap);
   uint32_t lo, hi;
   block_chunk(count, gridDim.x, blockIdx.x, lo, hi);
-  // exclusive prefix of the digit totals, plus this block's offset inside each digit
-  if (threadIdx.x < 256) s_prefix[threadIdx.x] = digit_total[threadIdx.x];
-  __syncthreads();
-  for (int off = 1; off < 256; off <<= 1) {
-    uint32_t add = 0;
-    if (threadIdx.x < 256 && threadIdx.x >= off) add = s_prefix[threadIdx.x - off];
-    __syncthreads();
-    if (threadIdx.x < 256) s_prefix[threadIdx.x] += add;
-    __syncthreads();
+  // start of each digit in the output, plus this block's offset inside the digit
+  {
+    uint32_t all;
+    const uint32_t start = block_scan256(digit_total[threadIdx.x], s_warp, all);
+    s_base[threadIdx.x] = start + offsets[threadIdx.x * gridDim.x + blockIdx.x];
   }
-  if (threadIdx.x < 256)
-    s_base[threadIdx.x] = s_prefix[threadIdx.x] - digit_total[threadIdx.x] +
-                          offsets[threadIdx.x * gridDim.x + blockIdx.x];
   __syncthreads();
   for (uint32_t tile = lo; tile < hi; tile += kSortTile) {
     for (int d = lane; d < 256; d += 32) s_whist[warp][d] = 0;
     __syncwarp();
-    uint32_t k[kSortItems], v[kSortItems], local[kSortItems];
-    int dig[kSortItems];
+    uint32_t k[kSortItems], v[kSortItems], local[kSortItems], dig[kSortItems];
+    bool valid[kSortItems];
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
       const uint32_t idx = tile + warp * (32 * kSortItems) + it * 32 + lane;
-      const bool valid = idx < hi;
-      k[it] = valid ? keys_in[idx] : 0u;
-      v[it] = valid ? vals_in[idx] : 0u;
-      dig[it] = valid ? (int)((k[it] >> shift) & 255u) : 256;
-      const uint32_t peers = __match_any_sync(0xffffffffu, dig[it]);
+      valid[it] = idx < hi;
+      k[it] = valid[it] ? keys_in[idx] : 0u;
+      v[it] = valid[it] ? vals_in[idx] : 0u;
+      dig[it] = (k[it] >> shift) & 255u;
+    }
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const uint32_t peers = digit_peers(dig[it], valid[it], nbits);
       uint32_t base = 0;
-      if (valid) base = s_whist[warp][dig[it]];
+      if (valid[it]) base = s_whist[warp][dig[it]];
       __syncwarp();
-      if (valid && lane == __ffs(peers) - 1) s_whist[warp][dig[it]] = base + __popc(peers);
+      if (valid[it] && lane == __ffs(peers) - 1) s_whist[warp][dig[it]] = base + __popc(peers);
       __syncwarp();
       local[it] = base + __popc(peers & lt_mask);
     }
     __syncthreads();
-    if (threadIdx.x < 256) {
-      uint32_t run = 0;
+    uint32_t run = 0;  // this thread's digit: items in the tile
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        uint32_t c = s_whist[w][threadIdx.x];
-        s_whist[w][threadIdx.x] = run;
-        run += c;
-      }
-      s_total[threadIdx.x] = run;
-      s_prefix[threadIdx.x] = run;
+    for (int w = 0; w < W; ++w) {
+      const uint32_t c = s_whist[w][threadIdx.x];
+      s_whist[w][threadIdx.x] = run;
+      run += c;
     }
-    __syncthreads();
-    // exclusive scan of the 256 digit totals (Hillis-Steele on 256 threads)
-    for (int off = 1; off < 256; off <<= 1) {
-      uint32_t add = 0;
-      if (threadIdx.x < 256 && threadIdx.x >= off) add = s_prefix[threadIdx.x - off];
-      __syncthreads();
-      if (threadIdx.x < 256) s_prefix[threadIdx.x] += add;
-      __syncthreads();
-    }
-    if (threadIdx.x < 256) s_prefix[threadIdx.x] -= s_total[threadIdx.x];
+    uint32_t tile_items;
+    s_prefix[threadIdx.x] = block_scan256(run, s_warp, tile_items);
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-      if (dig[it] < 256) {
+      if (valid[it]) {
         const uint32_t pos = s_prefix[dig[it]] + s_whist[warp][dig[it]] + local[it];
         s_keys[pos] = k[it];
         s_vals[pos] = v[it];
       }
     }
     __syncthreads();
-    const uint32_t n_tile = min((uint32_t)kSortTile, hi - tile);
-    for (uint32_t i = threadIdx.x; i < n_tile; i += kSortThreads) {
+    for (uint32_t i = threadIdx.x; i < tile_items; i += kSortThreads) {
       const uint32_t key = s_keys[i];
       const uint32_t d = (key >> shift) & 255u;
       const uint32_t out = s_base[d] + (i - s_prefix[d]);
@@ -197,7 +220,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
       vals_out[out] = s_vals[i];
     }
     __syncthreads();
-    if (threadIdx.x < 256) s_base[threadIdx.x] += s_total[threadIdx.x];
+    s_base[threadIdx.x] += run;
     __syncthreads();
   }
 }
@@ -210,12 +233,13 @@ static fgs_status radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
   const int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
+    const int nbits = std::min(8, bits - shift);
     uint32_t *ki = (p & 1) ? k1 : k0, *vi = (p & 1) ? v1 : v0;
     uint32_t *ko = (p & 1) ? k0 : k1, *vo = (p & 1) ? v0 : v1;
-    k_radix_upsweep<<<nblocks, kSortThreads, 0, st>>>(ki, d_count, host_count, cap, shift, counts);
+    k_radix_upsweep<<<nblocks, kSortThreads, 0, st>>>(ki, d_count, host_count, cap, shift, nbits, counts);
     k_digit_scan<<<256, kScanThreads, 0, st>>>(counts, nblocks, digit_total);
     k_radix_downsweep<<<nblocks, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_count, host_count, cap, shift,
-                                                        counts, digit_total);
+                                                        nbits, counts, digit_total);
     count_launch(3);
   }
   FGS_CHECK_LAUNCH("radix_sort");

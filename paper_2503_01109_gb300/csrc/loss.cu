@@ -75,10 +75,10 @@ __global__ void k_scale_reg(const float *__restrict__ ls, int64_t cap, int64_t n
     gls[cap + i] += wn * g2 * s2;
     gls[2 * cap + i] += wn * (s3 > 0.f ? 1.f : 0.f) * s3;
   }
-  double s = (double)val * (double)wn;
+  float s = val * wn;  // warp sums in FP32, block and grid sums in FP64
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -99,6 +99,16 @@ struct AdamPlanes {
 
 __global__ void k_adam_step_incr(int32_t *d_step) { *d_step += 1; }
 
+__device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, float b1, float b2, float eps,
+                                         float lr, float c1, float c2) {
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  p -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
+// VEC: four consecutive elements per thread with 16-byte loads (every plane
+// 16-byte aligned); else one element per thread.
+template <bool VEC>
 __global__ void k_adam(AdamPlanes P, int64_t n, const int64_t *d_n, float b1, float b2, float eps, int32_t step,
                        const int32_t *d_step) {
   const int plane = blockIdx.y;
@@ -110,13 +120,27 @@ __global__ void k_adam(AdamPlanes P, int64_t n, const int64_t *d_n, float b1, fl
   const float *__restrict__ g = P.g[plane];
   float *__restrict__ m = P.m[plane];
   float *__restrict__ v = P.v[plane];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < live; i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  const int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * (VEC ? 4 : 1);
+  if (i0 >= live) return;
+  if (VEC && i0 + 4 <= live) {
+    float4 pp = *reinterpret_cast<const float4 *>(p + i0), gg = *reinterpret_cast<const float4 *>(g + i0);
+    float4 mm = *reinterpret_cast<const float4 *>(m + i0), vv = *reinterpret_cast<const float4 *>(v + i0);
+    adam_one(pp.x, gg.x, mm.x, vv.x, b1, b2, eps, lr, c1, c2);
+    adam_one(pp.y, gg.y, mm.y, vv.y, b1, b2, eps, lr, c1, c2);
+    adam_one(pp.z, gg.z, mm.z, vv.z, b1, b2, eps, lr, c1, c2);
+    adam_one(pp.w, gg.w, mm.w, vv.w, b1, b2, eps, lr, c1, c2);
+    *reinterpret_cast<float4 *>(p + i0) = pp;
+    *reinterpret_cast<float4 *>(m + i0) = mm;
+    *reinterpret_cast<float4 *>(v + i0) = vv;
+    return;
+  }
+  const int64_t i1 = VEC ? min(i0 + 4, live) : i0 + 1;
+  for (int64_t i = i0; i < i1; ++i) {
+    float pi = p[i], mi = m[i], vi = v[i];
+    adam_one(pi, g[i], mi, vi, b1, b2, eps, lr, c1, c2);
+    p[i] = pi;
     m[i] = mi;
     v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
   }
 }
 
@@ -218,9 +242,18 @@ extern "C" fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads
     k_adam_step_incr<<<1, 1, 0, st>>>(d_step);
     count_launch();
   }
-  const int64_t want = (params->n + 1023) / 1024;
-  const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 2 * num_sms()));
-  k_adam<<<dim3(bx, 14), 256, 0, st>>>(P, params->n, params->d_n, hp->beta1, hp->beta2, hp->eps, hp->step, d_step);
+  bool aligned = true;
+  for (int k = 0; k < 14; ++k)
+    aligned = aligned && ((reinterpret_cast<uintptr_t>(P.p[k]) | reinterpret_cast<uintptr_t>(P.g[k]) |
+                           reinterpret_cast<uintptr_t>(P.m[k]) | reinterpret_cast<uintptr_t>(P.v[k])) & 15) == 0;
+  const int64_t per_block = aligned ? 1024 : 256;
+  const unsigned bx = (unsigned)std::max<int64_t>(1, (params->n + per_block - 1) / per_block);
+  if (aligned)
+    k_adam<true><<<dim3(bx, 14), 256, 0, st>>>(P, params->n, params->d_n, hp->beta1, hp->beta2, hp->eps, hp->step,
+                                               d_step);
+  else
+    k_adam<false><<<dim3(bx, 14), 256, 0, st>>>(P, params->n, params->d_n, hp->beta1, hp->beta2, hp->eps, hp->step,
+                                                d_step);
   count_launch();
   FGS_CHECK_LAUNCH("fgs_adam");
   return FGS_OK;

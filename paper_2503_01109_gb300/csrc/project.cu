@@ -149,6 +149,19 @@ __global__ void k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict_
   if (i >= n || i >= live_count(d_n, n)) return;
   GaussLocal L;
   load_gaussian(g, i, L);
+  // The kernel only adds to the gradient planes: their old values are loaded
+  // here, together, so that their latencies overlap instead of each
+  // read-modify-write waiting for the one before it.
+  const int64_t c = out.cap;
+  const float old_logit = out.logits[i];
+  float old_mu[3], old_ls[3], old_q[4];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    old_mu[k] = out.means[k * c + i];
+    old_ls[k] = out.log_scales[k * c + i];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) old_q[k] = out.quats[k * c + i];
   float gmu[3] = {0.f, 0.f, 0.f};
   float GSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (symmetric, xx xy xz yy yz zz)
   float go = 0.f;
@@ -226,12 +239,11 @@ __global__ void k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict_
 #pragma unroll
     for (int k = 0; k < 3; ++k) gmu[k] += Rc[k] * gp0 + Rc[3 + k] * gp1 + Rc[6 + k] * gp2;
   }
-  const int64_t c = out.cap;
-  out.logits[i] += go * L.o * (1.f - L.o);
+  out.logits[i] = old_logit + go * L.o * (1.f - L.o);
   if (!any) return;
-  out.means[i] += gmu[0];
-  out.means[c + i] += gmu[1];
-  out.means[2 * c + i] += gmu[2];
+  out.means[i] = old_mu[0] + gmu[0];
+  out.means[c + i] = old_mu[1] + gmu[1];
+  out.means[2 * c + i] = old_mu[2] + gmu[2];
   // Sigma = M M^T, M = R diag(s): dL/dM = 2 GSig M
   float M[9];
 #pragma unroll
@@ -249,7 +261,7 @@ __global__ void k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict_
       gs += gm * L.R[3 * r + k];
       gR[3 * r + k] = gm * L.s[k];
     }
-    out.log_scales[k * c + i] += gs * L.s[k];
+    out.log_scales[k * c + i] = old_ls[k] + gs * L.s[k];
   }
   const float w = L.qn[0], qx = L.qn[1], qy = L.qn[2], qz = L.qn[3];
   float gq[4];
@@ -262,7 +274,7 @@ __global__ void k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict_
                  gR[5] * qy + gR[6] * qx + gR[7] * qy);
   const float dot = w * gq[0] + qx * gq[1] + qy * gq[2] + qz * gq[3];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) out.quats[k * c + i] += (gq[k] - L.qn[k] * dot) * L.qinv;
+  for (int k = 0; k < 4; ++k) out.quats[k * c + i] = old_q[k] + (gq[k] - L.qn[k] * dot) * L.qinv;
 }
 
 fgs_status launch_project_bwd(const fgs_gaussians *g, const DevViews &vs, const int32_t *radius,
