@@ -128,8 +128,11 @@ constexpr float kLn2 = 0.693147180559945309f;
 __device__ __forceinline__ float4 stage_g0(float4 r0) {  // (mx, my, a, b) -> (mx, my, A, B)
   return make_float4(r0.x, r0.y, __fmul_rn(-0.5f * kLog2e, r0.z), __fmul_rn(-kLog2e, r0.w));
 }
-__device__ __forceinline__ float4 stage_g1(float4 r1) {  // (c, o, z, thr) -> (C, o, z, thr)
-  return make_float4(__fmul_rn(-0.5f * kLog2e, r1.x), r1.y, r1.z, r1.w);
+// (c, o, z, thr) -> (C, o, z, P) with P = -log2(255 o): alpha = o 2^power2 falls
+// below 1/255 exactly where power2 < P, so the blend skips those pairs before
+// the ex2 (the forward and the adjoint share the test, hence the decisions).
+__device__ __forceinline__ float4 stage_g1(float4 r1) {
+  return make_float4(__fmul_rn(-0.5f * kLog2e, r1.x), r1.y, r1.z, -log2f(__fmul_rn(255.f, r1.y)));
 }
 
 // power * log2(e) at pixel (px, py) for a staged conic (A, B, C); dx = mx - px, dy = my - py.

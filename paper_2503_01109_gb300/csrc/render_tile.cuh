@@ -37,6 +37,24 @@ struct PxPerThread {
   static constexpr int bwd = (TW * TH >= 256) ? FGS_BWD_PX : 2;
 };
 
+// Pixel owned by a thread: each warp covers a block kWarpW pixels wide and
+// (32 / kWarpW) * PX rows high, so that the 32 lanes' pixels are close together
+// and stop blending after similar numbers of splats; the blocks tile the tile
+// row by row.  Writes the thread's column and first row (tile coordinates).
+#ifndef FGS_WARP_W
+#define FGS_WARP_W 8
+#endif
+template <int TW, int TH, int PX>
+__device__ __forceinline__ void thread_pixel(int &x, int &y0) {
+  constexpr int WW = TW < FGS_WARP_W ? TW : FGS_WARP_W;
+  constexpr int WH = (32 / WW) * PX;
+  static_assert(TW % WW == 0 && TH % WH == 0 && (TW / WW) * (TH / WH) * 32 * PX == TW * TH,
+                "warp blocks must tile the tile");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  x = (warp % (TW / WW)) * WW + lane % WW;
+  y0 = (warp / (TW / WW)) * WH + (lane / WW) * PX;
+}
+
 // Shared memory of one tile pass (bytes): forward / adjoint.
 template <int BATCH>
 struct TileSmem {
@@ -56,8 +74,10 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int t, char
   const DevCam &cm = a.vs.cam[v];
   const int lt = t - cm.tile_base;
   const int ty = lt / cm.tiles_x, tx = lt - ty * cm.tiles_x;
-  const int px = tx * TW + (threadIdx.x % TW);
-  const int py0 = ty * TH + (threadIdx.x / TW) * PX;
+  int lx, ly0;
+  thread_pixel<TW, TH, PX>(lx, ly0);
+  const int px = tx * TW + lx;
+  const int py0 = ty * TH + ly0;
   const float fpx = (float)px;
   const int2 range = a.ranges[t];
   const int n = range.y - range.x;
@@ -95,9 +115,8 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int t, char
           const float4 g0 = s_g0[k], g1 = s_g1[k];
           float dx, dy;
           const float power2 = splat_power2(g0.x, g0.y, g0.z, g0.w, g1.x, fpx, fpy, dx, dy);
-          if (power2 > 0.f) continue;
+          if (power2 > 0.f || power2 < g1.w) continue;  // g1.w: alpha < 1/255 below it
           const float alpha = fminf(kAlphaMax, __fmul_rn(g1.y, ex2_approx(power2)));
-          if (alpha < kAlphaMin) continue;
           const float Tn = T[0] * (1.f - alpha);
           if (Tn < kTMin) {
             done[0] = true;
@@ -124,9 +143,8 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int t, char
             any_live = true;
             float dx, dy;
             const float power2 = splat_power2(g0.x, g0.y, g0.z, g0.w, g1.x, fpx, (float)(py0 + q), dx, dy);
-            if (power2 > 0.f) continue;
+            if (power2 > 0.f || power2 < g1.w) continue;
             const float alpha = fminf(kAlphaMax, __fmul_rn(g1.y, ex2_approx(power2)));
-            if (alpha < kAlphaMin) continue;
             const float Tn = T[q] * (1.f - alpha);
             if (Tn < kTMin) {
               done[q] = true;
@@ -242,8 +260,10 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
   const DevCam &cm = a.vs.cam[v];
   const int lt = t - cm.tile_base;
   const int ty = lt / cm.tiles_x, tx = lt - ty * cm.tiles_x;
-  const int px = tx * TW + (threadIdx.x % TW);
-  const int py0 = ty * TH + (threadIdx.x / TW) * PX;
+  int lx, ly0;
+  thread_pixel<TW, TH, PX>(lx, ly0);
+  const int px = tx * TW + lx;
+  const int py0 = ty * TH + ly0;
   const float fpx = (float)px;
   const int2 range = a.ranges[t];
   const float4 *sp = a.splat + 2 * (int64_t)v * a.stride;
@@ -318,11 +338,10 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
         if (j >= last[q]) continue;
         float dx, dy;
         const float power2 = splat_power2(g0.x, g0.y, g0.z, g0.w, g1.x, fpx, (float)(py0 + q), dx, dy);
-        if (power2 > 0.f) continue;
+        if (power2 > 0.f || power2 < g1.w) continue;
         const float G = ex2_approx(power2);
         const float raw = __fmul_rn(g1.y, G);
         const float alpha = fminf(kAlphaMax, raw);
-        if (alpha < kAlphaMin) continue;
         contrib = true;
         const float rom = __fdividef(1.f, 1.f - alpha);
         T[q] *= rom;  // transmittance in front of this splat
