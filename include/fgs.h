@@ -137,17 +137,22 @@ int64_t fgs_num_tiles(const fgs_camera *cams, int32_t n_views, fgs_tiling tiling
  *   tile_keys[k], ids[k] for k < *d_num_pairs: global tile index and Gaussian id,
  *   sorted by (tile, depth, id).  tile_ranges[2*t], [2*t+1] = [start, end) of tile t
  *   (0, 0 for an empty tile).
- * ws/ws_bytes: scratch of at least fgs_bin_sort_workspace_size(n_views*stride,
- *   pair_capacity) bytes, 256-byte aligned.
- * Device errors: FGS_DEV_PAIR_OVERFLOW when the pair count exceeds pair_capacity;
- *   *d_num_pairs then holds the required count and the lists are not valid.
- * err: INVALID_ARGUMENT for small workspace, pair_capacity outside 1..2^31-1. */
+ * ws/ws_bytes: scratch of at least fgs_bin_sort_workspace_size(cams, n_views,
+ *   tiling, n_views*stride, pair_capacity) bytes, 256-byte aligned.
+ * Device errors: FGS_DEV_PAIR_OVERFLOW when the pair count, or the count of
+ *   (record, tile row) entries of the rows' lists, exceeds pair_capacity;
+ *   *d_num_pairs then holds the required count (for the rows: a lower bound) and
+ *   the lists are not valid.
+ * err: INVALID_ARGUMENT for small workspace, pair_capacity outside 1..2^31-1, more
+ *   than 4096 tile rows over all views. */
 fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const fgs_camera *cams,
                         int32_t n_views, fgs_tiling tiling, void *ws, size_t ws_bytes,
                         uint32_t *tile_keys, int32_t *ids, int64_t pair_capacity,
                         int32_t *tile_ranges, int64_t *d_num_pairs, int32_t *d_status,
                         void *stream);
-size_t fgs_bin_sort_workspace_size(int64_t n_records, int64_t pair_capacity);
+/* Workspace of fgs_bin_sort for this view set and tiling (0 on bad input). */
+size_t fgs_bin_sort_workspace_size(const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
+                                   int64_t n_records, int64_t pair_capacity);
 
 /* ---------------------------------------------------------------------------------
  * fgs_render_fwd -- alpha blending of eq1 for the three readings the paper gives

@@ -1,18 +1,19 @@
 // binsort.cu -- tile binning and depth ordering of the splats eq1 blends front to back.
 //
 // The required order of every tile's list is (float32 depth bits, Gaussian id).
-// Instead of radix-sorting 64-bit (tile | depth) keys of every (tile, Gaussian)
-// pair, the visible records are compacted in record order and sorted by depth
-// ONCE (stable, so equal depths stay in id order), pairs are emitted in that
-// order, and a stable sort on
-// the tile index alone (a few bits, one or two 8-bit passes) finishes the job:
-// within a tile the pairs keep their emission order, which is depth then id.
+// The visible records are compacted in record order and sorted by depth once
+// (stable LSD radix, so equal depths stay in id order; with several views, one
+// more stable pass on the view index keeps each view's records together).  The
+// (tile, Gaussian) pairs are then never sorted: two stable partitions -- records
+// into the tile rows their rect spans, then each row's records into the row's
+// tiles their support ellipse reaches -- write every pair straight to its place
+// in (tile, depth, id) order.
 //
 // The radix sort is LSD, 8-bit digits, reduce-then-scan: an upsweep histogram per
 // block chunk, a per-digit scan of the blocks' counts, and a downsweep that
-// ranks 2048-item tiles stably with per-bit warp ballots, reorders them in shared memory
-// and writes each digit run coalesced.  Item counts may live on the device (the
-// pair count), so the whole binning can be captured in a CUDA graph.
+// ranks 2048-item tiles stably with per-bit warp ballots, reorders them in shared
+// memory and writes each digit run coalesced.  Every count the kernels need lives
+// on the device, so the whole binning can be captured in a CUDA graph.
 #include "common.cuh"
 
 namespace fgs {
@@ -344,260 +345,551 @@ __global__ void __launch_bounds__(kScanBlock) k_vis_scatter(const float4 *__rest
 }
 
 
-// A visible record prepared by its own lane (box and support), so that a warp
-// walking its 32 records one after the other only broadcasts them.
-struct PreparedRecord {
-  uint32_t rec, x0, y0, x1, y1;
-  SupportSplat sp;
+// ---------------------------------------------------------------------------------
+// Tile lists by row partition.
+//
+// The depth-sorted visible records are partitioned twice, each time stably, so
+// that every list keeps depth order without a sort of the pairs:
+//   rows:  the records whose rect spans tile row g, for every global row g
+//          (views after one another), in depth order;
+//   tiles: each row's list cut into chunks of kTileChunk entries; within its row a
+//          record keeps the rect's tiles that its support ellipse reaches, and a
+//          chunk writes its pairs of tile x after those of the row's earlier
+//          chunks: positions come from per-(chunk, x) counts scanned over the
+//          row's chunks, per-warp counts scanned over the chunk's warps and
+//          ballot ranks within a warp.
+// Rows ordered by view then y, tiles of a row by x: the pairs come out sorted by
+// global tile, then depth, then id, and each step is a counting pass, a scan and
+// a writing pass over small per-chunk tables.
+
+constexpr int kRecChunk = 256;    // records per chunk of the row partition
+constexpr int kTileChunk = 512;   // row-list entries per chunk of the tile partition
+constexpr int kMaxRows = 4096;    // global tile rows (shared-memory row histogram)
+constexpr int kPartGrid = 8;      // persistent CTAs per SM of the partition kernels
+
+struct RowGeom {
+  int n_views, n_rows, tx_max;
+  int64_t stride;
+  int row_base[FGS_MAX_VIEWS + 1];  // first global row of each view
+  int tiles_x[FGS_MAX_VIEWS];
+  int tile_base[FGS_MAX_VIEWS];
 };
 
-__device__ __forceinline__ PreparedRecord prepare_record(const float4 *__restrict__ splat,
-                                                         const uint2 *__restrict__ rect, uint32_t rec, bool valid) {
-  PreparedRecord p{};
-  if (!valid) {
-    p.x0 = 1;  // empty box
-    return p;
-  }
+__device__ __forceinline__ int view_of_row(const RowGeom &G, int g) {
+  int v = 0;
+#pragma unroll 1
+  while (v + 1 < G.n_views && g >= G.row_base[v + 1]) ++v;
+  return v;
+}
+
+__device__ __forceinline__ void record_rows(const RowGeom &G, const uint2 *__restrict__ rect, uint32_t rec, int &g0,
+                                            int &g1) {
+  const int v = (int)(rec / (uint64_t)G.stride);
   const uint2 rc = rect[rec];
-  p.rec = rec;
-  p.x0 = rc.x & 0xFFFFu;
-  p.y0 = rc.x >> 16;
-  p.x1 = rc.y & 0xFFFFu;
-  p.y1 = rc.y >> 16;
-  p.sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
-  return p;
+  g0 = G.row_base[v] + (int)(rc.x >> 16);
+  g1 = G.row_base[v] + (int)(rc.y >> 16);
 }
 
-__device__ __forceinline__ PreparedRecord shfl_record(const PreparedRecord &p, int src) {
-  PreparedRecord q;
-  q.rec = __shfl_sync(0xffffffffu, p.rec, src);
-  q.x0 = __shfl_sync(0xffffffffu, p.x0, src);
-  q.y0 = __shfl_sync(0xffffffffu, p.y0, src);
-  q.x1 = __shfl_sync(0xffffffffu, p.x1, src);
-  q.y1 = __shfl_sync(0xffffffffu, p.y1, src);
-  q.sp.mx = __shfl_sync(0xffffffffu, p.sp.mx, src);
-  q.sp.my = __shfl_sync(0xffffffffu, p.sp.my, src);
-  q.sp.a = __shfl_sync(0xffffffffu, p.sp.a, src);
-  q.sp.b = __shfl_sync(0xffffffffu, p.sp.b, src);
-  q.sp.c = __shfl_sync(0xffffffffu, p.sp.c, src);
-  q.sp.thr = __shfl_sync(0xffffffffu, p.sp.thr, src);
-  q.sp.sx = __shfl_sync(0xffffffffu, p.sp.sx, src);
-  q.sp.sy = __shfl_sync(0xffffffffu, p.sp.sy, src);
-  return q;
-}
-
-// Tiles per sorted visible record (those of its box that its opacity-aware
-// ellipse reaches), then per-block sums for the scan.  A warp counts its 32
-// records one after the other, its lanes testing 32 of the record's tiles at a
-// time, so large footprints do not serialise one thread.
-__global__ void __launch_bounds__(kScanBlock) k_counts_blocksum(const float4 *__restrict__ splat,
-                                                                const uint32_t *__restrict__ svals,
-                                                                const uint2 *__restrict__ rect,
-                                                                const int64_t *__restrict__ d_vis, int tw, int th,
-                                                                uint32_t *__restrict__ cnt,
-                                                                uint32_t *__restrict__ bsum) {
-  __shared__ uint32_t red[kScanBlock / 32];
-  const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
-  const int64_t R = *d_vis;
-  const int lane = threadIdx.x & 31;
-  const PreparedRecord mine = prepare_record(splat, rect, j < R ? svals[j] : 0u, j < R);
-  uint32_t c = 0;
-  uint32_t pending = __ballot_sync(0xffffffffu, j < R && mine.x0 <= mine.x1 && mine.y0 <= mine.y1);
-  while (pending) {
-    const int src = __ffs(pending) - 1;
-    pending &= pending - 1;
-    const PreparedRecord pr = shfl_record(mine, src);
-    const uint32_t x0 = pr.x0, y0 = pr.y0, x1 = pr.x1, y1 = pr.y1;
-    const SupportSplat &sp = pr.sp;
-    uint32_t n = 0;
-    {
-      const uint32_t w = x1 - x0 + 1u, box = w * (y1 - y0 + 1u);
-      for (uint32_t q0 = 0; q0 < box; q0 += 32) {
-        const uint32_t q = q0 + lane;
-        bool keep = false;
-        if (q < box) {
-          const uint32_t dy = q / w, dx = q - dy * w;
-          keep = tile_in_support(sp, (int)(x0 + dx), (int)(y0 + dy), tw, th);
-        }
-        n += __popc(__ballot_sync(0xffffffffu, keep));
-      }
-    }
-    if (lane == src) c = n;
-  }
-  if (j < R) cnt[j] = c;
-  uint32_t s = c;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    uint32_t t = red[threadIdx.x];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = t;
-  }
-}
-
-// Exclusive scan of the block sums with 64-bit total; the total is the pair count.
-__global__ void __launch_bounds__(kScanThreads) k_scan_bsum(uint32_t *__restrict__ bsum, int nb,
-                                                            int64_t *__restrict__ d_num_pairs,
-                                                            int64_t pair_cap, int32_t *__restrict__ d_status,
-                                                            int64_t *__restrict__ d_sort_count) {
-  __shared__ unsigned long long part[kScanThreads];
-  const int per = (nb + kScanThreads - 1) / kScanThreads;
-  const int lo = threadIdx.x * per, hi = min(nb, lo + per);
+// Exclusive scan of n counts in place by one CTA of 1024 threads (a consecutive
+// slice per thread); every thread gets the total.
+__device__ uint64_t cta_scan_inplace(uint32_t *__restrict__ a, int64_t n, unsigned long long *part) {
+  const int64_t per = (n + 1023) / 1024;
+  const int64_t lo = threadIdx.x * per, hi = min(n, lo + per);
   unsigned long long s = 0;
-  for (int i = lo; i < hi; ++i) s += bsum[i];
+  for (int64_t i = lo; i < hi; ++i) s += a[i];
   part[threadIdx.x] = s;
   __syncthreads();
-  for (int off = 1; off < kScanThreads; off <<= 1) {
-    unsigned long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
+  for (int off = 1; off < 1024; off <<= 1) {
+    const unsigned long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned long long run = part[threadIdx.x] - s;
+  for (int64_t i = lo; i < hi; ++i) {
+    const uint32_t v = a[i];
+    a[i] = (uint32_t)run;
+    run += v;
+  }
+  const uint64_t total = part[1023];
+  __syncthreads();
+  return total;
+}
+
+// Rows, counting pass: per record chunk b, the number of its records spanning each
+// global row, into rowcnt[g * nb_cap + b].
+__global__ void __launch_bounds__(kRecChunk) k_row_count(RowGeom G, const uint32_t *__restrict__ srec,
+                                                         const uint2 *__restrict__ rect,
+                                                         const int64_t *__restrict__ d_vis, int64_t nb_cap,
+                                                         uint32_t *__restrict__ rowcnt) {
+  __shared__ uint32_t s_rows[kMaxRows];
+  const int64_t R = *d_vis;
+  const int64_t nb = (R + kRecChunk - 1) / kRecChunk;
+  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    for (int g = threadIdx.x; g < G.n_rows; g += kRecChunk) s_rows[g] = 0;
+    __syncthreads();
+    const int64_t j = b * kRecChunk + threadIdx.x;
+    if (j < R) {
+      int g0, g1;
+      record_rows(G, rect, srec[j], g0, g1);
+      for (int g = g0; g <= g1; ++g) atomicAdd(&s_rows[g], 1u);
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < G.n_rows; g += kRecChunk) rowcnt[(int64_t)g * nb_cap + b] = s_rows[g];
+    __syncthreads();
+  }
+}
+
+// Rows, scan: one CTA per row turns its chunk counts into exclusive offsets and
+// writes the row's total.
+__global__ void __launch_bounds__(1024) k_row_scan(const int64_t *__restrict__ d_vis, int64_t nb_cap,
+                                                   uint32_t *__restrict__ rowcnt, uint32_t *__restrict__ rowtot) {
+  __shared__ unsigned long long part[1024];
+  const int64_t nb = (*d_vis + kRecChunk - 1) / kRecChunk;
+  const uint64_t total = cta_scan_inplace(rowcnt + (int64_t)blockIdx.x * nb_cap, nb, part);
+  if (threadIdx.x == 0) rowtot[blockIdx.x] = (uint32_t)min(total, (uint64_t)0xFFFFFFFFu);
+}
+
+// Rows, starts and the tile chunk table (one CTA): row_start[g] (exclusive scan of
+// the row totals, total entries at [n_rows]); on overflow of the row-list
+// capacity the status bit is set and every row is left empty.  chunk_start[g]:
+// first tile chunk of row g, chunk_row[c]: row of chunk c, *d_nchunks: count.
+__global__ void __launch_bounds__(1024) k_row_starts(RowGeom G, const uint32_t *__restrict__ rowtot,
+                                                     int64_t row_cap, uint32_t *__restrict__ row_start,
+                                                     uint32_t *__restrict__ chunk_start,
+                                                     uint32_t *__restrict__ chunk_row, int64_t chunk_cap,
+                                                     int64_t *__restrict__ d_nchunks, int32_t *__restrict__ d_status,
+                                                     int64_t *__restrict__ d_num_pairs,
+                                                     int64_t *__restrict__ d_sort_count) {
+  __shared__ unsigned long long part[1024];
+  __shared__ int s_over;
+  const int NR = G.n_rows;
+  for (int g = threadIdx.x; g < NR; g += 1024) row_start[g] = rowtot[g];
+  __syncthreads();
+  const uint64_t E = cta_scan_inplace(row_start, NR, part);
+  if (threadIdx.x == 0) {
+    s_over = E > (uint64_t)row_cap;
+    row_start[NR] = s_over ? 0u : (uint32_t)E;
+    // -1 marks the overflow for k_tile_row_starts, which sets the final count
+    *d_sort_count = s_over ? -1 : 0;
+    if (s_over) {
+      if (d_status) atomicOr(d_status, FGS_DEV_PAIR_OVERFLOW);
+      *d_num_pairs = (int64_t)E;  // a lower bound of the pairs needed
+    }
+  }
+  __syncthreads();
+  const bool over = s_over;
+  for (int g = threadIdx.x; g < NR; g += 1024) {
+    if (over) row_start[g] = 0;
+    chunk_start[g] = over ? 0u : (rowtot[g] + kTileChunk - 1) / kTileChunk;
+  }
+  __syncthreads();
+  const uint64_t NC = cta_scan_inplace(chunk_start, NR, part);
+  if (threadIdx.x == 0) {
+    chunk_start[NR] = (uint32_t)NC;
+    *d_nchunks = (int64_t)min(NC, (uint64_t)chunk_cap);
+  }
+  __syncthreads();
+  const int64_t nc = (int64_t)min(NC, (uint64_t)chunk_cap);
+  for (int64_t c = threadIdx.x; c < nc; c += 1024) {  // row of chunk c: last g with chunk_start[g] <= c
+    int lo = 0, hi = NR - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (chunk_start[mid] <= (uint64_t)c) lo = mid;
+      else hi = mid - 1;
+    }
+    chunk_row[c] = (uint32_t)lo;
+  }
+}
+
+// Rows, writing pass: record j (depth rank) goes to rowlist at row_start[g] + the
+// offset of its chunk in row g + its rank among the chunk's earlier records that
+// span g (warp prefix in shared memory, ballot rank inside the warp).
+__global__ void __launch_bounds__(kRecChunk) k_row_emit(RowGeom G, const uint32_t *__restrict__ srec,
+                                                        const uint2 *__restrict__ rect,
+                                                        const int64_t *__restrict__ d_vis, int64_t nb_cap,
+                                                        const uint32_t *__restrict__ rowcnt,
+                                                        const uint32_t *__restrict__ row_start,
+                                                        uint32_t *__restrict__ rowlist) {
+  constexpr int NW = kRecChunk / 32;
+  __shared__ uint32_t s_wc[NW][32];
+  __shared__ int s_lo, s_hi;
+  const int64_t R = *d_vis;
+  const int64_t nb = (R + kRecChunk - 1) / kRecChunk;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  if (row_start[G.n_rows] == 0) return;  // no entries, or the row lists overflowed
+  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    if (threadIdx.x == 0) {
+      s_lo = 0x7FFFFFFF;
+      s_hi = -1;
+    }
+    __syncthreads();
+    const int64_t j = b * kRecChunk + threadIdx.x;
+    int g0 = 0, g1 = -1;
+    if (j < R) record_rows(G, rect, srec[j], g0, g1);
+    if (g0 <= g1) {
+      atomicMin(&s_lo, g0);
+      atomicMax(&s_hi, g1);
+    }
+    __syncthreads();
+    const int lo = s_lo, hi = s_hi;
+    for (int gb = lo; gb <= hi; gb += 32) {
+      // rows gb .. gb + 31 this record spans, as bits
+      uint32_t m = 0;
+      if (g0 <= g1 && g1 >= gb && g0 < gb + 32) {
+        const int a = max(g0, gb) - gb, e = min(g1, gb + 31) - gb;
+        m = (e == 31 ? 0xFFFFFFFFu : ((1u << (e + 1)) - 1u)) & ~((1u << a) - 1u);
+      }
+      uint32_t mine = 0;
+#pragma unroll 4
+      for (int bit = 0; bit < 32; ++bit) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, (m >> bit) & 1u);
+        if (lane == bit) mine = __popc(bal);
+      }
+      s_wc[warp][lane] = mine;
+      __syncthreads();
+      uint32_t before = 0;  // this lane's row: records of the chunk's earlier warps
+      for (int w = 0; w < warp; ++w) before += s_wc[w][lane];
+#pragma unroll 4
+      for (int bit = 0; bit < 32; ++bit) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, (m >> bit) & 1u);
+        const uint32_t pre = __shfl_sync(0xffffffffu, before, bit);
+        if ((m >> bit) & 1u) {
+          const int g = gb + bit;
+          const uint32_t pos = row_start[g] + rowcnt[(int64_t)g * nb_cap + b] + pre + __popc(bal & lt);
+          rowlist[pos] = (uint32_t)j;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+struct TileChunk {
+  int g, v, y, tx;
+  uint32_t e0, e1;
+};
+
+__device__ __forceinline__ TileChunk tile_chunk(const RowGeom &G, const uint32_t *__restrict__ chunk_row,
+                                                const uint32_t *__restrict__ chunk_start,
+                                                const uint32_t *__restrict__ row_start, int64_t c) {
+  TileChunk k;
+  k.g = (int)chunk_row[c];
+  k.v = view_of_row(G, k.g);
+  k.y = k.g - G.row_base[k.v];
+  k.tx = G.tiles_x[k.v];
+  k.e0 = row_start[k.g] + (uint32_t)(c - chunk_start[k.g]) * kTileChunk;
+  k.e1 = min(k.e0 + kTileChunk, row_start[k.g + 1]);
+  return k;
+}
+
+// Tiles, counting pass: per chunk c of a row list, the number of its records that
+// keep tile x of the row, into tcnt[c * tx_max + x].
+__global__ void __launch_bounds__(kTileChunk) k_tile_count(RowGeom G, const float4 *__restrict__ splat,
+                                                           const uint32_t *__restrict__ srec,
+                                                           const uint2 *__restrict__ rect, int tw, int th,
+                                                           const uint32_t *__restrict__ rowlist,
+                                                           const uint32_t *__restrict__ row_start,
+                                                           const uint32_t *__restrict__ chunk_start,
+                                                           const uint32_t *__restrict__ chunk_row,
+                                                           const int64_t *__restrict__ d_nchunks,
+                                                           uint32_t *__restrict__ tcnt) {
+  extern __shared__ uint32_t s_cnt[];  // [tx_max]
+  const int64_t NC = *d_nchunks;
+  for (int64_t c = blockIdx.x; c < NC; c += gridDim.x) {
+    const TileChunk k = tile_chunk(G, chunk_row, chunk_start, row_start, c);
+    for (int x = threadIdx.x; x < k.tx; x += kTileChunk) s_cnt[x] = 0;
+    __syncthreads();
+    const uint32_t e = k.e0 + threadIdx.x;
+    if (e < k.e1) {
+      const uint32_t rec = srec[rowlist[e]];
+      const uint2 rc = rect[rec];
+      const SupportSplat sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
+      const int x1 = (int)(rc.y & 0xFFFFu);
+      for (int x = (int)(rc.x & 0xFFFFu); x <= x1; ++x)
+        if (tile_in_support(sp, x, k.y, tw, th)) atomicAdd(&s_cnt[x], 1u);
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < k.tx; x += kTileChunk) tcnt[c * G.tx_max + x] = s_cnt[x];
+    __syncthreads();
+  }
+}
+
+// Tiles, scan over chunks: one CTA per row; tpre[c][x] = pairs of tile x in the
+// row's chunks before c, ttot[g][x] = the tile's total, rowp[g] = the row's total.
+__global__ void __launch_bounds__(256) k_tile_chunk_scan(RowGeom G, const uint32_t *__restrict__ chunk_start,
+                                                         const uint32_t *__restrict__ tcnt,
+                                                         uint32_t *__restrict__ tpre, uint32_t *__restrict__ ttot,
+                                                         unsigned long long *__restrict__ rowp) {
+  __shared__ unsigned long long red[8];
+  const int g = blockIdx.x;
+  const int v = view_of_row(G, g);
+  const int tx = G.tiles_x[v];
+  const uint32_t c0 = chunk_start[g], c1 = chunk_start[g + 1];
+  unsigned long long row_sum = 0;
+  for (int x = threadIdx.x; x < tx; x += 256) {
+    uint32_t run = 0;
+#pragma unroll 8
+    for (uint32_t c = c0; c < c1; ++c) {
+      const uint32_t t = tcnt[(int64_t)c * G.tx_max + x];
+      tpre[(int64_t)c * G.tx_max + x] = run;
+      run += t;
+    }
+    ttot[(int64_t)g * G.tx_max + x] = run;
+    row_sum += run;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) row_sum += __shfl_xor_sync(0xffffffffu, row_sum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = row_sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    rowp[g] = t;
+  }
+}
+
+// Tiles, row starts (one CTA): exclusive scan of the rows' pair totals; the total
+// is the pair count, checked against the capacity.
+__global__ void __launch_bounds__(1024) k_tile_row_starts(RowGeom G, unsigned long long *__restrict__ rowp,
+                                                          int64_t pair_cap, int64_t *__restrict__ d_num_pairs,
+                                                          int32_t *__restrict__ d_status,
+                                                          int64_t *__restrict__ d_sort_count) {
+  __shared__ unsigned long long part[1024];
+  const int NR = G.n_rows;
+  const int per = (NR + 1023) / 1024;
+  const int lo = threadIdx.x * per, hi = min(NR, lo + per);
+  unsigned long long s = 0;
+  for (int i = lo; i < hi; ++i) s += rowp[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const unsigned long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
     __syncthreads();
     part[threadIdx.x] += v;
     __syncthreads();
   }
   unsigned long long run = part[threadIdx.x] - s;
   for (int i = lo; i < hi; ++i) {
-    uint32_t v = bsum[i];
-    bsum[i] = (uint32_t)(run > 0xFFFFFFFFull ? 0xFFFFFFFFull : run);
+    const unsigned long long v = rowp[i];
+    rowp[i] = run;
     run += v;
   }
-  if (threadIdx.x == kScanThreads - 1) {
-    const unsigned long long total = part[kScanThreads - 1];
-    *d_num_pairs = (int64_t)total;
-    const bool over = total > (unsigned long long)pair_cap;
-    if (over && d_status) atomicOr(d_status, FGS_DEV_PAIR_OVERFLOW);
-    *d_sort_count = over ? 0 : (int64_t)total;
+  if (threadIdx.x == 1023) {
+    const unsigned long long total = part[1023];
+    if (*d_sort_count < 0) {  // the row lists overflowed: no pairs, count already recorded
+      *d_sort_count = 0;
+    } else {
+      *d_num_pairs = (int64_t)total;
+      const bool over = total > (unsigned long long)pair_cap;
+      if (over && d_status) atomicOr(d_status, FGS_DEV_PAIR_OVERFLOW);
+      *d_sort_count = over ? 0 : (int64_t)total;
+    }
   }
 }
 
-// Emits the (tile, id) pairs of every sorted record at its scanned offset.  A
-// warp cooperates on one record at a time so that large footprints do not
-// serialise a single thread.
-__global__ void __launch_bounds__(kScanBlock) k_emit(const float4 *__restrict__ splat, int tw, int th,
-                                                     const uint32_t *__restrict__ svals,
-                                                     const uint2 *__restrict__ rect,
-                                                     const uint32_t *__restrict__ cnt,
-                                                     const uint32_t *__restrict__ bsum,
-                                                     const int64_t *__restrict__ d_vis, int64_t stride, DevViews vs,
-                                                     const int64_t *d_sort_count, uint32_t *__restrict__ tile_keys,
-                                                     uint32_t *__restrict__ ids) {
-  __shared__ uint32_t warp_sum[kScanBlock / 32];
-  const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
-  const int64_t R = *d_vis;
+// Tiles, ranges: one CTA per row scans the row's tile totals: tstart[g][x] = first
+// pair of tile x, tile_ranges = [start, end) ((0, 0) for an empty tile or when the
+// pairs overflowed).
+__global__ void __launch_bounds__(256) k_tile_ranges_rows(RowGeom G, const unsigned long long *__restrict__ rowp,
+                                                          const uint32_t *__restrict__ ttot,
+                                                          const int64_t *__restrict__ d_sort_count,
+                                                          uint32_t *__restrict__ tstart,
+                                                          int2 *__restrict__ ranges) {
+  __shared__ uint32_t s_warp[8];
+  const int g = blockIdx.x;
+  const int v = view_of_row(G, g);
+  const int tx = G.tiles_x[v];
+  const int y = g - G.row_base[v];
+  const bool ok = *d_sort_count > 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t c = j < R ? cnt[j] : 0u;
-  // block-local exclusive scan of c
-  uint32_t incl = c;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) warp_sum[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < kScanBlock / 32 ? warp_sum[lane] : 0u;
-    uint32_t wi = w;
+  uint32_t carry = (uint32_t)rowp[g];
+  for (int xb = 0; xb < tx; xb += 256) {
+    const int x = xb + threadIdx.x;
+    const uint32_t t = x < tx ? ttot[(int64_t)g * G.tx_max + x] : 0u;
+    uint32_t incl = t;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += t;
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
     }
-    if (lane < kScanBlock / 32) warp_sum[lane] = wi - w;
-  }
-  __syncthreads();
-  const uint32_t off = bsum[blockIdx.x] + warp_sum[warp] + (incl - c);
-  const int64_t sort_count = *d_sort_count;  // 0 on overflow: emit nothing
-  // warp-cooperative emission: each lane's record in turn
-  const bool has = c > 0 && sort_count > 0;
-  const PreparedRecord mine = prepare_record(splat, rect, has ? svals[j] : 0u, has);
-  uint32_t pending = __ballot_sync(0xffffffffu, has);
-  while (pending) {
-    const int src = __ffs(pending) - 1;
-    pending &= pending - 1;
-    const uint32_t rc_off = __shfl_sync(0xffffffffu, off, src);
-    const uint32_t rc_cnt = __shfl_sync(0xffffffffu, c, src);
-    const PreparedRecord pr = shfl_record(mine, src);
-    const uint32_t rec = pr.rec;
-    const uint32_t v = (uint32_t)(rec / stride), id = (uint32_t)(rec - (uint64_t)v * stride);
-    const uint32_t x0 = pr.x0, y0 = pr.y0, x1 = pr.x1;
-    const uint32_t w = x1 - x0 + 1u, box = w * (pr.y1 - y0 + 1u);
-    const uint32_t tb = (uint32_t)vs.cam[v].tile_base, tx = (uint32_t)vs.cam[v].tiles_x;
-    const SupportSplat &sp = pr.sp;
-    // the box's tiles in row-major order, 32 candidates per step; the ones the
-    // ellipse reaches are written at consecutive positions (rc_cnt in total)
-    uint32_t out = rc_off;
-    for (uint32_t q0 = 0; q0 < box; q0 += 32) {
-      const uint32_t q = q0 + lane;
-      bool keep = false;
-      uint32_t t = 0;
-      if (q < box) {
-        const uint32_t dy = q / w, dx = q - dy * w;
-        keep = tile_in_support(sp, (int)(x0 + dx), (int)(y0 + dy), tw, th);
-        t = tb + (y0 + dy) * tx + (x0 + dx);
-      }
-      const uint32_t m = __ballot_sync(0xffffffffu, keep);
-      if (keep) {
-        const uint32_t pos = out + __popc(m & ((1u << lane) - 1u));
-        tile_keys[pos] = t;
-        ids[pos] = id;
-      }
-      out += __popc(m);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    for (int w = 0; w < 8; ++w) {
+      before += w < warp ? s_warp[w] : 0u;
+      all += s_warp[w];
     }
-    (void)rc_cnt;
+    const uint32_t start = carry + before + incl - t;
+    if (x < tx) {
+      tstart[(int64_t)g * G.tx_max + x] = start;
+      ranges[G.tile_base[v] + y * tx + x] = (ok && t > 0) ? make_int2((int)start, (int)(start + t)) : make_int2(0, 0);
+    }
+    carry += all;
+    __syncthreads();
   }
 }
 
-__global__ void k_tile_ranges(const uint32_t *__restrict__ tile_keys, const int64_t *d_sort_count,
-                              int64_t cap, int2 *__restrict__ ranges) {
-  const int64_t P = min(*d_sort_count, cap);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += stride) {
-    const uint32_t t = tile_keys[k];
-    const uint32_t prev = k > 0 ? tile_keys[k - 1] : 0xFFFFFFFFu;
-    const uint32_t next = k + 1 < P ? tile_keys[k + 1] : 0xFFFFFFFFu;
-    if (prev != t) ranges[t].x = (int)k;
-    if (next != t) ranges[t].y = (int)(k + 1);
+// Tiles, writing pass: the chunk's records in order, 32 tiles of the row at a time;
+// pair (tile x, record) goes to tstart[g][x] + tpre[c][x] + the pairs of x kept by
+// the chunk's earlier warps + its ballot rank in the warp.
+__global__ void __launch_bounds__(kTileChunk) k_tile_emit(RowGeom G, const float4 *__restrict__ splat,
+                                                          const uint32_t *__restrict__ srec,
+                                                          const uint2 *__restrict__ rect, int tw, int th,
+                                                          const uint32_t *__restrict__ rowlist,
+                                                          const uint32_t *__restrict__ row_start,
+                                                          const uint32_t *__restrict__ chunk_start,
+                                                          const uint32_t *__restrict__ chunk_row,
+                                                          const int64_t *__restrict__ d_nchunks,
+                                                          const uint32_t *__restrict__ tpre,
+                                                          const uint32_t *__restrict__ tstart,
+                                                          const int64_t *__restrict__ d_sort_count,
+                                                          uint32_t *__restrict__ tile_keys,
+                                                          uint32_t *__restrict__ ids) {
+  constexpr int NW = kTileChunk / 32;
+  __shared__ uint32_t s_wc[NW][32];
+  __shared__ int s_lo, s_hi;
+  if (*d_sort_count == 0) return;
+  const int64_t NC = *d_nchunks;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (int64_t c = blockIdx.x; c < NC; c += gridDim.x) {
+    const TileChunk k = tile_chunk(G, chunk_row, chunk_start, row_start, c);
+    if (threadIdx.x == 0) {
+      s_lo = 0x7FFFFFFF;
+      s_hi = -1;
+    }
+    __syncthreads();
+    const uint32_t e = k.e0 + threadIdx.x;
+    int x0 = 0, x1 = -1;
+    uint32_t id = 0;
+    SupportSplat sp{};
+    if (e < k.e1) {
+      const uint32_t rec = srec[rowlist[e]];
+      const uint2 rc = rect[rec];
+      x0 = (int)(rc.x & 0xFFFFu);
+      x1 = (int)(rc.y & 0xFFFFu);
+      id = rec - (uint32_t)k.v * (uint32_t)G.stride;
+      sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
+      atomicMin(&s_lo, x0);
+      atomicMax(&s_hi, x1);
+    }
+    __syncthreads();
+    const int lo = s_lo, hi = s_hi;
+    const int64_t trow = (int64_t)k.g * G.tx_max, crow = c * G.tx_max;
+    const uint32_t tbase = (uint32_t)(G.tile_base[k.v] + k.y * k.tx);
+    for (int xb = lo; xb <= hi; xb += 32) {
+      uint32_t m = 0;  // tiles xb .. xb + 31 this record keeps
+      const int a = max(x0, xb), b = min(x1, xb + 31);
+      for (int x = a; x <= b; ++x)
+        if (tile_in_support(sp, x, k.y, tw, th)) m |= 1u << (x - xb);
+      uint32_t mine = 0;
+#pragma unroll 4
+      for (int bit = 0; bit < 32; ++bit) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, (m >> bit) & 1u);
+        if (lane == bit) mine = __popc(bal);
+      }
+      s_wc[warp][lane] = mine;
+      __syncthreads();
+      uint32_t before = 0;
+      for (int w = 0; w < warp; ++w) before += s_wc[w][lane];
+      if (xb + lane < k.tx) before += tstart[trow + xb + lane] + tpre[crow + xb + lane];
+#pragma unroll 4
+      for (int bit = 0; bit < 32; ++bit) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, (m >> bit) & 1u);
+        const uint32_t pre = __shfl_sync(0xffffffffu, before, bit);
+        if ((m >> bit) & 1u) {
+          const uint32_t pos = pre + __popc(bal & lt);
+          tile_keys[pos] = tbase + (uint32_t)(xb + bit);
+          ids[pos] = id;
+        }
+      }
+      __syncthreads();
+    }
   }
+}
+
+__global__ void k_view_keys(const uint32_t *__restrict__ recs, const int64_t *__restrict__ d_vis, int64_t stride,
+                            uint32_t *__restrict__ keys) {
+  const int64_t R = *d_vis;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < R; j += (int64_t)gridDim.x * blockDim.x)
+    keys[j] = (uint32_t)(recs[j] / (uint64_t)stride);
 }
 
 struct BinWs {
   uint32_t *dk0, *dv0, *dk1, *dv1;  // depth sort ping-pong, R each
-  uint32_t *cnt;                    // R
-  uint32_t *bsum;                   // ceil(R / 1024)
-  uint32_t *tk1, *tv1;              // tile sort ping-pong, pair_capacity each
+  uint32_t *bsum;                   // ceil(R / 1024) + 1
   uint32_t *counts;                 // 256 * kSortMaxBlocks
   uint32_t *digit_total;            // 256
-  int64_t *sort_count;              // 1
-  int64_t *vis_count;               // 1
+  int64_t *vis_count, *sort_count, *nchunks;
+  uint32_t *rowcnt;                 // n_rows * nb_cap
+  uint32_t *rowtot;                 // n_rows
+  uint32_t *row_start;              // n_rows + 1
+  uint32_t *chunk_start;            // n_rows + 1
+  uint32_t *chunk_row;              // chunk_cap
+  uint32_t *rowlist;                // row_cap
+  uint32_t *tcnt, *tpre;            // chunk_cap * tx_max
+  uint32_t *ttot, *tstart;          // n_rows * tx_max
+  unsigned long long *rowp;         // n_rows
+  int64_t nb_cap, row_cap, chunk_cap;
   size_t bytes;
 };
 
-static BinWs carve(void *base, int64_t R, int64_t cap) {
+static BinWs carve(void *base, int64_t R, int64_t cap, int n_rows, int tx_max) {
   BinWs w;
   char *p = static_cast<char *>(base);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     char *q = p ? p + off : nullptr;
-    off += align_up(bytes);
+    off += align_up(std::max<size_t>(bytes, 1));
     return q;
   };
-  const size_t r4 = (size_t)std::max<int64_t>(R, 1) * 4, c4 = (size_t)std::max<int64_t>(cap, 1) * 4;
+  R = std::max<int64_t>(R, 1);
+  w.nb_cap = (R + kRecChunk - 1) / kRecChunk;
+  w.row_cap = std::max<int64_t>(cap, 1);
+  w.chunk_cap = (w.row_cap + kTileChunk - 1) / kTileChunk + n_rows;
+  const size_t r4 = (size_t)R * 4, nr = (size_t)n_rows, txm = (size_t)tx_max;
   w.dk0 = (uint32_t *)take(r4);
   w.dv0 = (uint32_t *)take(r4);
   w.dk1 = (uint32_t *)take(r4);
   w.dv1 = (uint32_t *)take(r4);
-  w.cnt = (uint32_t *)take(r4);
   w.bsum = (uint32_t *)take((size_t)((R + kScanBlock - 1) / kScanBlock + 1) * 4);
-  w.tk1 = (uint32_t *)take(c4);
-  w.tv1 = (uint32_t *)take(c4);
   w.counts = (uint32_t *)take((size_t)256 * kSortMaxBlocks * 4);
   w.digit_total = (uint32_t *)take(256 * 4);
-  w.sort_count = (int64_t *)take(8);
   w.vis_count = (int64_t *)take(8);
+  w.sort_count = (int64_t *)take(8);
+  w.nchunks = (int64_t *)take(8);
+  w.rowcnt = (uint32_t *)take(nr * (size_t)w.nb_cap * 4);
+  w.rowtot = (uint32_t *)take(nr * 4);
+  w.row_start = (uint32_t *)take((nr + 1) * 4);
+  w.chunk_start = (uint32_t *)take((nr + 1) * 4);
+  w.chunk_row = (uint32_t *)take((size_t)w.chunk_cap * 4);
+  w.rowlist = (uint32_t *)take((size_t)w.row_cap * 4);
+  w.tcnt = (uint32_t *)take((size_t)w.chunk_cap * txm * 4);
+  w.tpre = (uint32_t *)take((size_t)w.chunk_cap * txm * 4);
+  w.ttot = (uint32_t *)take(nr * txm * 4);
+  w.tstart = (uint32_t *)take(nr * txm * 4);
+  w.rowp = (unsigned long long *)take(nr * 8);
   w.bytes = off;
   return w;
+}
+
+static bool row_geom(const DevViews &vs, int64_t stride, RowGeom *G) {
+  G->n_views = vs.n;
+  G->stride = stride;
+  G->tx_max = 0;
+  int rows = 0;
+  for (int v = 0; v < vs.n; ++v) {
+    G->row_base[v] = rows;
+    G->tiles_x[v] = vs.cam[v].tiles_x;
+    G->tile_base[v] = vs.cam[v].tile_base;
+    G->tx_max = std::max(G->tx_max, vs.cam[v].tiles_x);
+    rows += vs.cam[v].tiles_y;
+  }
+  G->row_base[vs.n] = rows;
+  G->n_rows = rows;
+  return rows <= kMaxRows;
 }
 
 static int bits_for(int64_t v) {
@@ -610,9 +902,14 @@ static int bits_for(int64_t v) {
 
 using namespace fgs;
 
-extern "C" size_t fgs_bin_sort_workspace_size(int64_t n_records, int64_t pair_capacity) {
-  if (n_records < 0 || pair_capacity < 0) return 0;
-  return carve(nullptr, n_records, pair_capacity).bytes;
+extern "C" size_t fgs_bin_sort_workspace_size(const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
+                                              int64_t n_records, int64_t pair_capacity) {
+  if (n_records < 0 || pair_capacity < 0 || !tiling_ok(tiling)) return 0;
+  DevViews vs;
+  if (!make_views(cams, n_views, tiling.tile_w, tiling.tile_h, &vs)) return 0;
+  RowGeom G;
+  if (!row_geom(vs, 1, &G)) return 0;
+  return carve(nullptr, n_records, pair_capacity, G.n_rows, G.tx_max).bytes;
 }
 
 extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const fgs_camera *cams,
@@ -628,14 +925,16 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   DevViews vs;
   if (!make_views(cams, n_views, tiling.tile_w, tiling.tile_h, &vs)) return FGS_ERR_INVALID_ARGUMENT;
   FGS_CHECK_ARG((int64_t)n_views * proj->stride < 0xFFFFFFFFll, "fgs_bin_sort: too many records");
+  RowGeom G;
+  FGS_CHECK_ARG(row_geom(vs, proj->stride, &G), "fgs_bin_sort: more than %d tile rows", kMaxRows);
   const int64_t R = (int64_t)n_views * n;
-  BinWs w = carve(ws, R, pair_capacity);
+  BinWs w = carve(ws, R, pair_capacity, G.n_rows, G.tx_max);
   FGS_CHECK_ARG(ws != nullptr && ws_bytes >= w.bytes, "fgs_bin_sort: workspace %zu < %zu bytes", ws_bytes,
                 w.bytes);
   FGS_CHECK_ARG((reinterpret_cast<uintptr_t>(ws) & 255) == 0, "fgs_bin_sort: workspace not 256-byte aligned");
   cudaStream_t st = as_stream(stream);
-  FGS_CUDA(cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)vs.total_tiles, st), "memset ranges");
   if (R == 0) {
+    FGS_CUDA(cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)vs.total_tiles, st), "memset ranges");
     FGS_CUDA(cudaMemsetAsync(d_num_pairs, 0, 8, st), "memset pairs");
     return FGS_OK;
   }
@@ -652,24 +951,37 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   fgs_status s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, w.vis_count, 0, R, 32, sort_blocks(R), w.counts,
                             w.digit_total, st);
   if (s != FGS_OK) return s;
-  k_counts_blocksum<<<(unsigned)nb, kScanBlock, 0, st>>>(splat, w.dv0, rect, w.vis_count, tiling.tile_w,
-                                                         tiling.tile_h, w.cnt, w.bsum);
-  k_scan_bsum<<<1, kScanThreads, 0, st>>>(w.bsum, (int)nb, d_num_pairs, pair_capacity, d_status, w.sort_count);
-  // emit into the buffer the tile sort ends in the caller's arrays
-  const int tbits = std::max(1, bits_for(vs.total_tiles));
-  const int passes = (tbits + 7) / 8;
-  uint32_t *ek = (passes & 1) ? w.tk1 : tile_keys;
-  uint32_t *ev = (passes & 1) ? w.tv1 : reinterpret_cast<uint32_t *>(ids);
-  k_emit<<<(unsigned)nb, kScanBlock, 0, st>>>(splat, tiling.tile_w, tiling.tile_h, w.dv0, rect, w.cnt, w.bsum,
-                                              w.vis_count, proj->stride, vs, w.sort_count, ek, ev);
-  count_launch(3);
-  FGS_CHECK_LAUNCH("fgs_bin_sort emit");
-  s = radix_sort(ek, ev, (passes & 1) ? tile_keys : w.tk1, (passes & 1) ? reinterpret_cast<uint32_t *>(ids) : w.tv1,
-                 w.sort_count, 0, pair_capacity, tbits, sort_blocks(pair_capacity), w.counts, w.digit_total, st);
-  if (s != FGS_OK) return s;
-  k_tile_ranges<<<32 * num_sms(), 256, 0, st>>>(tile_keys, w.sort_count, pair_capacity,
-                                               reinterpret_cast<int2 *>(tile_ranges));
-  count_launch();
-  FGS_CHECK_LAUNCH("fgs_bin_sort ranges");
+  const uint32_t *srec = w.dv0;
+  if (n_views > 1) {
+    // views made contiguous again (stable): rows of one view stay together
+    k_view_keys<<<4 * num_sms(), 256, 0, st>>>(w.dv0, w.vis_count, proj->stride, w.dk0);
+    count_launch();
+    s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, w.vis_count, 0, R, bits_for(n_views), sort_blocks(R), w.counts,
+                   w.digit_total, st);
+    if (s != FGS_OK) return s;
+    srec = w.dv1;  // one pass: the result is in the second buffer
+  }
+  const int grid = kPartGrid * num_sms();
+  const int NR = G.n_rows;
+  k_row_count<<<grid, kRecChunk, 0, st>>>(G, srec, rect, w.vis_count, w.nb_cap, w.rowcnt);
+  k_row_scan<<<NR, 1024, 0, st>>>(w.vis_count, w.nb_cap, w.rowcnt, w.rowtot);
+  k_row_starts<<<1, 1024, 0, st>>>(G, w.rowtot, w.row_cap, w.row_start, w.chunk_start, w.chunk_row, w.chunk_cap,
+                                   w.nchunks, d_status, d_num_pairs, w.sort_count);
+  k_row_emit<<<grid, kRecChunk, 0, st>>>(G, srec, rect, w.vis_count, w.nb_cap, w.rowcnt, w.row_start, w.rowlist);
+  count_launch(4);
+  FGS_CHECK_LAUNCH("fgs_bin_sort rows");
+  const int tw = tiling.tile_w, th = tiling.tile_h;
+  const size_t cnt_smem = sizeof(uint32_t) * (size_t)G.tx_max;
+  k_tile_count<<<grid, kTileChunk, cnt_smem, st>>>(G, splat, srec, rect, tw, th, w.rowlist, w.row_start,
+                                                   w.chunk_start, w.chunk_row, w.nchunks, w.tcnt);
+  k_tile_chunk_scan<<<NR, 256, 0, st>>>(G, w.chunk_start, w.tcnt, w.tpre, w.ttot, w.rowp);
+  k_tile_row_starts<<<1, 1024, 0, st>>>(G, w.rowp, pair_capacity, d_num_pairs, d_status, w.sort_count);
+  k_tile_ranges_rows<<<NR, 256, 0, st>>>(G, w.rowp, w.ttot, w.sort_count, w.tstart,
+                                         reinterpret_cast<int2 *>(tile_ranges));
+  k_tile_emit<<<grid, kTileChunk, 0, st>>>(G, splat, srec, rect, tw, th, w.rowlist, w.row_start, w.chunk_start,
+                                           w.chunk_row, w.nchunks, w.tpre, w.tstart, w.sort_count, tile_keys,
+                                           reinterpret_cast<uint32_t *>(ids));
+  count_launch(5);
+  FGS_CHECK_LAUNCH("fgs_bin_sort tiles");
   return FGS_OK;
 }

@@ -84,7 +84,7 @@ _SIGS = {
     "fgs_num_tiles": ([c_void_p, c_int32, Tiling], c_int64),
     "fgs_bin_sort": ([c_void_p, c_int64, c_void_p, c_int32, Tiling, c_void_p, c_size_t, c_void_p, c_void_p, c_int64,
                       c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
-    "fgs_bin_sort_workspace_size": ([c_int64, c_int64], c_size_t),
+    "fgs_bin_sort_workspace_size": ([c_void_p, c_int32, Tiling, c_int64, c_int64], c_size_t),
     "fgs_render_fwd": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p, c_void_p,
                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "fgs_render_bwd": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -307,8 +307,9 @@ def fgs_project(g: GaussianMap, cams: list, til: Tiling, proj: Projection, statu
                              _stream()), "fgs_project")
 
 
-def fgs_bin_sort_workspace_size(n_records: int, pair_capacity: int) -> int:
-    return int(lib().fgs_bin_sort_workspace_size(int(n_records), int(pair_capacity)))
+def fgs_bin_sort_workspace_size(cams: list, til: Tiling, n_records: int, pair_capacity: int) -> int:
+    return int(lib().fgs_bin_sort_workspace_size(camera_array(cams), len(cams), til, int(n_records),
+                                                 int(pair_capacity)))
 
 
 def fgs_bin_sort(proj: Projection, n: int, cams: list, til: Tiling, ws: torch.Tensor, tile_keys: torch.Tensor,

@@ -44,7 +44,8 @@ class Mapper:
         self.ranges = torch.zeros(self.n_tiles, 2, dtype=torch.int32, device=dev)
         self.num_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
-        self.ws_bin = fgs.ws_tensor(fgs.fgs_bin_sort_workspace_size(self.V * cap, self.pair_capacity), dev)
+        self.ws_bin = fgs.ws_tensor(fgs.fgs_bin_sort_workspace_size(self.cams, self.til, self.V * cap,
+                                                                    self.pair_capacity), dev)
         self.grad2d = torch.zeros(self.V, cap, 8, dtype=torch.float32, device=dev)
         self.grads = g.zeros_like()
         self.m = g.zeros_like()

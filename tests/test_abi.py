@@ -45,7 +45,8 @@ def test_host_checks_need_no_gpu(lib):
     assert L.fgs_num_tiles(cams, 1, fgs.tiling(16, 32, 64)) == 8
     assert L.fgs_num_tiles(cams, 1, fgs.tiling(12, 12, 64)) == -1
     assert L.fgs_num_tiles(cams, 0, fgs.tiling(16, 16, 64)) == -1
-    assert L.fgs_bin_sort_workspace_size(1000, 5000) > 0
+    assert L.fgs_bin_sort_workspace_size(cams, 1, fgs.tiling(16, 16, 128), 1000, 5000) > 0
+    assert L.fgs_bin_sort_workspace_size(cams, 1, fgs.tiling(12, 12, 128), 1000, 5000) == 0
     # an argument error returns before any CUDA call
     g = fgs.Gaussians()
     g.n, g.capacity = 5, 2
