@@ -416,6 +416,30 @@ __device__ uint64_t cta_scan_inplace(uint32_t *__restrict__ a, int64_t n, unsign
   return total;
 }
 
+// 32x32 bit transpose across a warp: on entry bit b of lane L's word is entry
+// (L, b); on return lane b holds column b, i.e. the ballot of bit b over the
+// warp.  Five exchange stages swap the off-diagonal blocks of size 16, 8, .., 1.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  constexpr uint32_t kHi[5] = {0xFFFF0000u, 0xFF00FF00u, 0xF0F0F0F0u, 0xCCCCCCCCu, 0xAAAAAAAAu};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
+    const uint32_t t = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & kHi[s]) | ((t >> j) & ~kHi[s])) : ((x & ~kHi[s]) | ((t << j) & kHi[s]));
+  }
+  return x;
+}
+
+// Stable multi-bin ranking in one warp: lane L belongs to bin b (of 32) where bit
+// b of its m is set.  s_wc_row[b] receives the warp's count of bin b; the return
+// value is column `lane` (the lanes in bin `lane`), from which a lane's rank in
+// bin b is popc(column b & lanes below it).
+__device__ __forceinline__ uint32_t warp_bin_counts(uint32_t m, int lane, uint32_t *s_wc_row) {
+  const uint32_t col = warp_transpose32(m, lane);
+  s_wc_row[lane] = __popc(col);
+  return col;
+}
+
 // Rows, counting pass: per record chunk b, the number of its records spanning each
 // global row, into rowcnt[g * nb_cap + b].
 __global__ void __launch_bounds__(kRecChunk) k_row_count(RowGeom G, const uint32_t *__restrict__ srec,
@@ -541,24 +565,19 @@ __global__ void __launch_bounds__(kRecChunk) k_row_emit(RowGeom G, const uint32_
         const int a = max(g0, gb) - gb, e = min(g1, gb + 31) - gb;
         m = (e == 31 ? 0xFFFFFFFFu : ((1u << (e + 1)) - 1u)) & ~((1u << a) - 1u);
       }
-      uint32_t mine = 0;
-#pragma unroll 4
-      for (int bit = 0; bit < 32; ++bit) {
-        const uint32_t bal = __ballot_sync(0xffffffffu, (m >> bit) & 1u);
-        if (lane == bit) mine = __popc(bal);
-      }
-      s_wc[warp][lane] = mine;
+      const uint32_t col = warp_bin_counts(m, lane, s_wc[warp]);
       __syncthreads();
-      uint32_t before = 0;  // this lane's row: records of the chunk's earlier warps
+      // lane L: first position of row gb + L for this warp's records
+      uint32_t before = 0;
       for (int w = 0; w < warp; ++w) before += s_wc[w][lane];
-#pragma unroll 4
-      for (int bit = 0; bit < 32; ++bit) {
-        const uint32_t bal = __ballot_sync(0xffffffffu, (m >> bit) & 1u);
-        const uint32_t pre = __shfl_sync(0xffffffffu, before, bit);
-        if ((m >> bit) & 1u) {
-          const int g = gb + bit;
-          const uint32_t pos = row_start[g] + rowcnt[(int64_t)g * nb_cap + b] + pre + __popc(bal & lt);
-          rowlist[pos] = (uint32_t)j;
+      if (gb + lane < G.n_rows) before += row_start[gb + lane] + rowcnt[(int64_t)(gb + lane) * nb_cap + b];
+      for (uint32_t rem = m; __any_sync(0xffffffffu, rem != 0u);) {
+        const int bit = rem ? __ffs(rem) - 1 : 0;
+        const uint32_t c = __shfl_sync(0xffffffffu, col, bit);
+        const uint32_t base = __shfl_sync(0xffffffffu, before, bit);
+        if (rem) {
+          rowlist[base + __popc(c & lt)] = (uint32_t)j;
+          rem &= rem - 1u;
         }
       }
       __syncthreads();
@@ -584,8 +603,16 @@ __device__ __forceinline__ TileChunk tile_chunk(const RowGeom &G, const uint32_t
   return k;
 }
 
+// One row-list entry as the tile writing pass needs it: Gaussian id, the rect's
+// tile columns x0 | x1 << 16, and the tiles of x0 .. x0 + 63 the support keeps
+// (bit i = tile x0 + i; valid when the rect is at most 64 tiles wide).
+struct EntryInfo {
+  uint32_t id, xr, m0, m1;
+};
+
 // Tiles, counting pass: per chunk c of a row list, the number of its records that
-// keep tile x of the row, into tcnt[c * tx_max + x].
+// keep tile x of the row, into tcnt[c * tx_max + x], and every entry's EntryInfo.
+// A thread tests its own record's tiles.
 __global__ void __launch_bounds__(kTileChunk) k_tile_count(RowGeom G, const float4 *__restrict__ splat,
                                                            const uint32_t *__restrict__ srec,
                                                            const uint2 *__restrict__ rect, int tw, int th,
@@ -594,7 +621,8 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_count(RowGeom G, const floa
                                                            const uint32_t *__restrict__ chunk_start,
                                                            const uint32_t *__restrict__ chunk_row,
                                                            const int64_t *__restrict__ d_nchunks,
-                                                           uint32_t *__restrict__ tcnt) {
+                                                           uint32_t *__restrict__ tcnt,
+                                                           EntryInfo *__restrict__ einfo) {
   extern __shared__ uint32_t s_cnt[];  // [tx_max]
   const int64_t NC = *d_nchunks;
   for (int64_t c = blockIdx.x; c < NC; c += gridDim.x) {
@@ -606,9 +634,16 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_count(RowGeom G, const floa
       const uint32_t rec = srec[rowlist[e]];
       const uint2 rc = rect[rec];
       const SupportSplat sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
-      const int x1 = (int)(rc.y & 0xFFFFu);
-      for (int x = (int)(rc.x & 0xFFFFu); x <= x1; ++x)
-        if (tile_in_support(sp, x, k.y, tw, th)) atomicAdd(&s_cnt[x], 1u);
+      const int x0 = (int)(rc.x & 0xFFFFu), x1 = (int)(rc.y & 0xFFFFu);
+      uint64_t mk = 0;
+      for (int x = x0; x <= x1; ++x) {
+        if (tile_in_support(sp, x, k.y, tw, th)) {
+          atomicAdd(&s_cnt[x], 1u);
+          if (x - x0 < 64) mk |= 1ull << (x - x0);
+        }
+      }
+      einfo[e] = EntryInfo{rec - (uint32_t)k.v * (uint32_t)G.stride, rc.x & 0xFFFFu | (rc.y << 16),
+                           (uint32_t)mk, (uint32_t)(mk >> 32)};
     }
     __syncthreads();
     for (int x = threadIdx.x; x < k.tx; x += kTileChunk) tcnt[c * G.tx_max + x] = s_cnt[x];
@@ -733,21 +768,22 @@ __global__ void __launch_bounds__(256) k_tile_ranges_rows(RowGeom G, const unsig
 
 // Tiles, writing pass: the chunk's records in order, 32 tiles of the row at a time;
 // pair (tile x, record) goes to tstart[g][x] + tpre[c][x] + the pairs of x kept by
-// the chunk's earlier warps + its ballot rank in the warp.
+// the chunk's earlier warps + its rank among the warp's lanes that keep x.  The
+// kept tiles come from the counting pass (rects over 64 tiles wide test again).
 __global__ void __launch_bounds__(kTileChunk) k_tile_emit(RowGeom G, const float4 *__restrict__ splat,
-                                                          const uint32_t *__restrict__ srec,
-                                                          const uint2 *__restrict__ rect, int tw, int th,
-                                                          const uint32_t *__restrict__ rowlist,
+                                                          int tw, int th,
                                                           const uint32_t *__restrict__ row_start,
                                                           const uint32_t *__restrict__ chunk_start,
                                                           const uint32_t *__restrict__ chunk_row,
                                                           const int64_t *__restrict__ d_nchunks,
+                                                          const EntryInfo *__restrict__ einfo,
                                                           const uint32_t *__restrict__ tpre,
                                                           const uint32_t *__restrict__ tstart,
                                                           const int64_t *__restrict__ d_sort_count,
                                                           uint32_t *__restrict__ tile_keys,
                                                           uint32_t *__restrict__ ids) {
   constexpr int NW = kTileChunk / 32;
+  extern __shared__ uint32_t s_base[];  // [tx_max]: first position of tile x for this chunk
   __shared__ uint32_t s_wc[NW][32];
   __shared__ int s_lo, s_hi;
   if (*d_sort_count == 0) return;
@@ -760,53 +796,59 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_emit(RowGeom G, const float
       s_lo = 0x7FFFFFFF;
       s_hi = -1;
     }
+    const int64_t trow = (int64_t)k.g * G.tx_max, crow = c * G.tx_max;
+    for (int x = threadIdx.x; x < k.tx; x += kTileChunk) s_base[x] = tstart[trow + x] + tpre[crow + x];
     __syncthreads();
     const uint32_t e = k.e0 + threadIdx.x;
     int x0 = 0, x1 = -1;
-    uint32_t id = 0;
-    SupportSplat sp{};
+    EntryInfo inf{0u, 0u, 0u, 0u};
     if (e < k.e1) {
-      const uint32_t rec = srec[rowlist[e]];
-      const uint2 rc = rect[rec];
-      x0 = (int)(rc.x & 0xFFFFu);
-      x1 = (int)(rc.y & 0xFFFFu);
-      id = rec - (uint32_t)k.v * (uint32_t)G.stride;
-      sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
+      inf = einfo[e];
+      x0 = (int)(inf.xr & 0xFFFFu);
+      x1 = (int)(inf.xr >> 16);
       atomicMin(&s_lo, x0);
       atomicMax(&s_hi, x1);
     }
+    const bool wide = x1 - x0 + 1 > 64;
+    SupportSplat sp{};
+    if (wide) {
+      const int64_t rec = (int64_t)k.v * G.stride + inf.id;
+      sp = support_splat(splat[2 * rec], splat[2 * rec + 1]);
+    }
     __syncthreads();
     const int lo = s_lo, hi = s_hi;
-    const int64_t trow = (int64_t)k.g * G.tx_max, crow = c * G.tx_max;
     const uint32_t tbase = (uint32_t)(G.tile_base[k.v] + k.y * k.tx);
     for (int xb = lo; xb <= hi; xb += 32) {
       uint32_t m = 0;  // tiles xb .. xb + 31 this record keeps
       const int a = max(x0, xb), b = min(x1, xb + 31);
-      for (int x = a; x <= b; ++x)
-        if (tile_in_support(sp, x, k.y, tw, th)) m |= 1u << (x - xb);
-      uint32_t mine = 0;
-#pragma unroll 4
-      for (int bit = 0; bit < 32; ++bit) {
-        const uint32_t bal = __ballot_sync(0xffffffffu, (m >> bit) & 1u);
-        if (lane == bit) mine = __popc(bal);
+      if (a <= b) {
+        if (!wide) {
+          const uint64_t mk = ((uint64_t)inf.m1 << 32) | inf.m0;  // bit i: tile x0 + i
+          const int sh = xb - x0;
+          m = (uint32_t)(sh >= 0 ? (mk >> sh) : (mk << -sh));
+        } else {
+          for (int x = a; x <= b; ++x)
+            if (tile_in_support(sp, x, k.y, tw, th)) m |= 1u << (x - xb);
+        }
       }
-      s_wc[warp][lane] = mine;
+      const uint32_t col = warp_bin_counts(m, lane, s_wc[warp]);
       __syncthreads();
-      uint32_t before = 0;
+      uint32_t before = xb + lane < k.tx ? s_base[xb + lane] : 0u;
       for (int w = 0; w < warp; ++w) before += s_wc[w][lane];
-      if (xb + lane < k.tx) before += tstart[trow + xb + lane] + tpre[crow + xb + lane];
-#pragma unroll 4
-      for (int bit = 0; bit < 32; ++bit) {
-        const uint32_t bal = __ballot_sync(0xffffffffu, (m >> bit) & 1u);
-        const uint32_t pre = __shfl_sync(0xffffffffu, before, bit);
-        if ((m >> bit) & 1u) {
-          const uint32_t pos = pre + __popc(bal & lt);
+      for (uint32_t rem = m; __any_sync(0xffffffffu, rem != 0u);) {
+        const int bit = rem ? __ffs(rem) - 1 : 0;
+        const uint32_t cb = __shfl_sync(0xffffffffu, col, bit);
+        const uint32_t base = __shfl_sync(0xffffffffu, before, bit);
+        if (rem) {
+          const uint32_t pos = base + __popc(cb & lt);
           tile_keys[pos] = tbase + (uint32_t)(xb + bit);
-          ids[pos] = id;
+          ids[pos] = inf.id;
+          rem &= rem - 1u;
         }
       }
       __syncthreads();
     }
+    __syncthreads();
   }
 }
 
@@ -829,6 +871,7 @@ struct BinWs {
   uint32_t *chunk_start;            // n_rows + 1
   uint32_t *chunk_row;              // chunk_cap
   uint32_t *rowlist;                // row_cap
+  EntryInfo *einfo;                 // row_cap
   uint32_t *tcnt, *tpre;            // chunk_cap * tx_max
   uint32_t *ttot, *tstart;          // n_rows * tx_max
   unsigned long long *rowp;         // n_rows
@@ -866,6 +909,7 @@ static BinWs carve(void *base, int64_t R, int64_t cap, int n_rows, int tx_max) {
   w.chunk_start = (uint32_t *)take((nr + 1) * 4);
   w.chunk_row = (uint32_t *)take((size_t)w.chunk_cap * 4);
   w.rowlist = (uint32_t *)take((size_t)w.row_cap * 4);
+  w.einfo = (EntryInfo *)take((size_t)w.row_cap * sizeof(EntryInfo));
   w.tcnt = (uint32_t *)take((size_t)w.chunk_cap * txm * 4);
   w.tpre = (uint32_t *)take((size_t)w.chunk_cap * txm * 4);
   w.ttot = (uint32_t *)take(nr * txm * 4);
@@ -971,16 +1015,22 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   count_launch(4);
   FGS_CHECK_LAUNCH("fgs_bin_sort rows");
   const int tw = tiling.tile_w, th = tiling.tile_h;
-  const size_t cnt_smem = sizeof(uint32_t) * (size_t)G.tx_max;
-  k_tile_count<<<grid, kTileChunk, cnt_smem, st>>>(G, splat, srec, rect, tw, th, w.rowlist, w.row_start,
-                                                   w.chunk_start, w.chunk_row, w.nchunks, w.tcnt);
+  const size_t tx_smem = sizeof(uint32_t) * (size_t)G.tx_max;
+  if (tx_smem > 16384) {  // with the static arrays, past the default 48 KB of shared memory
+    FGS_CUDA(cudaFuncSetAttribute(k_tile_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tx_smem),
+             "k_tile_count smem");
+    FGS_CUDA(cudaFuncSetAttribute(k_tile_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tx_smem),
+             "k_tile_emit smem");
+  }
+  k_tile_count<<<grid, kTileChunk, tx_smem, st>>>(G, splat, srec, rect, tw, th, w.rowlist, w.row_start,
+                                                  w.chunk_start, w.chunk_row, w.nchunks, w.tcnt, w.einfo);
   k_tile_chunk_scan<<<NR, 256, 0, st>>>(G, w.chunk_start, w.tcnt, w.tpre, w.ttot, w.rowp);
   k_tile_row_starts<<<1, 1024, 0, st>>>(G, w.rowp, pair_capacity, d_num_pairs, d_status, w.sort_count);
   k_tile_ranges_rows<<<NR, 256, 0, st>>>(G, w.rowp, w.ttot, w.sort_count, w.tstart,
                                          reinterpret_cast<int2 *>(tile_ranges));
-  k_tile_emit<<<grid, kTileChunk, 0, st>>>(G, splat, srec, rect, tw, th, w.rowlist, w.row_start, w.chunk_start,
-                                           w.chunk_row, w.nchunks, w.tpre, w.tstart, w.sort_count, tile_keys,
-                                           reinterpret_cast<uint32_t *>(ids));
+  k_tile_emit<<<grid, kTileChunk, tx_smem, st>>>(G, splat, tw, th, w.row_start, w.chunk_start, w.chunk_row,
+                                                 w.nchunks, w.einfo, w.tpre, w.tstart, w.sort_count, tile_keys,
+                                                 reinterpret_cast<uint32_t *>(ids));
   count_launch(5);
   FGS_CHECK_LAUNCH("fgs_bin_sort tiles");
   return FGS_OK;
