@@ -835,15 +835,15 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_emit(RowGeom G, const float
       __syncthreads();
       uint32_t before = xb + lane < k.tx ? s_base[xb + lane] : 0u;
       for (int w = 0; w < warp; ++w) before += s_wc[w][lane];
-      for (uint32_t rem = m; __any_sync(0xffffffffu, rem != 0u);) {
-        const int bit = rem ? __ffs(rem) - 1 : 0;
+      // tile by tile, so that the lanes keeping a tile store to consecutive slots
+#pragma unroll 4
+      for (int bit = 0; bit < 32; ++bit) {
         const uint32_t cb = __shfl_sync(0xffffffffu, col, bit);
         const uint32_t base = __shfl_sync(0xffffffffu, before, bit);
-        if (rem) {
+        if ((m >> bit) & 1u) {
           const uint32_t pos = base + __popc(cb & lt);
           tile_keys[pos] = tbase + (uint32_t)(xb + bit);
           ids[pos] = inf.id;
-          rem &= rem - 1u;
         }
       }
       __syncthreads();

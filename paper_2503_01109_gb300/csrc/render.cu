@@ -24,8 +24,11 @@ __global__ void __launch_bounds__(TW *TH / PX) k_render_fwd(RenderArgs a) {
   render_fwd_tile<TW, TH, BATCH, PX>(a, blockIdx.x, smem);
 }
 
+#ifndef FGS_BWD_MINB
+#define FGS_BWD_MINB 1
+#endif
 template <int TW, int TH, int BATCH, int PX>
-__global__ void __launch_bounds__(TW *TH / PX) k_render_bwd(RenderBwdArgs a) {
+__global__ void __launch_bounds__(TW *TH / PX, FGS_BWD_MINB) k_render_bwd(RenderBwdArgs a) {
   __shared__ __align__(16) char smem[TileSmem<BATCH>::bwd];
   render_bwd_tile<TW, TH, BATCH, PX>(a, blockIdx.x, smem);
 }
