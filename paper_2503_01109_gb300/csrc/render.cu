@@ -1,18 +1,19 @@
 // render.cu -- eq1 alpha blending (colour, depth and opacity readings) per tile,
 // and its reverse-order adjoint.
 //
-// One CTA per (view, tile); each thread owns a few pixels.  The tile's depth-ordered list
-// is walked in batches of BATCH splats: each batch is gathered by id from the
-// splat records (two float4 loads plus three colour planes per splat) into
-// shared memory once and then evaluated by every pixel of the tile.  The walk
-// stops when every pixel of the tile is saturated (T < 1e-4).
+// One CTA per (view, tile); each thread owns one or two pixels of a compact warp
+// block.  The tile's depth-ordered list is walked in batches of BATCH splats:
+// each batch is gathered by id from the splat records (two float4 loads plus
+// three colour planes per splat) into shared memory once and then evaluated by
+// every pixel of the tile.  The walk stops when every pixel of the tile is
+// saturated (T < 1e-4).
 //
-// The backward walks the same lists back to front from the tile's largest
-// contributor count, recovering each pixel's transmittance by division by
-// (1 - alpha) (alpha <= 0.99) instead of storing it.  Per-splat gradients are
-// summed over a thread's pixels, reduced across the warp with a 16-shuffle
-// butterfly, accumulated per batch in shared memory and flushed with one global
-// atomic per (CTA, splat, field).
+// The backward walks the same lists back to front from each warp's largest
+// contributor position, recovering each pixel's transmittance by division by
+// (1 - alpha) (alpha <= 0.99) instead of storing it.  Per-splat sums are
+// accumulated over a thread's pixels, reduced across the warp with a 10-field
+// butterfly, added per batch in shared memory and flushed with one global atomic
+// per (CTA, splat, field).
 #include "render_tile.cuh"
 
 namespace fgs {

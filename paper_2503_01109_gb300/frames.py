@@ -230,13 +230,17 @@ class FramePipeline:
 
     @staticmethod
     def kernel_source_hash(kernel: str) -> str:
-        """sha256 of the sources a kernel is built from (changes invalidate its ncu figures)."""
+        """sha256 of the code a kernel is built from, comments and blank space
+        removed (a code change invalidates its ncu figures, a comment does not)."""
         here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
         files = {"render_bwd": ["common.cuh", "render_tile.cuh", "render.cu"],
                  "render_fwd": ["common.cuh", "render_tile.cuh", "render.cu"]}[kernel]
         h = hashlib.sha256()
         for f in files:
-            h.update(open(os.path.join(here, f), "rb").read())
+            text = open(os.path.join(here, f)).read()
+            text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+            text = re.sub(r"//[^\n]*", " ", text)
+            h.update(" ".join(text.split()).encode())
         return h.hexdigest()[:16]
 
     @staticmethod
