@@ -40,7 +40,8 @@ N_MAP = 1_000_000
 N_GT = 1_000_000
 ITERS_PER_FRAME = 3
 METRIC = "fwd+bwd mapping iters/s @1200x680, 1M Gaussians"
-WORKLOAD = "room map 1M Gaussians, 1200x680 f=600, seeded trajectory; per frame: render + Fourier seeding (<=50k) + 3 mapping iterations"
+WORKLOAD = ("room map 1M Gaussians, 1200x680 f=600, seeded trajectory; per frame: render + Fourier seeding (<=50k) "
+            "+ 3 mapping iterations + pruning (opacity < 0.005 or scale > 0.5 m)")
 
 
 def parse():

@@ -271,6 +271,29 @@ fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads, fgs_gauss
                     void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * fgs_prune -- Gaussian pruning (Sec. III-A, "Gaussian Pruning"): removes every
+ * Gaussian that has grown too large in some dimension or whose opacity is below a
+ * threshold, so that mapping can re-seed the region.  Decided in float32 on the
+ * parameters themselves: Gaussian i is removed when
+ *   opacity_logits[i] < p->min_logit   (opacity below sigmoid(min_logit)), or
+ *   max_k log_scales[k][i] > p->max_log_scale   (largest scale above exp(max_log_scale)).
+ * The survivors keep their order and are compacted in place in g and, when not
+ * NULL, in the Adam moments m and v (same capacity as g); planes past the new
+ * count are left as they were.
+ * Count: the live count is g->d_n ? *g->d_n : g->n; the new count is written to
+ *   *d_num_kept and, when g->d_n is set, to *g->d_n (so a captured graph can
+ *   replay it); the host g->n is not changed.
+ * ws: fgs_prune_workspace_size(g->capacity) bytes, 256-byte aligned.
+ * err: INVALID_ARGUMENT for NULLs, small workspace, m / v of another capacity. */
+typedef struct {
+  float min_logit;      /* remove when the opacity logit is below this             */
+  float max_log_scale;  /* remove when the largest log-scale is above this         */
+} fgs_prune_params;
+fgs_status fgs_prune(fgs_gaussians *g, fgs_gaussians *m, fgs_gaussians *v, const fgs_prune_params *p,
+                     void *ws, size_t ws_bytes, int64_t *d_num_kept, void *stream);
+size_t fgs_prune_workspace_size(int64_t capacity);
+
+/* ---------------------------------------------------------------------------------
  * fgs_fourier_seed -- adaptive densification of Sec. III-A for one frame.
  *   gray = 0.299 R + 0.587 G + 0.114 B of rgb_gt; F = DFT2(gray) (eq2);
  *   centred (eq3, read as the standard spectrum shift); high-pass H = 1 -

@@ -56,6 +56,10 @@ class AdamParams(ctypes.Structure):
     _fields_ = [("lr", c_float * 5), ("beta1", c_float), ("beta2", c_float), ("eps", c_float), ("step", c_int32)]
 
 
+class PruneParams(ctypes.Structure):
+    _fields_ = [("min_logit", c_float), ("max_log_scale", c_float)]
+
+
 class SeedParams(ctypes.Structure):
     _fields_ = [("d0", c_float), ("m", c_int32), ("n", c_int32), ("alpha_h", c_float), ("alpha_l", c_float),
                 ("tau_alpha", c_float), ("tau_depth_rel", c_float), ("tau_color", c_float), ("max_new", c_int32),
@@ -98,6 +102,8 @@ _SIGS = {
     "fgs_scale_reg": ([c_void_p, c_float, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p], c_int32),
     "fgs_scale_reg_workspace_size": ([c_int64], c_size_t),
     "fgs_adam": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_prune": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
+    "fgs_prune_workspace_size": ([c_int64], c_size_t),
     "fgs_last_error": ([], ctypes.c_char_p),
     "fgs_version": ([], c_int32),
     "fgs_launch_count": ([], c_int64),
@@ -398,6 +404,28 @@ def fgs_adam(g: GaussianMap, grads: GaussianMap, m: GaussianMap, v: GaussianMap,
     gs, gr, ms, vs = (x.struct(use_device_count) for x in (g, grads, m, v))
     _check(lib().fgs_adam(ctypes.byref(gs), ctypes.byref(gr), ctypes.byref(ms), ctypes.byref(vs), ctypes.byref(hp),
                           _ptr(d_step), _stream()), "fgs_adam")
+
+
+def prune_params(min_opacity: float = 0.005, max_scale: float = 0.5) -> PruneParams:
+    """Thresholds in the decision domain: opacity below min_opacity <=> logit below
+    logit(min_opacity); a scale above max_scale <=> a log-scale above log(max_scale)
+    (both rounded once to float32, the precision of the parameters)."""
+    p = float(np.float32(min_opacity))
+    return PruneParams(float(np.float32(math.log(p / (1.0 - p)))), float(np.float32(math.log(max_scale))))
+
+
+def fgs_prune_workspace_size(capacity: int) -> int:
+    return int(lib().fgs_prune_workspace_size(int(capacity)))
+
+
+def fgs_prune(g: GaussianMap, m: GaussianMap | None, v: GaussianMap | None, params: PruneParams, ws: torch.Tensor,
+              num_kept: torch.Tensor, use_device_count: bool = False):
+    gs = g.struct(use_device_count)
+    ms = m.struct(use_device_count) if m is not None else None
+    vs = v.struct(use_device_count) if v is not None else None
+    _check(lib().fgs_prune(ctypes.byref(gs), ctypes.byref(ms) if ms is not None else None,
+                           ctypes.byref(vs) if vs is not None else None, ctypes.byref(params), _ptr(ws),
+                           ws.numel() * ws.element_size(), _ptr(num_kept), _stream()), "fgs_prune")
 
 
 def fgs_memset_async(t: torch.Tensor, value: int = 0):

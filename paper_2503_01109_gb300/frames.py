@@ -142,8 +142,11 @@ def render_targets_views(gt_scene: dict, cams: list, tile=(16, 16), batch=128, d
 class FramePipeline:
     def __init__(self, scene: dict, cams: list, gt_scene: dict, capacity: int, tile=(16, 16), batch=128,
                  iters_per_frame: int = 3, device="cuda", loss_w=PAPER_LOSS, reg_w=PAPER_REG, seed_params=None,
-                 prior=None, extra_views: list | None = None):
+                 prior=None, extra_views: list | None = None, prune: fgs.PruneParams | None = None):
         self.cams = cams
+        # Gaussian pruning after each frame's iterations (Sec. III-A): opacity below
+        # 0.005 or a scale above 0.5 m (a tenth of the 4 x 3 x 3 m room's extent)
+        self.prune = prune if prune is not None else fgs.prune_params(0.005, 0.5)
         self.iters = iters_per_frame
         self.kernel_timer = KernelTimer()
         self.colors, self.depths = render_targets(gt_scene, cams, tile, batch, device)
@@ -154,12 +157,8 @@ class FramePipeline:
         self.g = fgs.GaussianMap.from_scene(scene, capacity, device)
         self.mapper = TimedMapper(self.g, cams[:1], fgs.tiling(*tile, batch), loss_w=loss_w, reg_w=reg_w,
                                   use_device_count=True, timer=self.kernel_timer)
-        self.seeder = None
-        try:
-            from .seeding import Seeder
-            self.seeder = Seeder(self.mapper, seed_params, prior)
-        except (ImportError, AttributeError, fgs.FGSError):
-            self.seeder = None
+        from .seeding import Seeder
+        self.seeder = Seeder(self.mapper, seed_params, prior)
         self.loss_host = torch.zeros(1, dtype=torch.float32).pin_memory()
         self.stage_c = torch.zeros_like(self.colors[0])
         self.stage_d = torch.zeros_like(self.depths[0])
@@ -182,11 +181,12 @@ class FramePipeline:
 
     def frame_step(self, k: int, from_host=None):
         self._use_frame(k % len(self.cams), from_host)
-        if self.seeder is not None:
-            with self.kernel_timer.span("seed"):
-                self.seeder.seed_frame(self.mapper.color_gt, self.mapper.depth_gt, self.cams[k % len(self.cams)])
+        with self.kernel_timer.span("seed"):
+            self.seeder.seed_frame(self.mapper.color_gt, self.mapper.depth_gt, self.cams[k % len(self.cams)])
         for _ in range(self.iters):
             self.mapper.iteration()
+        with self.kernel_timer.span("prune"):
+            self.mapper.prune(self.prune)
 
     # ------------------------------------------------------------------------------
     def check(self):

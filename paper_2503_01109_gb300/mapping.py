@@ -56,6 +56,8 @@ class Mapper:
         self.ws_loss = fgs.ws_tensor(fgs.fgs_loss_workspace_size(self.cams), dev)
         self.ws_reg = fgs.ws_tensor(fgs.fgs_scale_reg_workspace_size(cap), dev)
         self.d_step = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.ws_prune = None
+        self.num_kept = torch.zeros(1, dtype=torch.int64, device=dev)
         self.color_gt = torch.zeros_like(self.frame.color)
         self.depth_gt = torch.zeros_like(self.frame.depth)
         self.host_step = 0
@@ -97,6 +99,17 @@ class Mapper:
         self.host_step += 1
         fgs.fgs_adam(self.g, self.grads, self.m, self.v, self.lr, step=self.host_step,
                      d_step=self.d_step if self.use_dc else None, use_device_count=self.use_dc)
+
+    def prune(self, params: fgs.PruneParams):
+        """Gaussian pruning (Sec. III-A): drops too large or nearly transparent
+        Gaussians from the map and their Adam moments, keeping the others' order.
+        With the device count nothing synchronises; otherwise the host count is
+        read back."""
+        if self.ws_prune is None:
+            self.ws_prune = fgs.ws_tensor(fgs.fgs_prune_workspace_size(self.g.capacity), self.g.buf.device)
+        fgs.fgs_prune(self.g, self.m, self.v, params, self.ws_prune, self.num_kept, self.use_dc)
+        if not self.use_dc:
+            self.g.n = int(self.num_kept.item())
 
     def check_status(self):
         s = int(self.status.item())
