@@ -198,9 +198,10 @@ def window_measure(pipe, steps: int, warmup: int):
 
 def convergence_measure(seed_offset: int = 0):
     """Iterations and wall time to 30 dB from an empty map: plain per-view
-    Fourier-prior loop vs the learned prior vs the learned prior with a 3-keyframe
-    window, on a test trajectory; the prior is trained on a training trajectory of
-    the same ground-truth scene."""
+    Fourier-prior loop vs the learned prior vs the learned prior with a 3-view
+    window (previous frames, or co-visible + random keyframes), on a test
+    trajectory; the prior is trained on a training trajectory of the same
+    ground-truth scene."""
     from paper_2503_01109_gb300 import synthetic as syn
     from paper_2503_01109_gb300.convergence import compare
     from paper_2503_01109_gb300.frames import render_targets

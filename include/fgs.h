@@ -294,6 +294,34 @@ fgs_status fgs_prune(fgs_gaussians *g, fgs_gaussians *m, fgs_gaussians *v, const
 size_t fgs_prune_workspace_size(int64_t capacity);
 
 /* ---------------------------------------------------------------------------------
+ * fgs_covisibility -- co-visibility of keyframes with the current frame (Sec.
+ * III-C, "Keyframe Selection"): the fraction of the current frame's observed
+ * points that a keyframe also sees.  The current depth map is sampled every `step`
+ * pixels in x and y from (0, 0); a sample with depth d > 0 is back-projected,
+ *   p_c = (d (x - cx) / fx, d (y - cy) / fy, d),  p_w = R^T (p_c - t),
+ * and counted as inside keyframe k when q = R_k p_w + t_k has q.z > znear_k and
+ * projects to u = fx_k (q.x / q.z) + cx_k in [-0.5, W_k - 0.5), v likewise in
+ * [-0.5, H_k - 0.5) -- every operation rounded to float32 in this order.
+ * out: d_inside[k] (int64) samples inside keyframe k, *d_valid (int64) samples
+ *   with depth > 0; co-visibility = d_inside[k] / *d_valid.
+ * err: INVALID_ARGUMENT for NULLs, step < 1, n_keyframes outside 1..256. */
+fgs_status fgs_covisibility(const float *depth, const fgs_camera *cam, const fgs_camera *keyframes,
+                            int32_t n_keyframes, int32_t step, int64_t *d_inside, int64_t *d_valid,
+                            void *stream);
+
+/* fgs_select_keyframes -- the keyframe window of Sec. III-C: keyframes whose
+ * co-visibility d_inside[k] / *d_valid exceeds `threshold` (0.7 in the paper) are
+ * co-visible; of the others, the round(frac * count) (frac 0.3 in the paper) with
+ * the smallest draws u[k] (ties by index) are the random keyframes.  The draws are
+ * an input (uniform numbers, one per keyframe, on the device).
+ * out: d_kind[k] = 1 co-visible, 2 random, 0 not selected; *d_count selected.
+ *   With *d_valid == 0 no keyframe is co-visible.
+ * err: INVALID_ARGUMENT for NULLs, n_keyframes outside 1..1024. */
+fgs_status fgs_select_keyframes(const int64_t *d_inside, const int64_t *d_valid, const float *u,
+                                int32_t n_keyframes, float threshold, float frac, int32_t *d_kind,
+                                int32_t *d_count, void *stream);
+
+/* ---------------------------------------------------------------------------------
  * fgs_fourier_seed -- adaptive densification of Sec. III-A for one frame.
  *   gray = 0.299 R + 0.587 G + 0.114 B of rgb_gt; F = DFT2(gray) (eq2);
  *   centred (eq3, read as the standard spectrum shift); high-pass H = 1 -

@@ -28,7 +28,7 @@ from . import fgs
 from .mapping import Mapper
 from .prior import PriorMLP, features as prior_features
 from .seeding import Seeder
-from .window import Window
+from .window import KeyframeSelector, Window
 
 
 def psnr(color: torch.Tensor, target: torch.Tensor) -> float:
@@ -41,9 +41,14 @@ class SlamLoop:
 
     def __init__(self, colors, depths, cams, capacity: int, prior: PriorMLP | None = None, window: int = 1,
                  tiling: fgs.Tiling | None = None, target_psnr: float = 30.0, max_iters: int = 60,
-                 seed_params: fgs.SeedParams | None = None, record_seeds: bool = False):
+                 seed_params: fgs.SeedParams | None = None, record_seeds: bool = False,
+                 selector: KeyframeSelector | None = None):
+        """window > 1: optimise the current frame with earlier keyframes -- the
+        window - 1 previous frames, or, with `selector`, the co-visible and random
+        keyframes it picks among all earlier frames (at most window - 1)."""
         self.colors, self.depths, self.cams = colors, depths, cams
         self.target, self.max_iters, self.window = target_psnr, max_iters, window
+        self.selector = selector
         self.g = fgs.GaussianMap(capacity, "cuda", 0)
         self.til = tiling or fgs.tiling(16, 16, 128)
         self.mapper = Mapper(self.g, [cams[0]], self.til, use_device_count=True)
@@ -53,8 +58,8 @@ class SlamLoop:
         self.seed_log = []   # (first index, count, features [n][272])
         self.frames = []     # per frame: iterations, seconds, final psnr
 
-    def _window_for(self, k: int):
-        ks = list(range(max(0, k - self.window + 1), k + 1))
+    def _window_for(self, k: int, picked: list | None = None):
+        ks = sorted(picked) + [k] if picked is not None else list(range(max(0, k - self.window + 1), k + 1))
         cams = [self.cams[j] for j in ks]
         if self.win is None or len(self.win.cams) != len(cams):
             self.win = Window(self.g, cams, self.til)
@@ -78,9 +83,14 @@ class SlamLoop:
             self.seed_log.append((base, n_new, prior_features(self.colors[k], self.depths[k], W, H, xy), hi))
         it, p = 0, 0.0
         use_window = self.window > 1 and k > 0
+        picked = None
+        if use_window and self.selector is not None:
+            self.selector.max_k = self.window - 1
+            picked = self.selector.select(self.depths[k].reshape(cam["height"], cam["width"]), cam, self.cams[:k])
+            use_window = len(picked) > 0
         while it < self.max_iters:
             if use_window:
-                w = self._window_for(k)
+                w = self._window_for(k, picked)
                 w.iteration()
                 f = w.frame.view(len(w.cams) - 1)["color"].reshape(-1)
             else:
@@ -188,9 +198,10 @@ def compare(gt_colors_train, gt_depths_train, cams_train, gt_colors_test, gt_dep
             capacity: int, target_psnr: float = 30.0, train_iters: int = 40, max_iters: int = 100,
             epochs: int = 12, window: int = 3) -> dict:
     """The whole experiment: pairs from the plain loop on a training trajectory,
-    prior training on the GPU, then the plain per-view loop, the per-view loop
-    with the learned prior and the batched window with the learned prior on a
-    test trajectory of the same scene."""
+    prior training on the GPU, then on a test trajectory of the same scene the
+    plain per-view loop, the per-view loop with the learned prior, the batched
+    window of the previous frames with the learned prior, and the batched window
+    of the co-visible and random keyframes (Sec. III-C) with the learned prior."""
     t0 = time.perf_counter()
     rec = SlamLoop(gt_colors_train, gt_depths_train, cams_train, capacity, target_psnr=1e9, max_iters=train_iters,
                    record_seeds=True)
@@ -207,9 +218,12 @@ def compare(gt_colors_train, gt_depths_train, cams_train, gt_colors_test, gt_dep
     t_train = time.perf_counter() - t0
     out = {"target_psnr": target_psnr, "pairs": int(feats.shape[0]), "train_loss": hist,
            "init_mse_held_out": err, "train_seconds": t_train}
-    for name, pr, win in (("plain", None, 1), ("learned_prior", prior, 1), ("learned_prior_window", prior, window)):
+    variants = (("plain", None, 1, None), ("learned_prior", prior, 1, None),
+                ("learned_prior_window", prior, window, None),
+                ("learned_prior_covis_window", prior, window, KeyframeSelector(seed=0)))
+    for name, pr, win, sel in variants:
         L = SlamLoop(gt_colors_test, gt_depths_test, cams_test, capacity, prior=pr, window=win,
-                     target_psnr=target_psnr, max_iters=max_iters)
+                     target_psnr=target_psnr, max_iters=max_iters, selector=sel)
         L.run()
         res = summarise(L.frames, target_psnr)
         res["psnr_all_frames_end"] = L.evaluate_all()

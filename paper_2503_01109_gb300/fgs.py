@@ -104,6 +104,9 @@ _SIGS = {
     "fgs_adam": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "fgs_prune": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
     "fgs_prune_workspace_size": ([c_int64], c_size_t),
+    "fgs_covisibility": ([c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_select_keyframes": ([c_void_p, c_void_p, c_void_p, c_int32, c_float, c_float, c_void_p, c_void_p,
+                              c_void_p], c_int32),
     "fgs_last_error": ([], ctypes.c_char_p),
     "fgs_version": ([], c_int32),
     "fgs_launch_count": ([], c_int64),
@@ -426,6 +429,18 @@ def fgs_prune(g: GaussianMap, m: GaussianMap | None, v: GaussianMap | None, para
     _check(lib().fgs_prune(ctypes.byref(gs), ctypes.byref(ms) if ms is not None else None,
                            ctypes.byref(vs) if vs is not None else None, ctypes.byref(params), _ptr(ws),
                            ws.numel() * ws.element_size(), _ptr(num_kept), _stream()), "fgs_prune")
+
+
+def fgs_covisibility(depth: torch.Tensor, cam: dict, keyframes: list, step: int, inside: torch.Tensor,
+                     valid: torch.Tensor):
+    _check(lib().fgs_covisibility(_ptr(depth), camera_array([cam]), camera_array(keyframes), len(keyframes),
+                                  int(step), _ptr(inside), _ptr(valid), _stream()), "fgs_covisibility")
+
+
+def fgs_select_keyframes(inside: torch.Tensor, valid: torch.Tensor, u: torch.Tensor, threshold: float, frac: float,
+                         kind: torch.Tensor, count: torch.Tensor):
+    _check(lib().fgs_select_keyframes(_ptr(inside), _ptr(valid), _ptr(u), inside.numel(), float(threshold),
+                                      float(frac), _ptr(kind), _ptr(count), _stream()), "fgs_select_keyframes")
 
 
 def fgs_memset_async(t: torch.Tensor, value: int = 0):

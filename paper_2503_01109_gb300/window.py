@@ -86,3 +86,35 @@ def autotune(g: fgs.GaussianMap, cams, color_gt, depth_gt, tiles=TILES, batches=
             table[(tile, batch)] = time_config(g, cams, color_gt, depth_gt, tile, batch, reps=reps, **kw)
     (tile, batch), _ = min(table.items(), key=lambda kv: kv[1])
     return fgs.tiling(tile[0], tile[1], batch), table
+
+
+class KeyframeSelector:
+    """The keyframe window of Sec. III-C: keyframes whose co-visibility with the
+    current frame exceeds `threshold` (co-visible) plus a random `frac` of the
+    others, decided on the device (``fgs_covisibility``, ``fgs_select_keyframes``);
+    the uniform draws come from a seeded generator.  At most `max_keyframes` are
+    returned: co-visible ones by decreasing co-visibility, then random ones in draw
+    order."""
+
+    def __init__(self, step: int = 4, threshold: float = 0.7, frac: float = 0.3, seed: int = 0,
+                 max_keyframes: int = 7, device="cuda"):
+        self.step, self.threshold, self.frac, self.max_k = int(step), float(threshold), float(frac), max_keyframes
+        self.gen = torch.Generator(device="cpu").manual_seed(seed)
+        self.device = device
+        self.valid = torch.zeros(1, dtype=torch.int64, device=device)
+        self.count = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def select(self, depth: torch.Tensor, cam: dict, keyframes: list) -> list:
+        K = len(keyframes)
+        if K == 0:
+            return []
+        inside = torch.zeros(K, dtype=torch.int64, device=self.device)
+        kind = torch.zeros(K, dtype=torch.int32, device=self.device)
+        u = torch.rand(K, generator=self.gen).to(self.device)
+        for a in range(0, K, 256):  # at most 256 keyframes per co-visibility call
+            fgs.fgs_covisibility(depth, cam, keyframes[a:a + 256], self.step, inside[a:a + 256], self.valid)
+        fgs.fgs_select_keyframes(inside, self.valid, u, self.threshold, self.frac, kind, self.count)
+        kind_h, inside_h, u_h = kind.cpu().numpy(), inside.cpu().numpy(), u.cpu().numpy()
+        covis = sorted((k for k in range(K) if kind_h[k] == 1), key=lambda k: (-int(inside_h[k]), k))
+        rand = sorted((k for k in range(K) if kind_h[k] == 2), key=lambda k: (float(u_h[k]), k))
+        return (covis + rand)[:self.max_k]
