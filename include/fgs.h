@@ -322,6 +322,86 @@ fgs_status fgs_select_keyframes(const int64_t *d_inside, const int64_t *d_valid,
                                 int32_t *d_count, void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * GICP tracking on the sparse map (Sec. III-B, eq12-eq14).  Point clouds are
+ * float32 [capacity][3] arrays with a count that lives on the device; per-point
+ * covariances are symmetric 3x3 stored as [capacity][6] (xx, xy, xz, yy, yz, zz).
+ * A uniform grid indexes a cloud for neighbour search: its cell edge bounds every
+ * neighbourhood radius used with it (covariance radius, correspondence distance),
+ * so 27 cells around a point hold every candidate. */
+typedef struct {
+  float origin[3];  /* corner of cell (0, 0, 0)                                 */
+  float cell;       /* cell edge (world units)                                  */
+  int32_t dims[3];  /* cells per axis (product <= 2^26); points outside are skipped */
+} fgs_grid;
+
+/* fgs_depth_points -- the observed points of a depth map in camera coordinates:
+ * pixels with x % step == 0, y % step == 0, depth d > 0 and, when mask is not NULL,
+ * (mask & mask_bits) != 0, as (d (x - cx) / fx, d (y - cy) / fy, d) in pixel order,
+ * each operation rounded to float32 in that order.
+ * out: xyz[capacity][3], *d_n; FGS_DEV_MAP_FULL and a truncated cloud when more
+ * points than capacity.  ws: fgs_depth_points_workspace_size(W, H, step). */
+fgs_status fgs_depth_points(const float *depth, const uint8_t *mask, uint8_t mask_bits, const fgs_camera *cam,
+                            int32_t step, float *xyz, int64_t capacity, int64_t *d_n, void *ws, size_t ws_bytes,
+                            int32_t *d_status, void *stream);
+size_t fgs_depth_points_workspace_size(int32_t width, int32_t height, int32_t step);
+
+/* fgs_transform_points -- xyz_out = R xyz_in + t for [R | t] = pose (row-major 3x4,
+ * double on the device), and covariances C_out = R C_in R^T when both pointers
+ * are set; in place is allowed. */
+fgs_status fgs_transform_points(const float *xyz_in, const float *cov_in, const int64_t *d_n, int64_t n_max,
+                                const double *d_pose, float *xyz_out, float *cov_out, void *stream);
+
+/* fgs_voxel_downsample -- uniform downsampling in 3D: of every occupied grid cell
+ * the point with the lowest index, appended in index order to out (the sparse
+ * map's addition of Sec. III-B).  Points outside the grid are dropped.
+ * out: out_xyz[out_capacity][3] from index *d_n_out on (then *d_n_out grows);
+ *   FGS_DEV_MAP_FULL when it would exceed out_capacity.
+ * ws: fgs_voxel_workspace_size(grid, n_max). */
+fgs_status fgs_voxel_downsample(const float *xyz, const int64_t *d_n, int64_t n_max, const fgs_grid *grid,
+                                void *ws, size_t ws_bytes, float *out_xyz, int64_t out_capacity,
+                                int64_t *d_n_out, int32_t *d_status, void *stream);
+size_t fgs_voxel_workspace_size(const fgs_grid *grid, int64_t n_max);
+
+/* fgs_grid_build -- cell index of a cloud: order[cell_start[c] .. cell_start[c+1])
+ * are the points in cell c (any order within a cell).  cell_start has
+ * cells + 1 entries; ws: fgs_grid_workspace_size(grid, n_max). */
+fgs_status fgs_grid_build(const float *xyz, const int64_t *d_n, int64_t n_max, const fgs_grid *grid,
+                          int32_t *cell_start, int32_t *order, void *ws, size_t ws_bytes, void *stream);
+size_t fgs_grid_workspace_size(const fgs_grid *grid, int64_t n_max);
+
+/* fgs_point_covariances -- GICP surface covariances: the neighbourhood of a point
+ * is its (up to) k nearest points within the grid's cell edge, itself included,
+ * ordered by (squared distance, index); C = (1/m) sum (x - mean)(x - mean)^T over
+ * them; with eigenvectors v1..v3 of C by increasing eigenvalue the covariance is
+ * regularised to eps v1 v1^T + v2 v2^T + v3 v3^T (a plane); fewer than 3
+ * neighbours give the identity.  k in 3..32. */
+fgs_status fgs_point_covariances(const float *xyz, const int64_t *d_n, int64_t n_max, const fgs_grid *grid,
+                                 const int32_t *cell_start, const int32_t *order, int32_t k, float eps,
+                                 float *cov, void *stream);
+
+/* fgs_gicp -- eq14 by Gauss-Newton: minimises sum_i d_i^T (C_q + R C_p R^T)^-1 d_i
+ * over T = [R | t], d_i = q_i - T p_i (eq12), q_i the nearest target point to T p_i
+ * within max_dist (ties by index; pairs without one are left out).  Increment
+ * xi = (w, v) of T <- (Rodrigues(w), v) T from the normal equations of the
+ * linearisation d + [[T p]_x, -I] xi; correspondences are renewed every iteration;
+ * it stops early when |xi| < 1e-9, and keeps the pose when fewer than 6 pairs or
+ * a singular system remain.  d_pose (double [12], row-major [R | t], the
+ * world-from-source pose) holds the initial guess and receives the result.
+ * d_stats (double [4]): cost and correspondences at the last evaluated pose, the
+ * fraction of source points with a target point within overlap_dist there (the
+ * keyframe test of Sec. III-C), iterations run.  ws: fgs_gicp_workspace_size(n_src_max). */
+typedef struct {
+  int32_t iterations;  /* at most this many Gauss-Newton steps                 */
+  float max_dist;      /* correspondence distance (<= the target grid's cell)  */
+  float overlap_dist;  /* overlap distance (<= the target grid's cell)         */
+} fgs_gicp_params;
+fgs_status fgs_gicp(const float *src_xyz, const float *src_cov, const int64_t *d_n_src, int64_t n_src_max,
+                    const float *tgt_xyz, const float *tgt_cov, const fgs_grid *grid, const int32_t *cell_start,
+                    const int32_t *order, const fgs_gicp_params *p, double *d_pose, double *d_stats, void *ws,
+                    size_t ws_bytes, void *stream);
+size_t fgs_gicp_workspace_size(int64_t n_src_max);
+
+/* ---------------------------------------------------------------------------------
  * fgs_fourier_seed -- adaptive densification of Sec. III-A for one frame.
  *   gray = 0.299 R + 0.587 G + 0.114 B of rgb_gt; F = DFT2(gray) (eq2);
  *   centred (eq3, read as the standard spectrum shift); high-pass H = 1 -

@@ -56,6 +56,27 @@ class AdamParams(ctypes.Structure):
     _fields_ = [("lr", c_float * 5), ("beta1", c_float), ("beta2", c_float), ("eps", c_float), ("step", c_int32)]
 
 
+class Grid(ctypes.Structure):
+    _fields_ = [("origin", c_float * 3), ("cell", c_float), ("dims", c_int32 * 3)]
+
+
+class GicpParams(ctypes.Structure):
+    _fields_ = [("iterations", c_int32), ("max_dist", c_float), ("overlap_dist", c_float)]
+
+
+def grid(origin, cell: float, dims) -> Grid:
+    g = Grid()
+    for k in range(3):
+        g.origin[k] = float(origin[k])
+        g.dims[k] = int(dims[k])
+    g.cell = float(cell)
+    return g
+
+
+def grid_cells(g: Grid) -> int:
+    return int(g.dims[0]) * int(g.dims[1]) * int(g.dims[2])
+
+
 class PruneParams(ctypes.Structure):
     _fields_ = [("min_logit", c_float), ("max_log_scale", c_float)]
 
@@ -107,6 +128,21 @@ _SIGS = {
     "fgs_covisibility": ([c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p], c_int32),
     "fgs_select_keyframes": ([c_void_p, c_void_p, c_void_p, c_int32, c_float, c_float, c_void_p, c_void_p,
                               c_void_p], c_int32),
+    "fgs_depth_points": ([c_void_p, c_void_p, ctypes.c_uint8, c_void_p, c_int32, c_void_p, c_int64, c_void_p,
+                          c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
+    "fgs_depth_points_workspace_size": ([c_int32, c_int32, c_int32], c_size_t),
+    "fgs_transform_points": ([c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_voxel_downsample": ([c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_size_t, c_void_p, c_int64, c_void_p,
+                              c_void_p, c_void_p], c_int32),
+    "fgs_voxel_workspace_size": ([c_void_p, c_int64], c_size_t),
+    "fgs_grid_build": ([c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p],
+                       c_int32),
+    "fgs_grid_workspace_size": ([c_void_p, c_int64], c_size_t),
+    "fgs_point_covariances": ([c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_int32, c_float, c_void_p,
+                               c_void_p], c_int32),
+    "fgs_gicp": ([c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                  c_void_p, c_void_p, c_void_p, c_size_t, c_void_p], c_int32),
+    "fgs_gicp_workspace_size": ([c_int64], c_size_t),
     "fgs_last_error": ([], ctypes.c_char_p),
     "fgs_version": ([], c_int32),
     "fgs_launch_count": ([], c_int64),
@@ -441,6 +477,57 @@ def fgs_select_keyframes(inside: torch.Tensor, valid: torch.Tensor, u: torch.Ten
                          kind: torch.Tensor, count: torch.Tensor):
     _check(lib().fgs_select_keyframes(_ptr(inside), _ptr(valid), _ptr(u), inside.numel(), float(threshold),
                                       float(frac), _ptr(kind), _ptr(count), _stream()), "fgs_select_keyframes")
+
+
+def fgs_depth_points(depth: torch.Tensor, mask: torch.Tensor | None, mask_bits: int, cam: dict, step: int,
+                     xyz: torch.Tensor, n: torch.Tensor, ws: torch.Tensor, status: torch.Tensor | None = None):
+    _check(lib().fgs_depth_points(_ptr(depth), _ptr(mask), int(mask_bits), camera_array([cam]), int(step), _ptr(xyz),
+                                  xyz.shape[0], _ptr(n), _ptr(ws), ws.numel() * ws.element_size(), _ptr(status),
+                                  _stream()), "fgs_depth_points")
+
+
+def fgs_depth_points_workspace_size(width: int, height: int, step: int) -> int:
+    return int(lib().fgs_depth_points_workspace_size(int(width), int(height), int(step)))
+
+
+def fgs_transform_points(xyz_in, cov_in, n: torch.Tensor, pose: torch.Tensor, xyz_out, cov_out=None):
+    _check(lib().fgs_transform_points(_ptr(xyz_in), _ptr(cov_in), _ptr(n), xyz_in.shape[0], _ptr(pose), _ptr(xyz_out),
+                                      _ptr(cov_out), _stream()), "fgs_transform_points")
+
+
+def fgs_voxel_workspace_size(g: Grid, n_max: int) -> int:
+    return int(lib().fgs_voxel_workspace_size(ctypes.byref(g), int(n_max)))
+
+
+def fgs_voxel_downsample(xyz, n: torch.Tensor, g: Grid, ws, out_xyz, n_out: torch.Tensor, status=None):
+    _check(lib().fgs_voxel_downsample(_ptr(xyz), _ptr(n), xyz.shape[0], ctypes.byref(g), _ptr(ws),
+                                      ws.numel() * ws.element_size(), _ptr(out_xyz), out_xyz.shape[0], _ptr(n_out),
+                                      _ptr(status), _stream()), "fgs_voxel_downsample")
+
+
+def fgs_grid_workspace_size(g: Grid, n_max: int) -> int:
+    return int(lib().fgs_grid_workspace_size(ctypes.byref(g), int(n_max)))
+
+
+def fgs_grid_build(xyz, n: torch.Tensor, g: Grid, cell_start, order, ws):
+    _check(lib().fgs_grid_build(_ptr(xyz), _ptr(n), xyz.shape[0], ctypes.byref(g), _ptr(cell_start), _ptr(order),
+                                _ptr(ws), ws.numel() * ws.element_size(), _stream()), "fgs_grid_build")
+
+
+def fgs_point_covariances(xyz, n: torch.Tensor, g: Grid, cell_start, order, k: int, eps: float, cov):
+    _check(lib().fgs_point_covariances(_ptr(xyz), _ptr(n), xyz.shape[0], ctypes.byref(g), _ptr(cell_start),
+                                       _ptr(order), int(k), float(eps), _ptr(cov), _stream()), "fgs_point_covariances")
+
+
+def fgs_gicp_workspace_size(n_src_max: int) -> int:
+    return int(lib().fgs_gicp_workspace_size(int(n_src_max)))
+
+
+def fgs_gicp(src, src_cov, n_src: torch.Tensor, tgt, tgt_cov, g: Grid, cell_start, order, params: GicpParams,
+             pose: torch.Tensor, stats: torch.Tensor, ws):
+    _check(lib().fgs_gicp(_ptr(src), _ptr(src_cov), _ptr(n_src), src.shape[0], _ptr(tgt), _ptr(tgt_cov),
+                          ctypes.byref(g), _ptr(cell_start), _ptr(order), ctypes.byref(params), _ptr(pose),
+                          _ptr(stats), _ptr(ws), ws.numel() * ws.element_size(), _stream()), "fgs_gicp")
 
 
 def fgs_memset_async(t: torch.Tensor, value: int = 0):

@@ -215,3 +215,33 @@ def fake_render(width: int, height: int, seed: int) -> dict:
     D = rng.uniform(1.5, 4.0, (height, width)) * A
     C = rng.uniform(0, 1, (3, height, width))
     return {"color": C.astype(np.float32), "depth": D.astype(np.float32), "alpha": A.astype(np.float32)}
+
+
+def box_depth(cam: dict, half=ROOM_HALF) -> np.ndarray:
+    """Depth [H][W] (camera z) of the inside of an axis-aligned box centred at the
+    origin, seen from a camera inside it: each pixel's ray hits the first face in
+    its direction of travel.  An exact, view-consistent geometry for tracking."""
+    W, H = cam["width"], cam["height"]
+    M = np.asarray(cam["world_to_cam"], np.float64).reshape(3, 4)
+    R, t = M[:, :3], M[:, 3]
+    o = -R.T @ t
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    dc = np.stack([(xs - cam["cx"]) / cam["fx"], (ys - cam["cy"]) / cam["fy"], np.ones_like(xs)], -1)
+    dw = dc @ R                                   # R^T d for every pixel
+    h = np.asarray(half, np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ts = np.where(dw > 0, (h - o) / dw, np.where(dw < 0, (-h - o) / dw, np.inf))
+    return ts.min(-1).astype(np.float32)         # the ray parameter is the camera z (d_c.z = 1)
+
+
+def corner_trajectory(n_frames: int, width: int, height: int, f: float, corner=(2.0, 1.5, 1.5)) -> list:
+    """Cameras drifting slowly near the room centre while looking at a corner of the
+    room, so that three faces are in view (every pose is then fixed by geometry)."""
+    cams = []
+    for k in range(n_frames):
+        p = np.array([0.3 + 0.015 * k, 0.2 + 0.004 * k, 0.25 + 0.01 * math.sin(0.3 * k)])
+        d = np.asarray(corner, np.float64) - p
+        yaw = math.atan2(d[0], d[2]) + 0.01 * k
+        pitch = -math.asin(d[1] / np.linalg.norm(d))
+        cams.append(pinhole(width, height, f, look_pose(p, yaw, pitch)))
+    return cams
