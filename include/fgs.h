@@ -384,9 +384,10 @@ fgs_status fgs_point_covariances(const float *xyz, const int64_t *d_n, int64_t n
  * within max_dist (ties by index; pairs without one are left out).  Increment
  * xi = (w, v) of T <- (Rodrigues(w), v) T from the normal equations of the
  * linearisation d + [[T p]_x, -I] xi; correspondences are renewed every iteration;
- * it stops early when |xi| < 1e-9, and keeps the pose when fewer than 6 pairs or
- * a singular system remain.  d_pose (double [12], row-major [R | t], the
- * world-from-source pose) holds the initial guess and receives the result.
+ * it stops early when |xi| < 1e-6 (a micro-radian and micrometre step), and
+ * keeps the pose when fewer than 6 pairs or a singular system remain.  d_pose
+ * (double [12], row-major [R | t], the world-from-source pose) holds the initial
+ * guess and receives the result.
  * d_stats (double [4]): cost and correspondences at the last evaluated pose, the
  * fraction of source points with a target point within overlap_dist there (the
  * keyframe test of Sec. III-C), iterations run.  ws: fgs_gicp_workspace_size(n_src_max). */

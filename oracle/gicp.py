@@ -15,7 +15,7 @@ Steps, in the paper's order and notation:
    point to T p_i within max_dist; d_i ~ N(0, C_q + R C_p R^T) (eq13); the
    increment xi = (w, v) of T <- (Rodrigues(w), v) T solves the normal equations
    of the linearisation d + [[T p]_x, -I] xi; correspondences are renewed every
-   iteration; it stops when |xi| < 1e-9, or keeps the pose when fewer than 6
+   iteration; it stops when |xi| < 1e-6, or keeps the pose when fewer than 6
    pairs or a singular system remain.
 
 Steps 1 and 2 and the neighbour sets of step 3 are integer decisions taken on
@@ -178,6 +178,6 @@ def gicp(src, src_cov, tgt, tgt_cov, pose0, iterations: int, max_dist: float, ov
         xi = -np.linalg.solve(H, b)
         Rw = rodrigues(xi[:3])
         T = np.hstack([Rw @ R, (Rw @ t + xi[3:])[:, None]])
-        if np.linalg.norm(xi) < 1e-9:
+        if np.linalg.norm(xi) < 1e-6:
             break
     return T, stats

@@ -769,7 +769,7 @@ __global__ void __launch_bounds__(64) k_gicp_solve(const double *__restrict__ pa
   }
   double nrm = 0.0;
   for (int r = 0; r < 6; ++r) nrm += xi[r] * xi[r];
-  if (sqrt(nrm) < 1e-9) ctl->done = 1;
+  if (sqrt(nrm) < 1e-6) ctl->done = 1;
 }
 
 __global__ void k_gicp_init(GicpCtl *ctl, double *stats) {
