@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--no-window", action="store_true", help="skip the keyframe-window measurement")
     p.add_argument("--no-convergence", action="store_true", help="skip the iterations-to-PSNR comparison")
     p.add_argument("--no-tracking", action="store_true", help="skip the GICP tracking / keyframe measurement")
+    p.add_argument("--no-ablation", action="store_true", help="skip the densification ablation")
     return p.parse_args()
 
 
@@ -273,6 +274,19 @@ def tracking_measure(frames: int = 20, warmup: int = 3):
                      "sparse map; keyframe when under 90% of the source points overlap the map"}
 
 
+def ablation_measure(seed_offset: int = 0):
+    """The densification ablation (tab6's variants) on 8 frames of the 1200x680
+    room trajectory from an empty map, 20 mapping iterations per frame."""
+    from paper_2503_01109_gb300 import synthetic as syn
+    from paper_2503_01109_gb300.ablation import densification_ablation
+    from paper_2503_01109_gb300.frames import render_targets
+
+    gt = syn.room_scene(N_GT, seed=3000 + seed_offset, kind="gt")
+    cams = syn.trajectory(8, seed=600 + seed_offset, width=W, height=H, f=F)
+    colors, depths = render_targets(gt, cams)
+    return densification_ablation(colors, depths, cams, capacity=4_000_000)
+
+
 def aggregate(ms_local: float, units_local: float, world: int, dist=None):
     """Whole-job throughput of N independent replicas: the slowest rank's time
     and the units all ranks processed (max / sum over ranks; no data exchange)."""
@@ -358,6 +372,9 @@ def run_ours(args):
     tracking = None
     if not args.no_tracking and rank == 0:
         tracking = tracking_measure()
+    ablation = None
+    if not args.no_ablation and rank == 0:
+        ablation = ablation_measure()
 
     peaks = load_peaks()
     roof = pipe.roofline(peaks, os.path.join(ROOT, "profiles"))
@@ -376,6 +393,7 @@ def run_ours(args):
         "window": window,
         "iters_to_psnr": conv,
         "tracking": tracking,
+        "densification_ablation": ablation,
     }
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(pipe)

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 SIZES = [(64, 48), (70, 45), (48, 64), (640, 480), (1200, 680)]
 
 
-def run_seed(W, H, seed, with_render=True, max_new=50000, capacity=None, prior=None, pose=None):
+def run_seed(W, H, seed, with_render=True, max_new=50000, capacity=None, prior=None, pose=None, grids=None):
     fr = syn.textured_frame(W, H, seed)
     cam = syn.pinhole(W, H, 0.9 * W, pose)
     rr = syn.fake_render(W, H, seed + 1) if with_render else None
@@ -27,7 +27,7 @@ def run_seed(W, H, seed, with_render=True, max_new=50000, capacity=None, prior=N
         rc = torch.as_tensor(rr["color"]).reshape(-1).cuda()
         rd = torch.as_tensor(rr["depth"]).reshape(-1).cuda()
         ra = torch.as_tensor(rr["alpha"]).reshape(-1).cuda()
-    prm = fgs.seed_params(max_new=max_new)
+    prm = fgs.seed_params(max_new=max_new, **(grids or {}))
     ws = fgs.ws_tensor(fgs.fgs_fourier_seed_workspace_size(W, H, max_new))
     mask = torch.zeros(H * W, dtype=torch.uint8, device="cuda")
     energy = torch.zeros(H * W, dtype=torch.float32, device="cuda")
@@ -39,6 +39,24 @@ def run_seed(W, H, seed, with_render=True, max_new=50000, capacity=None, prior=N
     return {"frame": fr, "cam": cam, "render": rr, "g": g, "mask": mask.view(H, W).cpu().numpy(),
             "energy": energy.view(H, W).cpu().numpy(), "num_new": int(num_new.item()), "threshold": int(thr.item()),
             "status": int(status.item())}
+
+
+@pytest.mark.parametrize("grids", [dict(m=8, n=8, alpha_h=4.0, alpha_l=4.0), dict(m=2, n=2, alpha_h=1.0, alpha_l=1.0)])
+def test_equidistant_seeding_bit_exact(cuda_device, grids):
+    # the equidistant densification of the ablation: one grid and one scale for every pixel
+    W, H = 640, 480
+    out = run_seed(W, H, seed=11, max_new=400_000, grids=grids)
+    fr, rr = out["frame"], out["render"]
+    ref = osd.seed_frame(fr["rgb"], fr["depth"], out["cam"], rr["color"], rr["depth"], rr["alpha"],
+                         max_new=400_000, energy32=out["energy"], **grids)
+    k = ref["xy"].shape[0]
+    assert out["num_new"] == k and np.array_equal(out["mask"], ref["mask"])
+    got = out["g"].to_scene(k)
+    assert np.abs(got["means"] - ref["gaussians"]["means"]).max() <= 1e-5 * np.abs(ref["gaussians"]["means"]).max()
+    assert np.abs(got["log_scales"] - ref["gaussians"]["log_scales"]).max() <= 1e-5
+    s = grids["m"]
+    ys, xs = ref["xy"][:, 1], ref["xy"][:, 0]
+    assert np.all(xs % s == 0) and np.all(ys % s == 0)       # one grid, whatever the frequency mask says
 
 
 @pytest.mark.parametrize("W,H", SIZES)
