@@ -270,6 +270,24 @@ fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads, fgs_gauss
                     fgs_gaussians *v, const fgs_adam_params *hp, int32_t *d_step,
                     void *stream);
 
+/* fgs_project_bwd_adam -- the end of a mapping iteration (Sec. III-D) in two
+ * passes instead of four calls: per Gaussian, the chain rule of fgs_project from
+ * grad2d (as fgs_project_bwd) plus the eq15 gradient with weight reg_weight (as
+ * fgs_scale_reg; 0 = none; its loss is added to *d_loss) is STORED into the 11
+ * geometric planes of grads (their old contents are ignored); then the Adam step of
+ * fgs_adam on all 14 parameters, with the RGB gradient taken from grads->rgb.
+ * Afterwards grads->rgb and every grad2d record read are zero again, ready for the
+ * next fgs_render_bwd_splats (the caller zeroes both once, before the first use);
+ * the geometric planes keep this step's gradients.  m and v as in fgs_adam; the
+ * step number as in fgs_adam.
+ * ws: fgs_project_bwd_adam_workspace_size(params->n) bytes, 16-byte aligned.
+ * err: INVALID_ARGUMENT for NULLs, small workspace, grads / m / v not covering params. */
+fgs_status fgs_project_bwd_adam(fgs_gaussians *params, const fgs_projected *proj, const fgs_camera *cams,
+                                int32_t n_views, float *grad2d, fgs_gaussians *grads, float reg_weight,
+                                float *d_loss, fgs_gaussians *m, fgs_gaussians *v, const fgs_adam_params *hp,
+                                int32_t *d_step, void *ws, size_t ws_bytes, void *stream);
+size_t fgs_project_bwd_adam_workspace_size(int64_t n);
+
 /* ---------------------------------------------------------------------------------
  * fgs_prune -- Gaussian pruning (Sec. III-A, "Gaussian Pruning"): removes every
  * Gaussian that has grown too large in some dimension or whose opacity is below a

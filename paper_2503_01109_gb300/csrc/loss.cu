@@ -91,33 +91,46 @@ __global__ void k_scale_reg(const float *__restrict__ ls, int64_t cap, int64_t n
 // Adam over the 14 parameter planes: blockIdx.y selects the plane.
 struct AdamPlanes {
   float *p[14];
-  const float *g[14];
+  float *g[14];
   float *m[14];
   float *v[14];
   float lr[14];
 };
 
-__global__ void k_adam_step_incr(int32_t *d_step) { *d_step += 1; }
+// Adam's bias corrections at step t as reciprocals: 1 / (1 - beta1^t), 1 / (1 - beta2^t).
+__device__ __forceinline__ float2 adam_bias(float b1, float b2, int t) {
+  return make_float2(1.f / (1.f - powf(b1, (float)t)), 1.f / (1.f - powf(b2, (float)t)));
+}
 
+// One bias-corrected Adam step of one parameter (r = adam_bias(b1, b2, t)).  The
+// square root and the quotient use the hardware approximations (a few ulp): the
+// step is a heuristic whose size needs no correctly rounded arithmetic, and the
+// IEEE sequences made the optimiser instruction-bound.
 __device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, float b1, float b2, float eps,
-                                         float lr, float c1, float c2) {
+                                         float lr, float2 r) {
   m = b1 * m + (1.f - b1) * g;
   v = b2 * v + (1.f - b2) * g * g;
-  p -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+  const float vh = v * r.y;
+  const float den = (vh > 0.f ? vh * rsqrtf(vh) : 0.f) + eps;
+  p -= __fdividef(lr * (m * r.x), den);
 }
+
+__global__ void k_adam_step_incr(int32_t *d_step) { *d_step += 1; }
 
 // VEC: four consecutive elements per thread with 16-byte loads (every plane
 // 16-byte aligned); else one element per thread.
+// Planes from zero_from on have their gradient cleared after it is read.
 template <bool VEC>
 __global__ void k_adam(AdamPlanes P, int64_t n, const int64_t *d_n, float b1, float b2, float eps, int32_t step,
-                       const int32_t *d_step) {
+                       const int32_t *d_step, int zero_from) {
   const int plane = blockIdx.y;
   const int64_t live = live_count(d_n, n);
   const int t = d_step ? *d_step : step;
-  const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+  const float2 r = adam_bias(b1, b2, t);
   const float lr = P.lr[plane];
   float *__restrict__ p = P.p[plane];
-  const float *__restrict__ g = P.g[plane];
+  float *__restrict__ g = P.g[plane];
+  const bool zero = plane >= zero_from;
   float *__restrict__ m = P.m[plane];
   float *__restrict__ v = P.v[plane];
   const int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * (VEC ? 4 : 1);
@@ -125,22 +138,24 @@ __global__ void k_adam(AdamPlanes P, int64_t n, const int64_t *d_n, float b1, fl
   if (VEC && i0 + 4 <= live) {
     float4 pp = *reinterpret_cast<const float4 *>(p + i0), gg = *reinterpret_cast<const float4 *>(g + i0);
     float4 mm = *reinterpret_cast<const float4 *>(m + i0), vv = *reinterpret_cast<const float4 *>(v + i0);
-    adam_one(pp.x, gg.x, mm.x, vv.x, b1, b2, eps, lr, c1, c2);
-    adam_one(pp.y, gg.y, mm.y, vv.y, b1, b2, eps, lr, c1, c2);
-    adam_one(pp.z, gg.z, mm.z, vv.z, b1, b2, eps, lr, c1, c2);
-    adam_one(pp.w, gg.w, mm.w, vv.w, b1, b2, eps, lr, c1, c2);
+    adam_one(pp.x, gg.x, mm.x, vv.x, b1, b2, eps, lr, r);
+    adam_one(pp.y, gg.y, mm.y, vv.y, b1, b2, eps, lr, r);
+    adam_one(pp.z, gg.z, mm.z, vv.z, b1, b2, eps, lr, r);
+    adam_one(pp.w, gg.w, mm.w, vv.w, b1, b2, eps, lr, r);
     *reinterpret_cast<float4 *>(p + i0) = pp;
     *reinterpret_cast<float4 *>(m + i0) = mm;
     *reinterpret_cast<float4 *>(v + i0) = vv;
+    if (zero) *reinterpret_cast<float4 *>(g + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
   const int64_t i1 = VEC ? min(i0 + 4, live) : i0 + 1;
   for (int64_t i = i0; i < i1; ++i) {
     float pi = p[i], mi = m[i], vi = v[i];
-    adam_one(pi, g[i], mi, vi, b1, b2, eps, lr, c1, c2);
+    adam_one(pi, g[i], mi, vi, b1, b2, eps, lr, r);
     p[i] = pi;
     m[i] = mi;
     v[i] = vi;
+    if (zero) g[i] = 0.f;
   }
 }
 
@@ -211,17 +226,13 @@ extern "C" fgs_status fgs_scale_reg(const fgs_gaussians *g, float weight, fgs_ga
   return FGS_OK;
 }
 
-extern "C" fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads, fgs_gaussians *m,
-                               fgs_gaussians *v, const fgs_adam_params *hp, int32_t *d_step, void *stream) {
-  if (!gaussians_ok(params, "params") || !gaussians_ok(grads, "grads") || !gaussians_ok(m, "m") ||
-      !gaussians_ok(v, "v"))
-    return FGS_ERR_INVALID_ARGUMENT;
-  FGS_CHECK_ARG(hp, "fgs_adam: NULL hyper-parameters");
-  FGS_CHECK_ARG(d_step || hp->step >= 1, "fgs_adam: step must be >= 1");
+namespace fgs {
+fgs_status launch_adam(fgs_gaussians *params, fgs_gaussians *grads, fgs_gaussians *m, fgs_gaussians *v,
+                       const fgs_adam_params *hp, int32_t *d_step, int zero_from, cudaStream_t st) {
   if (params->n == 0) return FGS_OK;
   AdamPlanes P;
-  auto fill = [&](int base, int cnt, float *pp, const float *gp, float *mp, float *vp, int64_t pc, int64_t gc,
-                  int64_t mc, int64_t vc, float lr) {
+  auto fill = [&](int base, int cnt, float *pp, float *gp, float *mp, float *vp, int64_t pc, int64_t gc, int64_t mc,
+                  int64_t vc, float lr) {
     for (int k = 0; k < cnt; ++k) {
       P.p[base + k] = pp + k * pc;
       P.g[base + k] = gp + k * gc;
@@ -237,7 +248,6 @@ extern "C" fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads
   fill(10, 1, params->opacity_logits, grads->opacity_logits, m->opacity_logits, v->opacity_logits, pc, gc, mc, vc,
        hp->lr[3]);
   fill(11, 3, params->rgb, grads->rgb, m->rgb, v->rgb, pc, gc, mc, vc, hp->lr[4]);
-  cudaStream_t st = as_stream(stream);
   if (d_step) {
     k_adam_step_incr<<<1, 1, 0, st>>>(d_step);
     count_launch();
@@ -250,13 +260,25 @@ extern "C" fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads
   const unsigned bx = (unsigned)std::max<int64_t>(1, (params->n + per_block - 1) / per_block);
   if (aligned)
     k_adam<true><<<dim3(bx, 14), 256, 0, st>>>(P, params->n, params->d_n, hp->beta1, hp->beta2, hp->eps, hp->step,
-                                               d_step);
+                                               d_step, zero_from);
   else
     k_adam<false><<<dim3(bx, 14), 256, 0, st>>>(P, params->n, params->d_n, hp->beta1, hp->beta2, hp->eps, hp->step,
-                                                d_step);
+                                                d_step, zero_from);
   count_launch();
   FGS_CHECK_LAUNCH("fgs_adam");
   return FGS_OK;
+}
+}  // namespace fgs
+
+extern "C" fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads, fgs_gaussians *m,
+                               fgs_gaussians *v, const fgs_adam_params *hp, int32_t *d_step, void *stream) {
+  if (!gaussians_ok(params, "params") || !gaussians_ok(grads, "grads") || !gaussians_ok(m, "m") ||
+      !gaussians_ok(v, "v"))
+    return FGS_ERR_INVALID_ARGUMENT;
+  FGS_CHECK_ARG(hp, "fgs_adam: NULL hyper-parameters");
+  FGS_CHECK_ARG(d_step || hp->step >= 1, "fgs_adam: step must be >= 1");
+  // zero_from = 14: the gradient is only read (the struct is const to the caller)
+  return launch_adam(params, const_cast<fgs_gaussians *>(grads), m, v, hp, d_step, 14, as_stream(stream));
 }
 
 // ---------------------------------------------------------------------------------

@@ -142,30 +142,19 @@ __global__ void k_project(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_
 // ---------------------------------------------------------------------------------
 // Adjoint.  grad2d[v][stride] records: mean2d x, y, conic a, b, c, opacity, depth, -.
 // Gradients are added to grads' planes; the thread owns its Gaussian, so no atomics.
-__global__ void k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_n, DevViews vs,
-                              const int32_t *__restrict__ radius, const float4 *__restrict__ grad2d,
-                              int64_t stride, GaussGrads out) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n || i >= live_count(d_n, n)) return;
-  GaussLocal L;
-  load_gaussian(g, i, L);
-  // The kernel only adds to the gradient planes: their old values are loaded
-  // here, together, so that their latencies overlap instead of each
-  // read-modify-write waiting for the one before it.
-  const int64_t c = out.cap;
-  const float old_logit = out.logits[i];
-  float old_mu[3], old_ls[3], old_q[4];
+// The chain rule of the projection for Gaussian i over every view: the gradients
+// of its means (g[0..2]), log-scales (g[3..5]), quaternion (g[6..9]) and opacity
+// logit (g[10]) from its splat records' gradients in grad2d.  Returns the mask of
+// the views whose record it read (0 when no view projects it; then only g[10] may
+// be non-zero).
+__device__ __forceinline__ uint32_t chain_rule(const GaussLocal &L, int64_t i, const DevViews &vs,
+                                               const int32_t *__restrict__ radius, const float4 *grad2d,
+                                               int64_t stride, float *g) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    old_mu[k] = out.means[k * c + i];
-    old_ls[k] = out.log_scales[k * c + i];
-  }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) old_q[k] = out.quats[k * c + i];
-  float gmu[3] = {0.f, 0.f, 0.f};
+  for (int k = 0; k < 11; ++k) g[k] = 0.f;
   float GSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (symmetric, xx xy xz yy yz zz)
   float go = 0.f;
-  bool any = false;
+  uint32_t read = 0u;
 #pragma unroll 1
   for (int v = 0; v < vs.n; ++v) {
     const int64_t r = v * stride + i;
@@ -173,7 +162,7 @@ __global__ void k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict_
     const DevCam &cm = vs.cam[v];
     ViewLocal V;
     if (!project_view(L, cm, V)) continue;
-    any = true;
+    read |= 1u << v;
     const float4 gA4 = grad2d[2 * r], gB4 = grad2d[2 * r + 1];
     const float rdet = 1.0f / V.det;
     const float A = V.c * rdet, B = -V.b * rdet, C = V.a * rdet;
@@ -237,13 +226,10 @@ __global__ void k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict_
     gp2 += -(gA4.x * cm.fx * x + gA4.y * cm.fy * y) * rz2 + gB4.z;
     // p = R_cam mu + t
 #pragma unroll
-    for (int k = 0; k < 3; ++k) gmu[k] += Rc[k] * gp0 + Rc[3 + k] * gp1 + Rc[6 + k] * gp2;
+    for (int k = 0; k < 3; ++k) g[k] += Rc[k] * gp0 + Rc[3 + k] * gp1 + Rc[6 + k] * gp2;
   }
-  out.logits[i] = old_logit + go * L.o * (1.f - L.o);
-  if (!any) return;
-  out.means[i] = old_mu[0] + gmu[0];
-  out.means[c + i] = old_mu[1] + gmu[1];
-  out.means[2 * c + i] = old_mu[2] + gmu[2];
+  g[10] = go * L.o * (1.f - L.o);
+  if (!read) return 0u;
   // Sigma = M M^T, M = R diag(s): dL/dM = 2 GSig M
   float M[9];
 #pragma unroll
@@ -261,7 +247,7 @@ __global__ void k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict_
       gs += gm * L.R[3 * r + k];
       gR[3 * r + k] = gm * L.s[k];
     }
-    out.log_scales[k * c + i] = old_ls[k] + gs * L.s[k];
+    g[3 + k] = gs * L.s[k];
   }
   const float w = L.qn[0], qx = L.qn[1], qy = L.qn[2], qz = L.qn[3];
   float gq[4];
@@ -274,8 +260,123 @@ __global__ void k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict_
                  gR[5] * qy + gR[6] * qx + gR[7] * qy);
   const float dot = w * gq[0] + qx * gq[1] + qy * gq[2] + qz * gq[3];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) out.quats[k * c + i] = old_q[k] + (gq[k] - L.qn[k] * dot) * L.qinv;
+  for (int k = 0; k < 4; ++k) g[6 + k] = (gq[k] - L.qn[k] * dot) * L.qinv;
+  return read;
 }
+
+__global__ void __launch_bounds__(256, 3) k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_n, DevViews vs,
+                              const int32_t *__restrict__ radius, const float4 *__restrict__ grad2d,
+                              int64_t stride, GaussGrads out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n || i >= live_count(d_n, n)) return;
+  GaussLocal L;
+  load_gaussian(g, i, L);
+  // The kernel only adds to the gradient planes: their old values are loaded
+  // here, together, so that their latencies overlap instead of each
+  // read-modify-write waiting for the one before it.
+  const int64_t c = out.cap;
+  const float old_logit = out.logits[i];
+  float old_mu[3], old_ls[3], old_q[4];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    old_mu[k] = out.means[k * c + i];
+    old_ls[k] = out.log_scales[k * c + i];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) old_q[k] = out.quats[k * c + i];
+  float gr[11];
+  const bool any = chain_rule(L, i, vs, radius, grad2d, stride, gr) != 0u;
+  out.logits[i] = old_logit + gr[10];
+  if (!any) return;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    out.means[k * c + i] = old_mu[k] + gr[k];
+    out.log_scales[k * c + i] = old_ls[k] + gr[3 + k];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out.quats[k * c + i] = old_q[k] + gr[6 + k];
+}
+
+constexpr int FUSED_THREADS = 256;
+
+// The first half of the end of a mapping iteration, per Gaussian: the chain rule
+// of the projection plus the eq15 regulariser's gradient (as fgs_scale_reg),
+// STORED into the 11 geometric gradient planes (nothing is read from them); the
+// grad2d records read are cleared; per-block FP64 partial sums of the eq15 loss.
+// The Adam pass that follows reads these planes and the RGB gradient.
+__global__ void __launch_bounds__(FUSED_THREADS, 3)
+    k_project_bwd_reg(GaussPtrs gp, int64_t n, const int64_t *__restrict__ d_n, DevViews vs,
+                      const int32_t *__restrict__ radius, float4 *__restrict__ grad2d, int64_t stride,
+                      GaussGrads out, float reg_weight, double *__restrict__ partials) {
+  __shared__ double red[FUSED_THREADS / 32];
+  const int64_t live = live_count(d_n, n);
+  const int tid = threadIdx.x;
+  const int64_t i = blockIdx.x * (int64_t)FUSED_THREADS + tid;
+  float reg_val = 0.f;
+  const float wn = live > 0 ? reg_weight / (float)live : 0.f;
+  if (i < live) {
+    GaussLocal L;
+    load_gaussian(gp, i, L);
+    float gq[11];
+    const uint32_t read = chain_rule(L, i, vs, radius, grad2d, stride, gq);
+    if (reg_weight != 0.f) {  // eq15, as fgs_scale_reg
+      const float s1 = L.s[0], s2 = L.s[1], s3 = L.s[2];
+      const float mm = 0.5f * (s1 + s2);
+      reg_val = fabsf(s1 - mm) + fabsf(s2 - mm) + fabsf(s3);
+      const float sg1 = s1 - mm > 0.f ? 1.f : (s1 - mm < 0.f ? -1.f : 0.f);
+      const float sg2 = s2 - mm > 0.f ? 1.f : (s2 - mm < 0.f ? -1.f : 0.f);
+      gq[3] += wn * (0.5f * sg1 - 0.5f * sg2) * s1;
+      gq[4] += wn * (0.5f * sg2 - 0.5f * sg1) * s2;
+      gq[5] += wn * (s3 > 0.f ? 1.f : 0.f) * s3;
+    }
+    const int64_t c = out.cap;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      out.means[k * c + i] = gq[k];
+      out.log_scales[k * c + i] = gq[3 + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out.quats[k * c + i] = gq[6 + k];
+    out.logits[i] = gq[10];
+    // The records read are cleared only now, after their values were used: a
+    // store issued right behind the load of the same address waits for that
+    // load in the memory pipeline and holds up the loads queued after it.
+    for (uint32_t b = read; b; b &= b - 1) {
+      const int64_t r = (int64_t)(__ffs(b) - 1) * stride + i;
+      grad2d[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      grad2d[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  float s = reg_val * wn;  // warp sums in FP32, block and grid sums in FP64 (as fgs_scale_reg)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((tid & 31) == 0) red[tid >> 5] = (double)s;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < FUSED_THREADS / 32; ++w) t += red[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
+// *d_loss += the sum of the per-block partial sums (FP64 over the blocks)
+__global__ void k_fused_reduce(const double *__restrict__ partials, int64_t count, float *d_loss) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < count; i += 256) s += partials[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *d_loss += (float)red[0];
+}
+
+// Adam over the 14 planes (loss.cu); planes from zero_from on have their gradient
+// cleared after it is read.
+fgs_status launch_adam(fgs_gaussians *params, fgs_gaussians *grads, fgs_gaussians *m, fgs_gaussians *v,
+                       const fgs_adam_params *hp, int32_t *d_step, int zero_from, cudaStream_t st);
 
 fgs_status launch_project_bwd(const fgs_gaussians *g, const DevViews &vs, const int32_t *radius,
                               const float *grad2d, int64_t stride, fgs_gaussians *grads,
@@ -330,4 +431,39 @@ extern "C" fgs_status fgs_project_bwd(const fgs_gaussians *g, const fgs_projecte
   DevViews vs;
   if (!make_views(cams, n_views, 16, 16, &vs)) return FGS_ERR_INVALID_ARGUMENT;
   return launch_project_bwd(g, vs, proj->radius, grad2d, proj->stride, grads, as_stream(stream));
+}
+
+extern "C" size_t fgs_project_bwd_adam_workspace_size(int64_t n) {
+  return align_up(sizeof(double) * (size_t)std::max<int64_t>((n + FUSED_THREADS - 1) / FUSED_THREADS, 1));
+}
+
+extern "C" fgs_status fgs_project_bwd_adam(fgs_gaussians *params, const fgs_projected *proj, const fgs_camera *cams,
+                                           int32_t n_views, float *grad2d, fgs_gaussians *grads, float reg_weight,
+                                           float *d_loss, fgs_gaussians *m, fgs_gaussians *v,
+                                           const fgs_adam_params *hp, int32_t *d_step, void *ws, size_t ws_bytes,
+                                           void *stream) {
+  if (!gaussians_ok(params, "params") || !gaussians_ok(grads, "grads") || !gaussians_ok(m, "m") ||
+      !gaussians_ok(v, "v"))
+    return FGS_ERR_INVALID_ARGUMENT;
+  FGS_CHECK_ARG(proj && proj->radius && proj->stride >= params->n && grad2d && hp && d_loss,
+                "fgs_project_bwd_adam: NULL argument");
+  FGS_CHECK_ARG((reinterpret_cast<uintptr_t>(grad2d) & 15) == 0, "fgs_project_bwd_adam: grad2d alignment");
+  FGS_CHECK_ARG(grads->n >= params->n && m->n >= params->n && v->n >= params->n,
+                "fgs_project_bwd_adam: grads, m and v must cover params");
+  FGS_CHECK_ARG(d_step || hp->step >= 1, "fgs_project_bwd_adam: step must be >= 1");
+  FGS_CHECK_ARG(ws && ws_bytes >= fgs_project_bwd_adam_workspace_size(params->n),
+                "fgs_project_bwd_adam: workspace");
+  DevViews vs;
+  if (!make_views(cams, n_views, 16, 16, &vs)) return FGS_ERR_INVALID_ARGUMENT;
+  if (params->n == 0) return FGS_OK;
+  cudaStream_t st = as_stream(stream);
+  const int64_t blocks = (params->n + FUSED_THREADS - 1) / FUSED_THREADS;
+  k_project_bwd_reg<<<(unsigned)blocks, FUSED_THREADS, 0, st>>>(
+      gauss_ptrs(params), params->n, params->d_n, vs, proj->radius, reinterpret_cast<float4 *>(grad2d),
+      proj->stride, gauss_grads(grads), reg_weight, static_cast<double *>(ws));
+  k_fused_reduce<<<1, 256, 0, st>>>(static_cast<double *>(ws), blocks, d_loss);
+  count_launch(2);
+  FGS_CHECK_LAUNCH("fgs_project_bwd_adam");
+  // Adam over all 14 planes; it clears the RGB gradient planes after reading them
+  return launch_adam(params, grads, m, v, hp, d_step, /*zero_from=*/11, st);
 }

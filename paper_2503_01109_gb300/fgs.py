@@ -143,6 +143,9 @@ _SIGS = {
     "fgs_gicp": ([c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                   c_void_p, c_void_p, c_void_p, c_size_t, c_void_p], c_int32),
     "fgs_gicp_workspace_size": ([c_int64], c_size_t),
+    "fgs_project_bwd_adam": ([c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_float, c_void_p, c_void_p,
+                              c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p], c_int32),
+    "fgs_project_bwd_adam_workspace_size": ([c_int64], c_size_t),
     "fgs_last_error": ([], ctypes.c_char_p),
     "fgs_version": ([], c_int32),
     "fgs_launch_count": ([], c_int64),
@@ -528,6 +531,25 @@ def fgs_gicp(src, src_cov, n_src: torch.Tensor, tgt, tgt_cov, g: Grid, cell_star
     _check(lib().fgs_gicp(_ptr(src), _ptr(src_cov), _ptr(n_src), src.shape[0], _ptr(tgt), _ptr(tgt_cov),
                           ctypes.byref(g), _ptr(cell_start), _ptr(order), ctypes.byref(params), _ptr(pose),
                           _ptr(stats), _ptr(ws), ws.numel() * ws.element_size(), _stream()), "fgs_gicp")
+
+
+def fgs_project_bwd_adam_workspace_size(n: int) -> int:
+    return int(lib().fgs_project_bwd_adam_workspace_size(int(n)))
+
+
+def fgs_project_bwd_adam(g: GaussianMap, proj: Projection, cams: list, grad2d, grads: GaussianMap, reg_weight: float,
+                         d_loss, m: GaussianMap, v: GaussianMap, lr=DEFAULT_LR, beta1=0.9, beta2=0.999, eps=1e-15,
+                         step: int = 1, d_step=None, ws=None, use_device_count=False):
+    hp = AdamParams()
+    for k in range(5):
+        hp.lr[k] = float(lr[k])
+    hp.beta1, hp.beta2, hp.eps, hp.step = beta1, beta2, eps, int(step)
+    gs, gr, ms, vs = (x.struct(use_device_count) for x in (g, grads, m, v))
+    ps = proj.struct()
+    _check(lib().fgs_project_bwd_adam(ctypes.byref(gs), ctypes.byref(ps), camera_array(cams), len(cams), _ptr(grad2d),
+                                      ctypes.byref(gr), float(reg_weight), _ptr(d_loss), ctypes.byref(ms),
+                                      ctypes.byref(vs), ctypes.byref(hp), _ptr(d_step), _ptr(ws),
+                                      ws.numel() * ws.element_size(), _stream()), "fgs_project_bwd_adam")
 
 
 def fgs_memset_async(t: torch.Tensor, value: int = 0):

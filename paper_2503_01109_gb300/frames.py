@@ -92,6 +92,7 @@ class TimedMapper(Mapper):
                                       dD, dA, self.grad2d, self.grads, self.status, self.use_dc)
         with self.timer.span("project_bwd"):
             fgs.fgs_project_bwd(self.g, self.proj, self.cams, self.grad2d, self.grads, self.use_dc)
+        self._clean = False
 
     def iteration(self):
         self._in_iteration = True
@@ -101,6 +102,14 @@ class TimedMapper(Mapper):
         with self.timer.span("loss"):
             fgs.fgs_loss(self.cams, self.frame.color, self.frame.depth, self.color_gt, self.depth_gt, *self.loss_w,
                          self.dC, self.dD, self.loss_acc, self.ws_loss)
+        if self.fused_tail:
+            self.ensure_clean()
+            with self.timer.span("render_bwd"):
+                fgs.fgs_render_bwd_splats(self.g, self.proj, self.cams, self.til, self.ids, self.ranges, self.frame,
+                                          self.dC, self.dD, None, self.grad2d, self.grads, self.status, self.use_dc)
+            with self.timer.span("project_bwd_adam"):
+                self.fused_tail_step()
+            return
         self.backward(self.dC, self.dD)
         if self.reg_w != 0.0:
             fgs.fgs_scale_reg(self.g, self.reg_w, self.grads, self.loss_acc, self.ws_reg, self.use_dc)

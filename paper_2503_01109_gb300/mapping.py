@@ -25,7 +25,8 @@ PAPER_REG = 0.01
 
 class Mapper:
     def __init__(self, g: fgs.GaussianMap, cams: list, til: fgs.Tiling | None = None, pair_capacity: int | None = None,
-                 loss_w=PAPER_LOSS, reg_w: float = PAPER_REG, lr=fgs.DEFAULT_LR, use_device_count: bool = True):
+                 loss_w=PAPER_LOSS, reg_w: float = PAPER_REG, lr=fgs.DEFAULT_LR, use_device_count: bool = True,
+                 fused_tail: bool = True):
         dev = g.buf.device
         self.g, self.cams = g, list(cams)
         self.til = til or fgs.tiling(16, 16, 128)
@@ -56,6 +57,11 @@ class Mapper:
         self.ws_loss = fgs.ws_tensor(fgs.fgs_loss_workspace_size(self.cams), dev)
         self.ws_reg = fgs.ws_tensor(fgs.fgs_scale_reg_workspace_size(cap), dev)
         self.d_step = torch.zeros(1, dtype=torch.int32, device=dev)
+        # the iteration's tail (projection adjoint, eq15, Adam) as one fused call that
+        # leaves the RGB gradient and grad2d zero; `_clean` tracks that state
+        self.fused_tail = bool(fused_tail)
+        self.ws_fused = fgs.ws_tensor(fgs.fgs_project_bwd_adam_workspace_size(cap), dev)
+        self._clean = True
         self.ws_prune = None
         self.num_kept = torch.zeros(1, dtype=torch.int64, device=dev)
         self.color_gt = torch.zeros_like(self.frame.color)
@@ -86,6 +92,23 @@ class Mapper:
         fgs.fgs_memset_async(self.grads.buf)
         fgs.fgs_render_bwd(self.g, self.proj, self.cams, self.til, self.ids, self.ranges, self.frame, dC, dD, dA,
                            self.grad2d, self.grads, self.status, self.use_dc)
+        self._clean = False
+
+    def ensure_clean(self):
+        """Zeroes the RGB gradient and grad2d unless the last fused tail left them so."""
+        if not self._clean:
+            fgs.fgs_memset_async(self.grads.buf)
+            fgs.fgs_memset_async(self.grad2d)
+            self._clean = True
+
+    def fused_tail_step(self):
+        """a8 + eq15 + a9 in one pass per Gaussian (fgs_project_bwd_adam)."""
+        self.host_step += 1
+        fgs.fgs_project_bwd_adam(self.g, self.proj, self.cams, self.grad2d, self.grads, self.reg_w, self.loss_acc,
+                                 self.m, self.v, self.lr, step=self.host_step,
+                                 d_step=self.d_step if self.use_dc else None, ws=self.ws_fused,
+                                 use_device_count=self.use_dc)
+        self._clean = True
 
     def iteration(self):
         """One mapping iteration a1-a9 against the current target."""
@@ -93,6 +116,12 @@ class Mapper:
         fgs.fgs_memset_async(self.loss_acc)
         fgs.fgs_loss(self.cams, self.frame.color, self.frame.depth, self.color_gt, self.depth_gt, *self.loss_w,
                      self.dC, self.dD, self.loss_acc, self.ws_loss)
+        if self.fused_tail:
+            self.ensure_clean()
+            fgs.fgs_render_bwd_splats(self.g, self.proj, self.cams, self.til, self.ids, self.ranges, self.frame,
+                                      self.dC, self.dD, None, self.grad2d, self.grads, self.status, self.use_dc)
+            self.fused_tail_step()
+            return
         self.backward(self.dC, self.dD)
         if self.reg_w != 0.0:
             fgs.fgs_scale_reg(self.g, self.reg_w, self.grads, self.loss_acc, self.ws_reg, self.use_dc)

@@ -29,12 +29,18 @@ class Window(Mapper):
         n = self.g.capacity if self.use_dc else self.g.n
         fgs.fgs_bin_sort(self.proj, n, self.cams, self.til, self.ws_bin, self.tile_keys, self.ids, self.ranges,
                          self.num_pairs, self.status)
-        fgs.fgs_memset_async(self.grads.buf)
-        fgs.fgs_memset_async(self.grad2d)
+        if self.fused_tail:
+            self.ensure_clean()
+        else:
+            fgs.fgs_memset_async(self.grads.buf)
+            fgs.fgs_memset_async(self.grad2d)
         fgs.fgs_memset_async(self.loss_acc)
         fgs.fgs_render_window(self.g, self.proj, self.cams, self.til, self.ids, self.ranges, self.color_gt,
                               self.depth_gt, *self.loss_w, self.frame, self.dC, self.dD, self.grad2d, self.grads,
                               self.loss_acc, self.ws_win, self.status, self.use_dc)
+        if self.fused_tail:
+            self.fused_tail_step()
+            return
         fgs.fgs_project_bwd(self.g, self.proj, self.cams, self.grad2d, self.grads, self.use_dc)
         if self.reg_w != 0.0:
             fgs.fgs_scale_reg(self.g, self.reg_w, self.grads, self.loss_acc, self.ws_reg, self.use_dc)

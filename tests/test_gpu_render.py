@@ -247,7 +247,9 @@ def test_mapping_iteration_tiny_config(cuda_device):
     tgt = syn.tiny_scene(2000, 1)
     st_t = orr.render_views(tgt, [cam])
     Cg, Dg = st_t["out"][0]["color"], st_t["out"][0]["depth"]
-    m = make_mapper(sc, [cam], loss_w=(1.0, 1.0, 0.0), reg_w=0.0)
+    # the separate end of the iteration keeps the gradients for inspection (the
+    # fused one consumes them; its parity with this path is tested on its own)
+    m = make_mapper(sc, [cam], loss_w=(1.0, 1.0, 0.0), reg_w=0.0, fused_tail=False)
     cg, dg = fgs.pack_images([cam], [Cg], [Dg])
     m.set_target(cg, dg)
     m.iteration()

@@ -68,7 +68,7 @@ def test_window_gradients_match_oracle(cuda_device):
     sc = syn.tiny_scene(2000, seed=11)
     frs = [syn.textured_frame(c["width"], c["height"], 20 + i) for i, c in enumerate(cams)]
     cg, dg = fgs.pack_images(cams, [f["rgb"] for f in frs], [f["depth"] for f in frs])
-    win = Window(fgs.GaussianMap.from_scene(sc), cams, fgs.tiling(16, 16, 128), reg_w=0.0)
+    win = Window(fgs.GaussianMap.from_scene(sc), cams, fgs.tiling(16, 16, 128), reg_w=0.0, fused_tail=False)
     win.set_target(cg, dg)
     win.iteration()
     torch.cuda.synchronize()
