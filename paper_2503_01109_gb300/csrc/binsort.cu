@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
                                                                 const int64_t *d_count, int64_t host_count,
                                                                 int64_t cap, int shift, int nbits,
                                                                 uint32_t *__restrict__ counts) {
+  pdl_enter();
   __shared__ uint32_t hist[kSortThreads / 32][256];
   const int warp = threadIdx.x >> 5;
   for (int d = threadIdx.x & 31; d < 256; d += 32) hist[warp][d] = 0;
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
 // in place; digit_total[d] receives the digit's item count.
 __global__ void __launch_bounds__(kScanThreads) k_digit_scan(uint32_t *__restrict__ counts, int nb,
                                                              uint32_t *__restrict__ digit_total) {
+  pdl_enter();
   __shared__ uint32_t warp_sum[kScanThreads / 32];
   const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *row = counts + (size_t)d * nb;
@@ -151,6 +153,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const int64_t *d_count,
     int64_t host_count, int64_t cap, int shift, int nbits, const uint32_t *__restrict__ offsets,
     const uint32_t *__restrict__ digit_total) {
+  pdl_enter();
   constexpr int W = kSortThreads / 32;
   __shared__ uint32_t s_whist[W][256];  // per warp and digit: count, then the warp's offset in the tile's run
   __shared__ uint32_t s_base[256];      // output position of this block's next item of each digit
@@ -237,10 +240,10 @@ static fgs_status radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
     const int nbits = std::min(8, bits - shift);
     uint32_t *ki = (p & 1) ? k1 : k0, *vi = (p & 1) ? v1 : v0;
     uint32_t *ko = (p & 1) ? k0 : k1, *vo = (p & 1) ? v0 : v1;
-    k_radix_upsweep<<<nblocks, kSortThreads, 0, st>>>(ki, d_count, host_count, cap, shift, nbits, counts);
-    k_digit_scan<<<256, kScanThreads, 0, st>>>(counts, nblocks, digit_total);
-    k_radix_downsweep<<<nblocks, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_count, host_count, cap, shift,
-                                                        nbits, counts, digit_total);
+    pdl_launch(k_radix_upsweep, nblocks, kSortThreads, 0, st, ki, d_count, host_count, cap, shift, nbits, counts);
+    pdl_launch(k_digit_scan, 256, kScanThreads, 0, st, counts, nblocks, digit_total);
+    pdl_launch(k_radix_downsweep, nblocks, kSortThreads, 0, st, ki, vi, ko, vo, d_count, host_count, cap, shift,
+               nbits, counts, digit_total);
     count_launch(3);
   }
   FGS_CHECK_LAUNCH("radix_sort");
@@ -276,6 +279,7 @@ __device__ __forceinline__ int64_t record_of(int64_t j, int64_t n, int64_t strid
 __global__ void __launch_bounds__(kScanBlock) k_vis_count(const int32_t *__restrict__ radius,
                                                           const uint2 *__restrict__ rect, int64_t n, int64_t stride,
                                                           int64_t R, uint32_t *__restrict__ bsum) {
+  pdl_enter();
   __shared__ uint32_t red[kScanBlock / 32];
   const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
   const bool vis = j < R && record_visible(radius, rect, record_of(j, n, stride));
@@ -292,6 +296,7 @@ __global__ void __launch_bounds__(kScanBlock) k_vis_count(const int32_t *__restr
 
 // Exclusive scan of nb block counts in place by one CTA; *total = their sum.
 __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *__restrict__ bsum, int nb, int64_t *total) {
+  pdl_enter();
   __shared__ unsigned long long part[1024];
   const int per = (nb + 1023) / 1024;
   const int lo = threadIdx.x * per, hi = min(nb, lo + per);
@@ -319,6 +324,7 @@ __global__ void __launch_bounds__(kScanBlock) k_vis_scatter(const float4 *__rest
                                                             const uint2 *__restrict__ rect, int64_t n, int64_t stride,
                                                             int64_t R, const uint32_t *__restrict__ bsum,
                                                             uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+  pdl_enter();
   __shared__ uint32_t wsum[kScanBlock / 32];
   const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -446,6 +452,7 @@ __global__ void __launch_bounds__(kRecChunk) k_row_count(RowGeom G, const uint32
                                                          const uint2 *__restrict__ rect,
                                                          const int64_t *__restrict__ d_vis, int64_t nb_cap,
                                                          uint32_t *__restrict__ rowcnt) {
+  pdl_enter();
   __shared__ uint32_t s_rows[kMaxRows];
   const int64_t R = *d_vis;
   const int64_t nb = (R + kRecChunk - 1) / kRecChunk;
@@ -468,6 +475,7 @@ __global__ void __launch_bounds__(kRecChunk) k_row_count(RowGeom G, const uint32
 // writes the row's total.
 __global__ void __launch_bounds__(1024) k_row_scan(const int64_t *__restrict__ d_vis, int64_t nb_cap,
                                                    uint32_t *__restrict__ rowcnt, uint32_t *__restrict__ rowtot) {
+  pdl_enter();
   __shared__ unsigned long long part[1024];
   const int64_t nb = (*d_vis + kRecChunk - 1) / kRecChunk;
   const uint64_t total = cta_scan_inplace(rowcnt + (int64_t)blockIdx.x * nb_cap, nb, part);
@@ -485,6 +493,7 @@ __global__ void __launch_bounds__(1024) k_row_starts(RowGeom G, const uint32_t *
                                                      int64_t *__restrict__ d_nchunks, int32_t *__restrict__ d_status,
                                                      int64_t *__restrict__ d_num_pairs,
                                                      int64_t *__restrict__ d_sort_count) {
+  pdl_enter();
   __shared__ unsigned long long part[1024];
   __shared__ int s_over;
   const int NR = G.n_rows;
@@ -535,6 +544,7 @@ __global__ void __launch_bounds__(kRecChunk) k_row_emit(RowGeom G, const uint32_
                                                         const uint32_t *__restrict__ rowcnt,
                                                         const uint32_t *__restrict__ row_start,
                                                         uint32_t *__restrict__ rowlist) {
+  pdl_enter();
   constexpr int NW = kRecChunk / 32;
   __shared__ uint32_t s_wc[NW][32];
   __shared__ int s_lo, s_hi;
@@ -623,6 +633,7 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_count(RowGeom G, const floa
                                                            const int64_t *__restrict__ d_nchunks,
                                                            uint32_t *__restrict__ tcnt,
                                                            EntryInfo *__restrict__ einfo) {
+  pdl_enter();
   extern __shared__ uint32_t s_cnt[];  // [tx_max]
   const int64_t NC = *d_nchunks;
   for (int64_t c = blockIdx.x; c < NC; c += gridDim.x) {
@@ -657,6 +668,7 @@ __global__ void __launch_bounds__(256) k_tile_chunk_scan(RowGeom G, const uint32
                                                          const uint32_t *__restrict__ tcnt,
                                                          uint32_t *__restrict__ tpre, uint32_t *__restrict__ ttot,
                                                          unsigned long long *__restrict__ rowp) {
+  pdl_enter();
   __shared__ unsigned long long red[8];
   const int g = blockIdx.x;
   const int v = view_of_row(G, g);
@@ -691,6 +703,7 @@ __global__ void __launch_bounds__(1024) k_tile_row_starts(RowGeom G, unsigned lo
                                                           int64_t pair_cap, int64_t *__restrict__ d_num_pairs,
                                                           int32_t *__restrict__ d_status,
                                                           int64_t *__restrict__ d_sort_count) {
+  pdl_enter();
   __shared__ unsigned long long part[1024];
   const int NR = G.n_rows;
   const int per = (NR + 1023) / 1024;
@@ -732,6 +745,7 @@ __global__ void __launch_bounds__(256) k_tile_ranges_rows(RowGeom G, const unsig
                                                           const int64_t *__restrict__ d_sort_count,
                                                           uint32_t *__restrict__ tstart,
                                                           int2 *__restrict__ ranges) {
+  pdl_enter();
   __shared__ uint32_t s_warp[8];
   const int g = blockIdx.x;
   const int v = view_of_row(G, g);
@@ -782,6 +796,7 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_emit(RowGeom G, const float
                                                           const int64_t *__restrict__ d_sort_count,
                                                           uint32_t *__restrict__ tile_keys,
                                                           uint32_t *__restrict__ ids) {
+  pdl_enter();
   constexpr int NW = kTileChunk / 32;
   extern __shared__ uint32_t s_base[];  // [tx_max]: first position of tile x for this chunk
   __shared__ uint32_t s_wc[NW][32];
@@ -854,6 +869,7 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_emit(RowGeom G, const float
 
 __global__ void k_view_keys(const uint32_t *__restrict__ recs, const int64_t *__restrict__ d_vis, int64_t stride,
                             uint32_t *__restrict__ keys) {
+  pdl_enter();
   const int64_t R = *d_vis;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < R; j += (int64_t)gridDim.x * blockDim.x)
     keys[j] = (uint32_t)(recs[j] / (uint64_t)stride);
@@ -987,10 +1003,10 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   const int64_t nb = (R + kScanBlock - 1) / kScanBlock;
   // ordered compaction of the visible records, then the depth sort over them
   // (4 passes, stable: equal depths keep record order = id order within a view)
-  k_vis_count<<<(unsigned)nb, kScanBlock, 0, st>>>(proj->radius, rect, n, proj->stride, R, w.bsum);
-  k_scan_blocks<<<1, 1024, 0, st>>>(w.bsum, (int)nb, w.vis_count);
-  k_vis_scatter<<<(unsigned)nb, kScanBlock, 0, st>>>(splat, proj->radius, rect, n, proj->stride, R, w.bsum, w.dk0,
-                                                     w.dv0);
+  pdl_launch(k_vis_count, (unsigned)nb, kScanBlock, 0, st, proj->radius, rect, n, proj->stride, R, w.bsum);
+  pdl_launch(k_scan_blocks, 1, 1024, 0, st, w.bsum, (int)nb, w.vis_count);
+  pdl_launch(k_vis_scatter, (unsigned)nb, kScanBlock, 0, st, splat, proj->radius, rect, n, proj->stride, R, w.bsum,
+             w.dk0, w.dv0);
   count_launch(3);
   fgs_status s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, w.vis_count, 0, R, 32, sort_blocks(R), w.counts,
                             w.digit_total, st);
@@ -998,7 +1014,7 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   const uint32_t *srec = w.dv0;
   if (n_views > 1) {
     // views made contiguous again (stable): rows of one view stay together
-    k_view_keys<<<4 * num_sms(), 256, 0, st>>>(w.dv0, w.vis_count, proj->stride, w.dk0);
+    pdl_launch(k_view_keys, 4 * num_sms(), 256, 0, st, w.dv0, w.vis_count, proj->stride, w.dk0);
     count_launch();
     s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, w.vis_count, 0, R, bits_for(n_views), sort_blocks(R), w.counts,
                    w.digit_total, st);
@@ -1007,11 +1023,12 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   }
   const int grid = kPartGrid * num_sms();
   const int NR = G.n_rows;
-  k_row_count<<<grid, kRecChunk, 0, st>>>(G, srec, rect, w.vis_count, w.nb_cap, w.rowcnt);
-  k_row_scan<<<NR, 1024, 0, st>>>(w.vis_count, w.nb_cap, w.rowcnt, w.rowtot);
-  k_row_starts<<<1, 1024, 0, st>>>(G, w.rowtot, w.row_cap, w.row_start, w.chunk_start, w.chunk_row, w.chunk_cap,
-                                   w.nchunks, d_status, d_num_pairs, w.sort_count);
-  k_row_emit<<<grid, kRecChunk, 0, st>>>(G, srec, rect, w.vis_count, w.nb_cap, w.rowcnt, w.row_start, w.rowlist);
+  pdl_launch(k_row_count, grid, kRecChunk, 0, st, G, srec, rect, w.vis_count, w.nb_cap, w.rowcnt);
+  pdl_launch(k_row_scan, NR, 1024, 0, st, w.vis_count, w.nb_cap, w.rowcnt, w.rowtot);
+  pdl_launch(k_row_starts, 1, 1024, 0, st, G, w.rowtot, w.row_cap, w.row_start, w.chunk_start, w.chunk_row,
+             w.chunk_cap, w.nchunks, d_status, d_num_pairs, w.sort_count);
+  pdl_launch(k_row_emit, grid, kRecChunk, 0, st, G, srec, rect, w.vis_count, w.nb_cap, w.rowcnt, w.row_start,
+             w.rowlist);
   count_launch(4);
   FGS_CHECK_LAUNCH("fgs_bin_sort rows");
   const int tw = tiling.tile_w, th = tiling.tile_h;
@@ -1022,15 +1039,14 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
     FGS_CUDA(cudaFuncSetAttribute(k_tile_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tx_smem),
              "k_tile_emit smem");
   }
-  k_tile_count<<<grid, kTileChunk, tx_smem, st>>>(G, splat, srec, rect, tw, th, w.rowlist, w.row_start,
-                                                  w.chunk_start, w.chunk_row, w.nchunks, w.tcnt, w.einfo);
-  k_tile_chunk_scan<<<NR, 256, 0, st>>>(G, w.chunk_start, w.tcnt, w.tpre, w.ttot, w.rowp);
-  k_tile_row_starts<<<1, 1024, 0, st>>>(G, w.rowp, pair_capacity, d_num_pairs, d_status, w.sort_count);
-  k_tile_ranges_rows<<<NR, 256, 0, st>>>(G, w.rowp, w.ttot, w.sort_count, w.tstart,
-                                         reinterpret_cast<int2 *>(tile_ranges));
-  k_tile_emit<<<grid, kTileChunk, tx_smem, st>>>(G, splat, tw, th, w.row_start, w.chunk_start, w.chunk_row,
-                                                 w.nchunks, w.einfo, w.tpre, w.tstart, w.sort_count, tile_keys,
-                                                 reinterpret_cast<uint32_t *>(ids));
+  pdl_launch(k_tile_count, grid, kTileChunk, tx_smem, st, G, splat, srec, rect, tw, th, w.rowlist, w.row_start,
+             w.chunk_start, w.chunk_row, w.nchunks, w.tcnt, w.einfo);
+  pdl_launch(k_tile_chunk_scan, NR, 256, 0, st, G, w.chunk_start, w.tcnt, w.tpre, w.ttot, w.rowp);
+  pdl_launch(k_tile_row_starts, 1, 1024, 0, st, G, w.rowp, pair_capacity, d_num_pairs, d_status, w.sort_count);
+  pdl_launch(k_tile_ranges_rows, NR, 256, 0, st, G, w.rowp, w.ttot, w.sort_count, w.tstart,
+             reinterpret_cast<int2 *>(tile_ranges));
+  pdl_launch(k_tile_emit, grid, kTileChunk, tx_smem, st, G, splat, tw, th, w.row_start, w.chunk_start, w.chunk_row,
+             w.nchunks, w.einfo, w.tpre, w.tstart, w.sort_count, tile_keys, reinterpret_cast<uint32_t *>(ids));
   count_launch(5);
   FGS_CHECK_LAUNCH("fgs_bin_sort tiles");
   return FGS_OK;

@@ -6,11 +6,53 @@
 
 #include <atomic>
 #include <cstdio>
+#include <cstdlib>
 #include <string>
+#include <utility>
 
 #include "../../include/fgs.h"
 
 namespace fgs {
+
+// ---------------------------------------------------------------------------------
+// Programmatic dependent launch (griddepcontrol).  The library's kernels follow
+// one another on one stream, many of them short (binning, scans, reductions), so
+// the gap between two dependent launches is a visible share of a step.  A kernel
+// launched by pdl_launch may be scheduled while the kernel before it drains; its
+// first statement is pdl_enter(), which waits until that kernel has completed and
+// its writes are visible (griddepcontrol.wait), then lets the next kernel be
+// scheduled in turn (griddepcontrol.launch_dependents).  Nothing before
+// pdl_enter() touches memory, so the order of every read and write is the plain
+// stream order.  FGS_PDL=0 in the environment launches without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char *e = std::getenv("FGS_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+// kernel<<<grid, block, smem, st>>>(args...) with programmatic stream
+// serialisation; launch errors surface through cudaGetLastError as for <<<>>>.
+template <typename... P, typename... A>
+inline void pdl_launch(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 // ---------------------------------------------------------------------------------
 // Rasteriser constants.  The paper states only the blend (eq1); these are the

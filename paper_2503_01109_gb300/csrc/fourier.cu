@@ -163,6 +163,7 @@ __device__ __forceinline__ void block_max_to(float v, uint32_t *dst) {
 // eq2 along x for every row of the gray frame; running max of |gray|.
 __global__ void __launch_bounds__(kFftThreads) k_fft_rows(const float *__restrict__ rgb, int W, int H, FftPlan plan,
                                                           float2 *__restrict__ spec, uint32_t *__restrict__ gray_max) {
+  pdl_enter();
   extern __shared__ float2 sm2[];
   float2 *a = sm2, *b = sm2 + W;
   const int y = blockIdx.x;
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows(const float *__restric
 // frequency (eq3 read as the spectrum shift), inverse DFT.
 __global__ void __launch_bounds__(kFftThreads) k_fft_cols(float2 *__restrict__ spec, int W, int H, FftPlan plan,
                                                           float d0) {
+  pdl_enter();
   extern __shared__ float2 sm2[];
   float2 *a = sm2, *b = sm2 + H * kColGroup;
   const int x0 = blockIdx.x * kColGroup;
@@ -221,6 +223,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(float2 *__restrict__ s
 __global__ void __launch_bounds__(kFftThreads) k_ifft_rows(const float2 *__restrict__ spec, int W, int H,
                                                            FftPlan plan, float *__restrict__ energy,
                                                            uint32_t *__restrict__ max_bits) {
+  pdl_enter();
   extern __shared__ float2 sm2[];
   float2 *a = sm2, *b = sm2 + W;
   const int y = blockIdx.x;
@@ -251,6 +254,7 @@ __device__ __forceinline__ int energy_bin(float e, float maxE, float floorE) {
 
 __global__ void k_hist(const float *__restrict__ energy, int64_t HW, const uint32_t *__restrict__ max_bits,
                        uint32_t *__restrict__ hist) {
+  pdl_enter();
   __shared__ uint32_t h[256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
   __syncthreads();
@@ -264,6 +268,7 @@ __global__ void k_hist(const float *__restrict__ energy, int64_t HW, const uint3
 
 // Triangle method between the peak and the far non-empty end; exact integers.
 __global__ void k_triangle(const uint32_t *__restrict__ hist, int32_t *__restrict__ d_threshold) {
+  pdl_enter();
   __shared__ int64_t hv[256];
   __shared__ int s_p, s_lo, s_hi;
   const int i = threadIdx.x;
@@ -351,6 +356,7 @@ __device__ __forceinline__ uint32_t pixel_flags(const SeedArgs &a, int64_t p, in
 }
 
 __global__ void __launch_bounds__(kSeedBlock) k_seed_count(SeedArgs a) {
+  pdl_enter();
   __shared__ uint32_t red_h[kSeedBlock / 32], red_l[kSeedBlock / 32];
   const int64_t HW = (int64_t)a.W * a.H;
   const int64_t p = blockIdx.x * (int64_t)kSeedBlock + threadIdx.x;
@@ -379,6 +385,7 @@ __global__ void __launch_bounds__(kSeedBlock) k_seed_count(SeedArgs a) {
 // Exclusive scans of the CTA counts, the capped seed count, the append base.
 __global__ void __launch_bounds__(1024) k_seed_scan(SeedArgs a, int nb, int64_t *d_n, int64_t host_n, int64_t cap,
                                                     int32_t *d_num_new, int32_t *d_status) {
+  pdl_enter();
   __shared__ uint32_t part_h[1024], part_l[1024];
   const int per = (nb + 1023) / 1024;
   const int lo = threadIdx.x * per, hi = min(nb, lo + per);
@@ -425,6 +432,7 @@ __global__ void __launch_bounds__(1024) k_seed_scan(SeedArgs a, int nb, int64_t 
 }
 
 __global__ void __launch_bounds__(kSeedBlock) k_seed_write(SeedArgs a, GaussGrads g) {
+  pdl_enter();
   __shared__ uint32_t wh[kSeedBlock / 32], wl[kSeedBlock / 32];
   const int64_t HW = (int64_t)a.W * a.H;
   const int64_t p = blockIdx.x * (int64_t)kSeedBlock + threadIdx.x;
@@ -579,11 +587,11 @@ extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_g
   }
   if (smem_col > 48 * 1024)
     FGS_CUDA(cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col), "attr");
-  k_fft_rows<<<H, kFftThreads, smem_row, st>>>(rgb_gt, W, H, px, w.spec, w.max_bits + 1);
-  k_fft_cols<<<(W + kColGroup - 1) / kColGroup, kFftThreads, smem_col, st>>>(w.spec, W, H, py, prm->d0);
-  k_ifft_rows<<<H, kFftThreads, smem_row, st>>>(w.spec, W, H, px, E, w.max_bits);
-  k_hist<<<4 * num_sms(), 256, 0, st>>>(E, HW, w.max_bits, w.hist);
-  k_triangle<<<1, 256, 0, st>>>(w.hist, d_threshold);
+  pdl_launch(k_fft_rows, H, kFftThreads, smem_row, st, rgb_gt, W, H, px, w.spec, w.max_bits + 1);
+  pdl_launch(k_fft_cols, (W + kColGroup - 1) / kColGroup, kFftThreads, smem_col, st, w.spec, W, H, py, prm->d0);
+  pdl_launch(k_ifft_rows, H, kFftThreads, smem_row, st, w.spec, W, H, px, E, w.max_bits);
+  pdl_launch(k_hist, 4 * num_sms(), 256, 0, st, E, HW, w.max_bits, w.hist);
+  pdl_launch(k_triangle, 1, 256, 0, st, w.hist, d_threshold);
   count_launch(5);
   FGS_CHECK_LAUNCH("fgs_fourier_seed fft");
   SeedArgs a;
@@ -621,9 +629,9 @@ extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_g
   a.seed_xy = seed_xy ? seed_xy : w.seed_xy;
   a.seed_hi = w.seed_hi;
   const int nb = (int)((HW + kSeedBlock - 1) / kSeedBlock);
-  k_seed_count<<<nb, kSeedBlock, 0, st>>>(a);
-  k_seed_scan<<<1, 1024, 0, st>>>(a, nb, g->d_n, g->n, g->capacity, d_num_new, d_status);
-  k_seed_write<<<nb, kSeedBlock, 0, st>>>(a, gauss_grads(g));
+  pdl_launch(k_seed_count, nb, kSeedBlock, 0, st, a);
+  pdl_launch(k_seed_scan, 1, 1024, 0, st, a, nb, g->d_n, g->n, g->capacity, d_num_new, d_status);
+  pdl_launch(k_seed_write, nb, kSeedBlock, 0, st, a, gauss_grads(g));
   count_launch(3);
   FGS_CHECK_LAUNCH("fgs_fourier_seed seeds");
   if (prior) {

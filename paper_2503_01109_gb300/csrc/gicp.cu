@@ -79,6 +79,7 @@ constexpr int kScanChunk = 4096;  // entries per block of the scan (1024 threads
 
 __global__ void __launch_bounds__(1024) k_scan_sums(const uint32_t *__restrict__ a, int64_t n,
                                                     unsigned long long *__restrict__ sums) {
+  pdl_enter();
   __shared__ unsigned long long red[32];
   const int64_t base = blockIdx.x * (int64_t)kScanChunk;
   unsigned long long s = 0;
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(1024) k_scan_sums(const uint32_t *__restrict__
 // one CTA: exclusive scan of nb block sums in place, total to *total
 __global__ void __launch_bounds__(1024) k_scan_top(unsigned long long *__restrict__ sums, int nb,
                                                    unsigned long long *__restrict__ total) {
+  pdl_enter();
   __shared__ unsigned long long part[1024];
   const int per = (nb + 1023) / 1024;
   const int lo = threadIdx.x * per, hi = min(nb, lo + per);
@@ -125,6 +127,7 @@ __global__ void __launch_bounds__(1024) k_scan_apply(const uint32_t *__restrict_
                                                      const unsigned long long *__restrict__ sums,
                                                      const unsigned long long *__restrict__ total,
                                                      int32_t *__restrict__ out) {
+  pdl_enter();
   __shared__ uint32_t s_val[kScanChunk];
   __shared__ uint32_t s_warp[32];
   const int64_t base = blockIdx.x * (int64_t)kScanChunk;
@@ -169,9 +172,9 @@ __global__ void __launch_bounds__(1024) k_scan_apply(const uint32_t *__restrict_
 static fgs_status exclusive_scan(const uint32_t *a, int64_t n, unsigned long long *sums, unsigned long long *total,
                                  int32_t *out, cudaStream_t st) {
   const int64_t nb = std::max<int64_t>(1, (n + kScanChunk - 1) / kScanChunk);
-  k_scan_sums<<<(unsigned)nb, 1024, 0, st>>>(a, n, sums);
-  k_scan_top<<<1, 1024, 0, st>>>(sums, (int)nb, total);
-  k_scan_apply<<<(unsigned)nb, 1024, 0, st>>>(a, n, sums, total, out);
+  pdl_launch(k_scan_sums, (unsigned)nb, 1024, 0, st, a, n, sums);
+  pdl_launch(k_scan_top, 1, 1024, 0, st, sums, (int)nb, total);
+  pdl_launch(k_scan_apply, (unsigned)nb, 1024, 0, st, a, n, sums, total, out);
   count_launch(3);
   FGS_CHECK_LAUNCH("exclusive_scan");
   return FGS_OK;
@@ -228,6 +231,7 @@ __device__ __forceinline__ bool sample_point(const DepthSample &D, int64_t s, fl
 }
 
 __global__ void __launch_bounds__(kGBlock) k_dp_count(DepthSample D, int64_t S, uint32_t *__restrict__ bsum) {
+  pdl_enter();
   __shared__ uint32_t red[kGBlock / 32];
   const int64_t s = blockIdx.x * (int64_t)kGBlock + threadIdx.x;
   float x, y, z;
@@ -245,6 +249,7 @@ __global__ void __launch_bounds__(kGBlock) k_dp_count(DepthSample D, int64_t S, 
 __global__ void __launch_bounds__(kGBlock) k_dp_scatter(DepthSample D, int64_t S, const int32_t *__restrict__ off,
                                                         int64_t nb, float *__restrict__ xyz, int64_t cap,
                                                         int64_t *__restrict__ d_n, int32_t *__restrict__ d_status) {
+  pdl_enter();
   __shared__ uint32_t wsum[kGBlock / 32];
   const int64_t s = blockIdx.x * (int64_t)kGBlock + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -326,6 +331,7 @@ __device__ __forceinline__ void rotate_cov(const float *R, const float *c, float
 // one thread per point: reads its own slots before writing them, so in place is safe
 __global__ void k_transform(const float *xyz_in, const float *cov_in, const int64_t *__restrict__ d_n, int64_t n_max,
                             const double *__restrict__ pose, float *xyz_out, float *cov_out) {
+  pdl_enter();
   const int64_t n = min(*d_n, n_max);
   const PoseF T = pose_f(pose);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -350,6 +356,7 @@ __global__ void k_transform(const float *xyz_in, const float *cov_in, const int6
 
 __global__ void k_grid_count(const float *__restrict__ xyz, const int64_t *__restrict__ d_n, int64_t n_max, GridDev G,
                              uint32_t *__restrict__ count, int32_t *__restrict__ cell_of_pt) {
+  pdl_enter();
   const int64_t n = min(*d_n, n_max);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int cx, cy, cz;
@@ -365,6 +372,7 @@ __global__ void k_grid_count(const float *__restrict__ xyz, const int64_t *__res
 __global__ void k_grid_fill(const int64_t *__restrict__ d_n, int64_t n_max, const int32_t *__restrict__ cell_of_pt,
                             const int32_t *__restrict__ cell_start, uint32_t *__restrict__ fill,
                             int32_t *__restrict__ order) {
+  pdl_enter();
   const int64_t n = min(*d_n, n_max);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int c = cell_of_pt[i];
@@ -374,6 +382,7 @@ __global__ void k_grid_fill(const int64_t *__restrict__ d_n, int64_t n_max, cons
 
 __global__ void k_voxel_first(const float *__restrict__ xyz, const int64_t *__restrict__ d_n, int64_t n_max,
                               GridDev G, uint32_t *__restrict__ first, int32_t *__restrict__ cell_of_pt) {
+  pdl_enter();
   const int64_t n = min(*d_n, n_max);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int cx, cy, cz;
@@ -396,6 +405,7 @@ __global__ void __launch_bounds__(kGBlock) k_voxel_count(const int64_t *__restri
                                                          const int32_t *__restrict__ cell_of_pt,
                                                          const uint32_t *__restrict__ first,
                                                          uint32_t *__restrict__ bsum) {
+  pdl_enter();
   __shared__ uint32_t red[kGBlock / 32];
   const int64_t n = min(*d_n, n_max);
   const int64_t i = blockIdx.x * (int64_t)kGBlock + threadIdx.x;
@@ -415,6 +425,7 @@ __global__ void __launch_bounds__(kGBlock) k_voxel_scatter(const float *__restri
                                                            const uint32_t *__restrict__ first,
                                                            const int32_t *__restrict__ off, float *__restrict__ out,
                                                            int64_t cap, const int64_t *__restrict__ d_n_out) {
+  pdl_enter();
   __shared__ uint32_t wsum[kGBlock / 32];
   __shared__ int64_t s_base;
   const int64_t n = min(*d_n, n_max);
@@ -445,6 +456,7 @@ __global__ void __launch_bounds__(kGBlock) k_voxel_scatter(const float *__restri
 
 __global__ void k_voxel_finish(const int32_t *__restrict__ off, int64_t nb, int64_t cap, int64_t *__restrict__ d_n_out,
                                int32_t *__restrict__ d_status) {
+  pdl_enter();
   const int64_t total = *d_n_out + off[nb];
   *d_n_out = total < cap ? total : cap;
   if (total > cap && d_status) atomicOr(d_status, FGS_DEV_MAP_FULL);
@@ -495,6 +507,7 @@ __global__ void __launch_bounds__(128) k_covariances(const float *__restrict__ x
                                                      int64_t n_max, GridDev G, const int32_t *__restrict__ cell_start,
                                                      const int32_t *__restrict__ order, int k, float eps,
                                                      float *__restrict__ cov) {
+  pdl_enter();
   const int64_t n = min(*d_n, n_max);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -600,6 +613,7 @@ __global__ void __launch_bounds__(kGBlock) k_gicp_step(const float *__restrict__
                                                        const double *__restrict__ pose, float max_dist,
                                                        float overlap_dist, const GicpCtl *__restrict__ ctl,
                                                        double *__restrict__ partials) {
+  pdl_enter();
   __shared__ float s_red[kGBlock / 32][kSums];
   if (ctl->done) return;
   const int64_t n = min(*d_n_src, n_max);
@@ -713,6 +727,7 @@ __global__ void __launch_bounds__(64) k_gicp_solve(const double *__restrict__ pa
                                                    const int64_t *__restrict__ d_n_src, int64_t n_max,
                                                    double *__restrict__ pose, GicpCtl *__restrict__ ctl,
                                                    double *__restrict__ stats) {
+  pdl_enter();
   __shared__ double s[kSums];
   if (ctl->done) return;
   if (threadIdx.x < kSums) {
@@ -773,6 +788,7 @@ __global__ void __launch_bounds__(64) k_gicp_solve(const double *__restrict__ pa
 }
 
 __global__ void k_gicp_init(GicpCtl *ctl, double *stats) {
+  pdl_enter();
   ctl->done = 0;
   ctl->iterations = 0;
   for (int k = 0; k < 4; ++k) stats[k] = 0.0;
@@ -875,11 +891,11 @@ extern "C" fgs_status fgs_depth_points(const float *depth, const uint8_t *mask, 
                 w.bytes);
   FGS_CHECK_ARG((reinterpret_cast<uintptr_t>(ws) & 255) == 0, "fgs_depth_points: workspace not 256-byte aligned");
   cudaStream_t st = as_stream(stream);
-  k_dp_count<<<(unsigned)nb, kGBlock, 0, st>>>(D, S, w.cnt);
+  pdl_launch(k_dp_count, (unsigned)nb, kGBlock, 0, st, D, S, w.cnt);
   count_launch();
   fgs_status s = exclusive_scan(w.cnt, nb, w.sums, w.total, w.off, st);
   if (s != FGS_OK) return s;
-  k_dp_scatter<<<(unsigned)nb, kGBlock, 0, st>>>(D, S, w.off, nb, xyz, capacity, d_n, d_status);
+  pdl_launch(k_dp_scatter, (unsigned)nb, kGBlock, 0, st, D, S, w.off, nb, xyz, capacity, d_n, d_status);
   count_launch();
   FGS_CHECK_LAUNCH("fgs_depth_points");
   return FGS_OK;
@@ -892,7 +908,7 @@ extern "C" fgs_status fgs_transform_points(const float *xyz_in, const float *cov
   FGS_CHECK_ARG((cov_in == nullptr) == (cov_out == nullptr), "fgs_transform_points: both covariances or neither");
   if (n_max <= 0) return FGS_OK;
   const unsigned blocks = (unsigned)std::min<int64_t>((n_max + 255) / 256, 8 * num_sms());
-  k_transform<<<blocks, 256, 0, as_stream(stream)>>>(xyz_in, cov_in, d_n, n_max, d_pose, xyz_out, cov_out);
+  pdl_launch(k_transform, blocks, 256, 0, as_stream(stream), xyz_in, cov_in, d_n, n_max, d_pose, xyz_out, cov_out);
   count_launch();
   FGS_CHECK_LAUNCH("fgs_transform_points");
   return FGS_OK;
@@ -920,14 +936,14 @@ extern "C" fgs_status fgs_voxel_downsample(const float *xyz, const int64_t *d_n,
   FGS_CUDA(cudaMemsetAsync(w.first, 0xFF, (size_t)grid_cells(*grid) * 4, st), "voxel first");
   const int64_t nb = (n_max + kGBlock - 1) / kGBlock;
   const unsigned gblocks = (unsigned)std::min<int64_t>(nb, 8 * num_sms());
-  k_voxel_first<<<gblocks, kGBlock, 0, st>>>(xyz, d_n, n_max, G, w.first, w.cell_of_pt);
-  k_voxel_count<<<(unsigned)nb, kGBlock, 0, st>>>(d_n, n_max, w.cell_of_pt, w.first, w.c.cnt);
+  pdl_launch(k_voxel_first, gblocks, kGBlock, 0, st, xyz, d_n, n_max, G, w.first, w.cell_of_pt);
+  pdl_launch(k_voxel_count, (unsigned)nb, kGBlock, 0, st, d_n, n_max, w.cell_of_pt, w.first, w.c.cnt);
   count_launch(2);
   fgs_status s = exclusive_scan(w.c.cnt, nb, w.c.sums, w.c.total, w.c.off, st);
   if (s != FGS_OK) return s;
-  k_voxel_scatter<<<(unsigned)nb, kGBlock, 0, st>>>(xyz, d_n, n_max, w.cell_of_pt, w.first, w.c.off, out_xyz,
-                                                    out_capacity, d_n_out);
-  k_voxel_finish<<<1, 1, 0, st>>>(w.c.off, nb, out_capacity, d_n_out, d_status);
+  pdl_launch(k_voxel_scatter, (unsigned)nb, kGBlock, 0, st, xyz, d_n, n_max, w.cell_of_pt, w.first, w.c.off, out_xyz,
+             out_capacity, d_n_out);
+  pdl_launch(k_voxel_finish, 1, 1, 0, st, w.c.off, nb, out_capacity, d_n_out, d_status);
   count_launch(2);
   FGS_CHECK_LAUNCH("fgs_voxel_downsample");
   return FGS_OK;
@@ -953,11 +969,11 @@ extern "C" fgs_status fgs_grid_build(const float *xyz, const int64_t *d_n, int64
   FGS_CUDA(cudaMemsetAsync(w.count, 0, (size_t)cells * 4, st), "grid count");
   FGS_CUDA(cudaMemsetAsync(w.fill, 0, (size_t)cells * 4, st), "grid fill");
   const unsigned gblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_max + 255) / 256, 8 * num_sms()));
-  k_grid_count<<<gblocks, 256, 0, st>>>(xyz, d_n, n_max, G, w.count, w.cell_of_pt);
+  pdl_launch(k_grid_count, gblocks, 256, 0, st, xyz, d_n, n_max, G, w.count, w.cell_of_pt);
   count_launch();
   fgs_status s = exclusive_scan(w.count, cells, w.sums, w.total, cell_start, st);
   if (s != FGS_OK) return s;
-  k_grid_fill<<<gblocks, 256, 0, st>>>(d_n, n_max, w.cell_of_pt, cell_start, w.fill, order);
+  pdl_launch(k_grid_fill, gblocks, 256, 0, st, d_n, n_max, w.cell_of_pt, cell_start, w.fill, order);
   count_launch();
   FGS_CHECK_LAUNCH("fgs_grid_build");
   return FGS_OK;
@@ -970,8 +986,8 @@ extern "C" fgs_status fgs_point_covariances(const float *xyz, const int64_t *d_n
   FGS_CHECK_ARG(grid_ok(grid), "fgs_point_covariances: bad grid");
   FGS_CHECK_ARG(k >= 3 && k <= kMaxK, "fgs_point_covariances: k must be 3..%d", kMaxK);
   if (n_max <= 0) return FGS_OK;
-  k_covariances<<<(unsigned)((n_max + 127) / 128), 128, 0, as_stream(stream)>>>(xyz, d_n, n_max, grid_dev(*grid),
-                                                                                 cell_start, order, k, eps, cov);
+  pdl_launch(k_covariances, (unsigned)((n_max + 127) / 128), 128, 0, as_stream(stream), xyz, d_n, n_max,
+             grid_dev(*grid), cell_start, order, k, eps, cov);
   count_launch();
   FGS_CHECK_LAUNCH("fgs_point_covariances");
   return FGS_OK;
@@ -1002,12 +1018,12 @@ extern "C" fgs_status fgs_gicp(const float *src_xyz, const float *src_cov, const
   cudaStream_t st = as_stream(stream);
   const int nb = (int)((n_src_max + kGBlock - 1) / kGBlock);
   const GridDev G = grid_dev(*grid);
-  k_gicp_init<<<1, 1, 0, st>>>(ctl, d_stats);
+  pdl_launch(k_gicp_init, 1, 1, 0, st, ctl, d_stats);
   count_launch();
   for (int it = 0; it < p->iterations; ++it) {
-    k_gicp_step<<<nb, kGBlock, 0, st>>>(src_xyz, src_cov, d_n_src, n_src_max, tgt_xyz, tgt_cov, G, cell_start,
-                                        order, d_pose, p->max_dist, p->overlap_dist, ctl, partials);
-    k_gicp_solve<<<1, 64, 0, st>>>(partials, nb, d_n_src, n_src_max, d_pose, ctl, d_stats);
+    pdl_launch(k_gicp_step, nb, kGBlock, 0, st, src_xyz, src_cov, d_n_src, n_src_max, tgt_xyz, tgt_cov, G, cell_start,
+               order, d_pose, p->max_dist, p->overlap_dist, ctl, partials);
+    pdl_launch(k_gicp_solve, 1, 64, 0, st, partials, nb, d_n_src, n_src_max, d_pose, ctl, d_stats);
     count_launch(2);
   }
   FGS_CHECK_LAUNCH("fgs_gicp");

@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(256) k_covisibility(const float *__restrict__ 
                                                       KfCam cur, KfArgs kf,
                                                       unsigned long long *__restrict__ d_inside,
                                                       unsigned long long *__restrict__ d_valid) {
+  pdl_enter();
   const int sx = (W + step - 1) / step, sy = (H + step - 1) / step;
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(256) k_covisibility(const float *__restrict__ 
 }
 
 __global__ void k_covis_zero(unsigned long long *inside, int n, unsigned long long *valid) {
+  pdl_enter();
   for (int k = threadIdx.x; k < n; k += blockDim.x) inside[k] = 0ull;
   if (threadIdx.x == 0) *valid = 0ull;
 }
@@ -95,6 +97,7 @@ __global__ void __launch_bounds__(kMaxSelect) k_select_keyframes(const int64_t *
                                                                  float threshold, float frac,
                                                                  int32_t *__restrict__ d_kind,
                                                                  int32_t *__restrict__ d_count) {
+  pdl_enter();
   __shared__ int s_rest[kMaxSelect];  // 1 where keyframe k is not co-visible
   __shared__ float s_u[kMaxSelect];
   __shared__ int s_nrest, s_count;
@@ -170,10 +173,10 @@ extern "C" fgs_status fgs_covisibility(const float *depth, const fgs_camera *cam
   cudaStream_t st = as_stream(stream);
   auto *inside = reinterpret_cast<unsigned long long *>(d_inside);
   auto *valid = reinterpret_cast<unsigned long long *>(d_valid);
-  k_covis_zero<<<1, 256, 0, st>>>(inside, n_keyframes, valid);
+  pdl_launch(k_covis_zero, 1, 256, 0, st, inside, n_keyframes, valid);
   const int64_t samples = (int64_t)((cam->width + step - 1) / step) * ((cam->height + step - 1) / step);
   const unsigned blocks = (unsigned)((samples + 255) / 256);
-  k_covisibility<<<blocks, 256, 0, st>>>(depth, cam->width, cam->height, step, cur, kf, inside, valid);
+  pdl_launch(k_covisibility, blocks, 256, 0, st, depth, cam->width, cam->height, step, cur, kf, inside, valid);
   count_launch(2);
   FGS_CHECK_LAUNCH("fgs_covisibility");
   return FGS_OK;
@@ -185,8 +188,8 @@ extern "C" fgs_status fgs_select_keyframes(const int64_t *d_inside, const int64_
   FGS_CHECK_ARG(d_inside && d_valid && u && d_kind && d_count, "fgs_select_keyframes: NULL argument");
   FGS_CHECK_ARG(n_keyframes >= 1 && n_keyframes <= kMaxSelect, "fgs_select_keyframes: 1..%d keyframes",
                 kMaxSelect);
-  k_select_keyframes<<<1, kMaxSelect, 0, as_stream(stream)>>>(d_inside, d_valid, u, n_keyframes, threshold, frac,
-                                                              d_kind, d_count);
+  pdl_launch(k_select_keyframes, 1, kMaxSelect, 0, as_stream(stream), d_inside, d_valid, u, n_keyframes, threshold,
+             frac, d_kind, d_count);
   count_launch();
   FGS_CHECK_LAUNCH("fgs_select_keyframes");
   return FGS_OK;

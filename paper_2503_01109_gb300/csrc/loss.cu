@@ -12,12 +12,14 @@
 namespace fgs {
 
 __global__ void __launch_bounds__(kLThreads) k_loss(LossArgs a) {
+  pdl_enter();
   extern __shared__ float sm[];
   loss_tile(a, blockIdx.x, sm);
 }
 
 // Sums `count` partials in a fixed order and adds the total to *d_loss.
 __global__ void k_reduce_partials(const double *__restrict__ partials, int64_t count, float *d_loss) {
+  pdl_enter();
   __shared__ double red[256];
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < count; i += 256) s += partials[i];
@@ -60,6 +62,7 @@ static bool loss_views(const fgs_camera *cams, int32_t n_views, LossViews *lv, i
 // mean over the live Gaussians, times weight.
 __global__ void k_scale_reg(const float *__restrict__ ls, int64_t cap, int64_t n, const int64_t *d_n,
                             float weight, float *__restrict__ gls, double *__restrict__ partials) {
+  pdl_enter();
   __shared__ double red[8];
   const int64_t live = live_count(d_n, n);
   const float wn = live > 0 ? weight / (float)live : 0.f;
@@ -115,7 +118,7 @@ __device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, 
   p -= __fdividef(lr * (m * r.x), den);
 }
 
-__global__ void k_adam_step_incr(int32_t *d_step) { *d_step += 1; }
+__global__ void k_adam_step_incr(int32_t *d_step) { pdl_enter(); *d_step += 1; }
 
 // VEC: four consecutive elements per thread with 16-byte loads (every plane
 // 16-byte aligned); else one element per thread.
@@ -123,6 +126,7 @@ __global__ void k_adam_step_incr(int32_t *d_step) { *d_step += 1; }
 template <bool VEC>
 __global__ void k_adam(AdamPlanes P, int64_t n, const int64_t *d_n, float b1, float b2, float eps, int32_t step,
                        const int32_t *d_step, int zero_from) {
+  pdl_enter();
   const int plane = blockIdx.y;
   const int64_t live = live_count(d_n, n);
   const int t = d_step ? *d_step : step;
@@ -200,8 +204,8 @@ extern "C" fgs_status fgs_loss(const fgs_camera *cams, int32_t n_views, const fl
   static_assert(sizeof(float) * (2 * kLIn * kLIn + 5 * kLIn * kLMid + 5 * kLMid * kLMid) <= 48 * 1024,
                 "loss tile must fit the default dynamic shared-memory limit");
   cudaStream_t st = as_stream(stream);
-  k_loss<<<blocks, kLThreads, smem, st>>>(a);
-  k_reduce_partials<<<1, 256, 0, st>>>(a.partials, blocks, d_loss);
+  pdl_launch(k_loss, blocks, kLThreads, smem, st, a);
+  pdl_launch(k_reduce_partials, 1, 256, 0, st, a.partials, blocks, d_loss);
   count_launch(2);
   FGS_CHECK_LAUNCH("fgs_loss");
   return FGS_OK;
@@ -218,9 +222,9 @@ extern "C" fgs_status fgs_scale_reg(const fgs_gaussians *g, float weight, fgs_ga
   if (g->n == 0) return FGS_OK;
   const int64_t blocks = (g->n + 255) / 256;
   cudaStream_t st = as_stream(stream);
-  k_scale_reg<<<(unsigned)blocks, 256, 0, st>>>(g->log_scales, g->capacity, g->n, g->d_n, weight, grads->log_scales,
-                                                static_cast<double *>(ws));
-  k_reduce_partials<<<1, 256, 0, st>>>(static_cast<double *>(ws), blocks, d_loss);
+  pdl_launch(k_scale_reg, (unsigned)blocks, 256, 0, st, g->log_scales, g->capacity, g->n, g->d_n, weight,
+             grads->log_scales, static_cast<double *>(ws));
+  pdl_launch(k_reduce_partials, 1, 256, 0, st, static_cast<double *>(ws), blocks, d_loss);
   count_launch(2);
   FGS_CHECK_LAUNCH("fgs_scale_reg");
   return FGS_OK;
@@ -249,7 +253,7 @@ fgs_status launch_adam(fgs_gaussians *params, fgs_gaussians *grads, fgs_gaussian
        hp->lr[3]);
   fill(11, 3, params->rgb, grads->rgb, m->rgb, v->rgb, pc, gc, mc, vc, hp->lr[4]);
   if (d_step) {
-    k_adam_step_incr<<<1, 1, 0, st>>>(d_step);
+    pdl_launch(k_adam_step_incr, 1, 1, 0, st, d_step);
     count_launch();
   }
   bool aligned = true;
@@ -259,11 +263,11 @@ fgs_status launch_adam(fgs_gaussians *params, fgs_gaussians *grads, fgs_gaussian
   const int64_t per_block = aligned ? 1024 : 256;
   const unsigned bx = (unsigned)std::max<int64_t>(1, (params->n + per_block - 1) / per_block);
   if (aligned)
-    k_adam<true><<<dim3(bx, 14), 256, 0, st>>>(P, params->n, params->d_n, hp->beta1, hp->beta2, hp->eps, hp->step,
-                                               d_step, zero_from);
+    pdl_launch(k_adam<true>, dim3(bx, 14), 256, 0, st, P, params->n, params->d_n, hp->beta1, hp->beta2, hp->eps,
+               hp->step, d_step, zero_from);
   else
-    k_adam<false><<<dim3(bx, 14), 256, 0, st>>>(P, params->n, params->d_n, hp->beta1, hp->beta2, hp->eps, hp->step,
-                                                d_step, zero_from);
+    pdl_launch(k_adam<false>, dim3(bx, 14), 256, 0, st, P, params->n, params->d_n, hp->beta1, hp->beta2, hp->eps,
+               hp->step, d_step, zero_from);
   count_launch();
   FGS_CHECK_LAUNCH("fgs_adam");
   return FGS_OK;
@@ -353,8 +357,8 @@ extern "C" fgs_status fgs_loss_noalloc(const fgs_camera *cams, int32_t n_views, 
   for (int i = 0; i < 11; ++i) a.g[i] = (float)(g[i] / gs);
   const size_t smem = sizeof(float) * (2 * kLIn * kLIn + 5 * kLIn * kLMid + 5 * kLMid * kLMid);
   cudaStream_t st = as_stream(stream);
-  k_loss<<<blocks, kLThreads, smem, st>>>(a);
-  k_reduce_partials<<<1, 256, 0, st>>>(scratch, blocks, d_loss);
+  pdl_launch(k_loss, blocks, kLThreads, smem, st, a);
+  pdl_launch(k_reduce_partials, 1, 256, 0, st, scratch, blocks, d_loss);
   count_launch(2);
   FGS_CHECK_LAUNCH("fgs_loss_noalloc");
   return FGS_OK;

@@ -89,6 +89,7 @@ __device__ __forceinline__ bool project_view(const GaussLocal &L, const DevCam &
 __global__ void k_project(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_n, DevViews vs,
                           int tw, int th, float4 *__restrict__ splat, int32_t *__restrict__ radius,
                           uint2 *__restrict__ rect, int64_t stride) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const bool alive = i < live_count(d_n, n);
@@ -264,9 +265,11 @@ __device__ __forceinline__ uint32_t chain_rule(const GaussLocal &L, int64_t i, c
   return read;
 }
 
-__global__ void __launch_bounds__(256, 3) k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_n, DevViews vs,
-                              const int32_t *__restrict__ radius, const float4 *__restrict__ grad2d,
-                              int64_t stride, GaussGrads out) {
+__global__ void __launch_bounds__(256, 3)
+    k_project_bwd(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_n, DevViews vs,
+                  const int32_t *__restrict__ radius, const float4 *__restrict__ grad2d, int64_t stride,
+                  GaussGrads out) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n || i >= live_count(d_n, n)) return;
   GaussLocal L;
@@ -308,6 +311,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 3)
     k_project_bwd_reg(GaussPtrs gp, int64_t n, const int64_t *__restrict__ d_n, DevViews vs,
                       const int32_t *__restrict__ radius, float4 *__restrict__ grad2d, int64_t stride,
                       GaussGrads out, float reg_weight, double *__restrict__ partials) {
+  pdl_enter();
   __shared__ double red[FUSED_THREADS / 32];
   const int64_t live = live_count(d_n, n);
   const int tid = threadIdx.x;
@@ -361,6 +365,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 3)
 
 // *d_loss += the sum of the per-block partial sums (FP64 over the blocks)
 __global__ void k_fused_reduce(const double *__restrict__ partials, int64_t count, float *d_loss) {
+  pdl_enter();
   __shared__ double red[256];
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < count; i += 256) s += partials[i];
@@ -384,9 +389,8 @@ fgs_status launch_project_bwd(const fgs_gaussians *g, const DevViews &vs, const 
   if (g->n == 0) return FGS_OK;
   const int threads = 256;
   const int64_t blocks = (g->n + threads - 1) / threads;
-  k_project_bwd<<<(unsigned)blocks, threads, 0, st>>>(gauss_ptrs(g), g->n, g->d_n, vs, radius,
-                                                       reinterpret_cast<const float4 *>(grad2d), stride,
-                                                       gauss_grads(grads));
+  pdl_launch(k_project_bwd, (unsigned)blocks, threads, 0, st, gauss_ptrs(g), g->n, g->d_n, vs, radius,
+             reinterpret_cast<const float4 *>(grad2d), stride, gauss_grads(grads));
   count_launch();
   FGS_CHECK_LAUNCH("project_bwd");
   return FGS_OK;
@@ -413,10 +417,9 @@ extern "C" fgs_status fgs_project(const fgs_gaussians *g, const fgs_camera *cams
   if (g->n == 0) return FGS_OK;
   const int threads = 256;
   const int64_t blocks = (g->n + threads - 1) / threads;
-  k_project<<<(unsigned)blocks, threads, 0, as_stream(stream)>>>(
-      gauss_ptrs(g), g->n, g->d_n, vs, tiling.tile_w, tiling.tile_h,
-      reinterpret_cast<float4 *>(out->splat), out->radius, reinterpret_cast<uint2 *>(out->rect),
-      out->stride);
+  pdl_launch(k_project, (unsigned)blocks, threads, 0, as_stream(stream), gauss_ptrs(g), g->n, g->d_n, vs,
+             tiling.tile_w, tiling.tile_h, reinterpret_cast<float4 *>(out->splat), out->radius,
+             reinterpret_cast<uint2 *>(out->rect), out->stride);
   count_launch();
   FGS_CHECK_LAUNCH("fgs_project");
   return FGS_OK;
@@ -458,10 +461,10 @@ extern "C" fgs_status fgs_project_bwd_adam(fgs_gaussians *params, const fgs_proj
   if (params->n == 0) return FGS_OK;
   cudaStream_t st = as_stream(stream);
   const int64_t blocks = (params->n + FUSED_THREADS - 1) / FUSED_THREADS;
-  k_project_bwd_reg<<<(unsigned)blocks, FUSED_THREADS, 0, st>>>(
-      gauss_ptrs(params), params->n, params->d_n, vs, proj->radius, reinterpret_cast<float4 *>(grad2d),
-      proj->stride, gauss_grads(grads), reg_weight, static_cast<double *>(ws));
-  k_fused_reduce<<<1, 256, 0, st>>>(static_cast<double *>(ws), blocks, d_loss);
+  pdl_launch(k_project_bwd_reg, (unsigned)blocks, FUSED_THREADS, 0, st, gauss_ptrs(params), params->n, params->d_n,
+             vs, proj->radius, reinterpret_cast<float4 *>(grad2d), proj->stride, gauss_grads(grads), reg_weight,
+             static_cast<double *>(ws));
+  pdl_launch(k_fused_reduce, 1, 256, 0, st, static_cast<double *>(ws), blocks, d_loss);
   count_launch(2);
   FGS_CHECK_LAUNCH("fgs_project_bwd_adam");
   // Adam over all 14 planes; it clears the RGB gradient planes after reading them

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(kPruneBlock) k_prune_count(const float *__rest
                                                              const float *__restrict__ logit, int64_t cap,
                                                              float min_logit, float max_log_scale,
                                                              uint32_t *__restrict__ bsum, int64_t *__restrict__ ctl) {
+  pdl_enter();
   __shared__ uint32_t red[kPruneBlock / 32];
   const int64_t live = ctl[2];
   const int64_t i = blockIdx.x * (int64_t)kPruneBlock + threadIdx.x;
@@ -75,15 +76,20 @@ __global__ void __launch_bounds__(kPruneBlock) k_prune_count(const float *__rest
 // ctl[1] starts at INT64_MAX (no Gaussian removed) and is lowered by k_prune_count;
 // ctl[2] keeps the live count the whole call works on.
 __global__ void k_prune_init(const int64_t *d_n, int64_t n, int64_t *ctl) {
+  pdl_enter();
   ctl[0] = 0;
   ctl[1] = INT64_MAX;
   ctl[2] = live_count(d_n, n);
 }
 
-__global__ void k_prune_finish(const int64_t *__restrict__ ctl, int64_t *__restrict__ d_n) { *d_n = ctl[0]; }
+__global__ void k_prune_finish(const int64_t *__restrict__ ctl, int64_t *__restrict__ d_n) {
+  pdl_enter();
+  *d_n = ctl[0];
+}
 
 __global__ void __launch_bounds__(1024) k_prune_scan(uint32_t *__restrict__ bsum, int nb, int64_t *__restrict__ ctl,
                                                      int64_t *__restrict__ d_num_kept) {
+  pdl_enter();
   __shared__ unsigned long long part[1024];
   const int per = (nb + 1023) / 1024;
   const int lo = threadIdx.x * per, hi = min(nb, lo + per);
@@ -116,6 +122,7 @@ __global__ void __launch_bounds__(kPruneBlock) k_prune_index(const float *__rest
                                                              const uint32_t *__restrict__ bsum,
                                                              const int64_t *__restrict__ ctl,
                                                              uint32_t *__restrict__ src) {
+  pdl_enter();
   __shared__ uint32_t wsum[kPruneBlock / 32];
   const int64_t live = ctl[2];
   const int64_t first = ctl[1];
@@ -147,6 +154,7 @@ struct PlaneSet {
 
 __global__ void k_prune_gather(PlaneSet P, const uint32_t *__restrict__ src, const int64_t *__restrict__ ctl,
                                int64_t cap, float *__restrict__ scratch) {
+  pdl_enter();
   const int64_t kept = ctl[0], first = ctl[1];
   if (first >= kept) return;  // nothing moves
   const float *__restrict__ plane = P.p[blockIdx.y];
@@ -158,6 +166,7 @@ __global__ void k_prune_gather(PlaneSet P, const uint32_t *__restrict__ src, con
 
 __global__ void k_prune_copy(PlaneSet P, const int64_t *__restrict__ ctl, int64_t cap,
                              const float *__restrict__ scratch) {
+  pdl_enter();
   const int64_t kept = ctl[0], first = ctl[1];
   if (first >= kept) return;
   float *__restrict__ plane = P.p[blockIdx.y];
@@ -209,24 +218,24 @@ extern "C" fgs_status fgs_prune(fgs_gaussians *g, fgs_gaussians *m, fgs_gaussian
   }
   const int64_t nb = std::max<int64_t>(1, (n + kPruneBlock - 1) / kPruneBlock);
   FGS_CHECK_ARG(nb <= 1024 * 1024, "fgs_prune: too many Gaussians");
-  k_prune_init<<<1, 1, 0, st>>>(g->d_n, n, w.ctl);
-  k_prune_count<<<(unsigned)nb, kPruneBlock, 0, st>>>(g->log_scales, g->opacity_logits, cap, p->min_logit,
-                                                      p->max_log_scale, w.bsum, w.ctl);
-  k_prune_scan<<<1, 1024, 0, st>>>(w.bsum, (int)nb, w.ctl, d_num_kept);
-  k_prune_index<<<(unsigned)nb, kPruneBlock, 0, st>>>(g->log_scales, g->opacity_logits, cap, p->min_logit,
-                                                      p->max_log_scale, w.bsum, w.ctl, w.src);
+  pdl_launch(k_prune_init, 1, 1, 0, st, g->d_n, n, w.ctl);
+  pdl_launch(k_prune_count, (unsigned)nb, kPruneBlock, 0, st, g->log_scales, g->opacity_logits, cap, p->min_logit,
+             p->max_log_scale, w.bsum, w.ctl);
+  pdl_launch(k_prune_scan, 1, 1024, 0, st, w.bsum, (int)nb, w.ctl, d_num_kept);
+  pdl_launch(k_prune_index, (unsigned)nb, kPruneBlock, 0, st, g->log_scales, g->opacity_logits, cap, p->min_logit,
+             p->max_log_scale, w.bsum, w.ctl, w.src);
   count_launch(4);
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2 * num_sms()));
   fgs_gaussians *bufs[3] = {g, m, v};
   for (int b = 0; b < 3; ++b) {
     if (!bufs[b]) continue;
     const PlaneSet P = planes_of(bufs[b]);
-    k_prune_gather<<<dim3(gx, 14), 256, 0, st>>>(P, w.src, w.ctl, cap, w.scratch);
-    k_prune_copy<<<dim3(gx, 14), 256, 0, st>>>(P, w.ctl, cap, w.scratch);
+    pdl_launch(k_prune_gather, dim3(gx, 14), 256, 0, st, P, w.src, w.ctl, cap, w.scratch);
+    pdl_launch(k_prune_copy, dim3(gx, 14), 256, 0, st, P, w.ctl, cap, w.scratch);
     count_launch(2);
   }
   if (g->d_n) {
-    k_prune_finish<<<1, 1, 0, st>>>(w.ctl, g->d_n);
+    pdl_launch(k_prune_finish, 1, 1, 0, st, w.ctl, g->d_n);
     count_launch();
   }
   FGS_CHECK_LAUNCH("fgs_prune");

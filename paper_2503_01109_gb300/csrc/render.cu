@@ -21,6 +21,7 @@ namespace fgs {
 
 template <int TW, int TH, int BATCH, int PX>
 __global__ void __launch_bounds__(TW *TH / PX) k_render_fwd(RenderArgs a) {
+  pdl_enter();
   __shared__ __align__(16) char smem[TileSmem<BATCH>::fwd];
   render_fwd_tile<TW, TH, BATCH, PX>(a, blockIdx.x, smem);
 }
@@ -30,6 +31,7 @@ __global__ void __launch_bounds__(TW *TH / PX) k_render_fwd(RenderArgs a) {
 #endif
 template <int TW, int TH, int BATCH, int PX>
 __global__ void __launch_bounds__(TW *TH / PX, FGS_BWD_MINB) k_render_bwd(RenderBwdArgs a) {
+  pdl_enter();
   __shared__ __align__(16) char smem[TileSmem<BATCH>::bwd];
   render_bwd_tile<TW, TH, BATCH, PX>(a, blockIdx.x, smem);
 }
@@ -37,12 +39,12 @@ __global__ void __launch_bounds__(TW *TH / PX, FGS_BWD_MINB) k_render_bwd(Render
 template <int TW, int TH, int BATCH>
 static void launch_fwd(const RenderArgs &a, int blocks, cudaStream_t st) {
   constexpr int PX = PxPerThread<TW, TH>::fwd;
-  k_render_fwd<TW, TH, BATCH, PX><<<blocks, TW * TH / PX, 0, st>>>(a);
+  pdl_launch(k_render_fwd<TW, TH, BATCH, PX>, blocks, TW * TH / PX, 0, st, a);
 }
 template <int TW, int TH, int BATCH>
 static void launch_bwd(const RenderBwdArgs &a, int blocks, cudaStream_t st) {
   constexpr int PX = PxPerThread<TW, TH>::bwd;
-  k_render_bwd<TW, TH, BATCH, PX><<<blocks, TW * TH / PX, 0, st>>>(a);
+  pdl_launch(k_render_bwd<TW, TH, BATCH, PX>, blocks, TW * TH / PX, 0, st, a);
 }
 
 #define FGS_DISPATCH_TILING(tiling, FN, ...)                                          \
