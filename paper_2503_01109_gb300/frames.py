@@ -24,30 +24,40 @@ from .mapping import Mapper, PAPER_LOSS, PAPER_REG
 
 
 class KernelTimer:
-    """CUDA events around selected library calls on the current stream."""
+    """CUDA events around selected library calls on the current stream.
+
+    An event between two launches ends the overlap of programmatic dependent
+    launch there, so a measurement of whole steps times only the spans it needs
+    (`enable(names)`) and leaves the others to a separate breakdown pass."""
 
     def __init__(self):
         self.on = False
+        self.only = None
         self.events = {}
 
-    def enable(self):
+    def enable(self, names=None):
         self.on = True
+        self.only = None if names is None else set(names)
         self.events = {}
 
     def disable(self):
         self.on = False
+
+    def active(self, name) -> bool:
+        return self.on and (self.only is None or name in self.only)
 
     def span(self, name):
         timer = self
 
         class _Span:
             def __enter__(self_):
-                if timer.on:
+                self_.live = timer.active(name)
+                if self_.live:
                     self_.e0 = torch.cuda.Event(enable_timing=True)
                     self_.e0.record(torch.cuda.current_stream())
 
             def __exit__(self_, *a):
-                if timer.on:
+                if self_.live:
                     e1 = torch.cuda.Event(enable_timing=True)
                     e1.record(torch.cuda.current_stream())
                     timer.events.setdefault(name, []).append((self_.e0, e1))
@@ -266,7 +276,10 @@ class FramePipeline:
             return None
         return float(m.group(1))
 
-    def roofline(self, peaks: dict, profiles_dir: str | None = None):
+    def roofline(self, peaks: dict, profiles_dir: str | None = None, total_ms: float | None = None):
+        """The dominant render kernel against the derived ALU peak, from the launches
+        timed since the timer was enabled; share_of_step relative to total_ms (the
+        timed region) when given, else to the sum of the timed spans."""
         t = self.kernel_timer
         totals = {k: sum(t.durations(k)) for k in t.events}
         if not totals:
@@ -292,5 +305,5 @@ class FramePipeline:
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)",
-                "share_of_step": round(totals[name] / sum(totals.values()), 3),
+                "share_of_step": round(totals[name] / (total_ms or sum(totals.values())), 3),
                 "avg_launch_ms": round(float(np.mean(durs)), 4)}
