@@ -231,6 +231,10 @@ extern "C" fgs_status fgs_scale_reg(const fgs_gaussians *g, float weight, fgs_ga
 }
 
 namespace fgs {
+void launch_reduce_partials(const double *partials, int64_t count, float *d_loss, cudaStream_t st) {
+  pdl_launch(k_reduce_partials, 1, 256, 0, st, partials, count, d_loss);
+}
+
 fgs_status launch_adam(fgs_gaussians *params, fgs_gaussians *grads, fgs_gaussians *m, fgs_gaussians *v,
                        const fgs_adam_params *hp, int32_t *d_step, int zero_from, cudaStream_t st) {
   if (params->n == 0) return FGS_OK;

@@ -363,20 +363,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 3)
   }
 }
 
-// *d_loss += the sum of the per-block partial sums (FP64 over the blocks)
-__global__ void k_fused_reduce(const double *__restrict__ partials, int64_t count, float *d_loss) {
-  pdl_enter();
-  __shared__ double red[256];
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < count; i += 256) s += partials[i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *d_loss += (float)red[0];
-}
+// *d_loss += the sum of `count` FP64 partials, in a fixed order (loss.cu).
+void launch_reduce_partials(const double *partials, int64_t count, float *d_loss, cudaStream_t st);
 
 // Adam over the 14 planes (loss.cu); planes from zero_from on have their gradient
 // cleared after it is read.
@@ -464,7 +452,7 @@ extern "C" fgs_status fgs_project_bwd_adam(fgs_gaussians *params, const fgs_proj
   pdl_launch(k_project_bwd_reg, (unsigned)blocks, FUSED_THREADS, 0, st, gauss_ptrs(params), params->n, params->d_n,
              vs, proj->radius, reinterpret_cast<float4 *>(grad2d), proj->stride, gauss_grads(grads), reg_weight,
              static_cast<double *>(ws));
-  pdl_launch(k_fused_reduce, 1, 256, 0, st, static_cast<double *>(ws), blocks, d_loss);
+  launch_reduce_partials(static_cast<double *>(ws), blocks, d_loss, st);
   count_launch(2);
   FGS_CHECK_LAUNCH("fgs_project_bwd_adam");
   // Adam over all 14 planes; it clears the RGB gradient planes after reading them
