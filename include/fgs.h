@@ -260,7 +260,10 @@ size_t fgs_scale_reg_workspace_size(int64_t n);
  * optimisation of Sec. III-D; the paper does not name the optimiser).
  * lr per group: means, log_scales, quats, opacity, rgb.  The step number t >= 1 is
  * params->step, or, when d_step is not NULL, *d_step + 1 read on the device
- * (the call then increments *d_step, so a captured graph can be replayed). */
+ * (the call then increments *d_step, so a captured graph can be replayed).
+ * Per element: m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), with the square root
+ * and the quotient by the hardware approximations (a few ulp). */
 typedef struct {
   float lr[5];
   float beta1, beta2, eps;
