@@ -122,6 +122,9 @@ typedef struct {
  *   tiles of the rect on which q exceeds thr at every pixel centre.
  * in : g (n Gaussians), cams[n_views] (host), tiling.
  * out: out->splat/radius/rect for n_views x g->n records (stride out->stride >= n).
+ * Failure detection: a Gaussian whose mean, scales exp(log_scales), normalised
+ *   quaternion, opacity or colour is not finite is culled from every view (radius
+ *   0), and FGS_DEV_NONFINITE is or-ed into *d_status when d_status is not NULL.
  * err: INVALID_ARGUMENT for n_views outside 1..FGS_MAX_VIEWS, bad tiling, NULLs. */
 fgs_status fgs_project(const fgs_gaussians *g, const fgs_camera *cams, int32_t n_views,
                        fgs_tiling tiling, fgs_projected *out, int32_t *d_status, void *stream);
@@ -290,6 +293,21 @@ fgs_status fgs_project_bwd_adam(fgs_gaussians *params, const fgs_projected *proj
                                 float *d_loss, fgs_gaussians *m, fgs_gaussians *v, const fgs_adam_params *hp,
                                 int32_t *d_step, void *ws, size_t ws_bytes, void *stream);
 size_t fgs_project_bwd_adam_workspace_size(int64_t n);
+
+/* fgs_grid_barrier_probe -- self-test of the bounded grid barrier that separates
+ * the phases of fgs_render_window (the paper has no counterpart: this is the
+ * failure detection of the persistent launch).  n_blocks CTAs of a cooperative
+ * grid each arrive once at a barrier that waits for n_expected arrivals; a CTA
+ * gives up after timeout_ns, or-es FGS_DEV_TIMEOUT into *d_status and returns, so
+ * a barrier that can never complete (n_expected > n_blocks: an arrival nothing
+ * will make) ends in about timeout_ns and leaves the context usable.
+ * out: *d_passed += the number of CTAs whose wait completed (n_blocks when
+ *   n_expected == n_blocks, 0 when it is larger).
+ * ws: 32 bytes of device scratch (cleared by the call).
+ * err: INVALID_ARGUMENT unless 1 <= n_blocks <= the SM count, n_expected >=
+ *   n_blocks and 1 us <= timeout_ns <= 5 s; NULLs. */
+fgs_status fgs_grid_barrier_probe(int32_t n_blocks, int32_t n_expected, int64_t timeout_ns, void *ws,
+                                  size_t ws_bytes, uint32_t *d_passed, int32_t *d_status, void *stream);
 
 /* ---------------------------------------------------------------------------------
  * fgs_prune -- Gaussian pruning (Sec. III-A, "Gaussian Pruning"): removes every

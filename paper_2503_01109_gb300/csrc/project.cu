@@ -86,15 +86,33 @@ __device__ __forceinline__ bool project_view(const GaussLocal &L, const DevCam &
   return V.det > 0.0f;
 }
 
+// A Gaussian whose position, scales, normalised quaternion, opacity or colour is
+// not finite (a diverged optimisation, a zero quaternion) is culled from every
+// view, and FGS_DEV_NONFINITE is set in *d_status (when given), once per warp.
+__device__ __forceinline__ bool gaussian_finite(const GaussPtrs &g, int64_t i, const GaussLocal &L) {
+  float s = L.o;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s += L.mu[k] + L.s[k] + g.rgb[k * g.cap + i];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s += L.qn[k];
+  return isfinite(s);
+}
+
 __global__ void k_project(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_n, DevViews vs,
                           int tw, int th, float4 *__restrict__ splat, int32_t *__restrict__ radius,
-                          uint2 *__restrict__ rect, int64_t stride) {
+                          uint2 *__restrict__ rect, int64_t stride, int32_t *d_status) {
   pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const bool alive = i < live_count(d_n, n);
+  bool alive = i < live_count(d_n, n);
   GaussLocal L;
-  if (alive) load_gaussian(g, i, L);
+  if (alive) {
+    load_gaussian(g, i, L);
+    const bool bad = !gaussian_finite(g, i, L);
+    const unsigned m = __ballot_sync(__activemask(), bad);
+    if (m && d_status && (int)(threadIdx.x & 31) == __ffs(m) - 1) atomicOr(d_status, FGS_DEV_NONFINITE);
+    alive = !bad;
+  }
 #pragma unroll 1
   for (int v = 0; v < vs.n; ++v) {
     const DevCam &cm = vs.cam[v];
@@ -391,7 +409,6 @@ using namespace fgs;
 extern "C" fgs_status fgs_project(const fgs_gaussians *g, const fgs_camera *cams, int32_t n_views,
                                   fgs_tiling tiling, fgs_projected *out, int32_t *d_status,
                                   void *stream) {
-  (void)d_status;
   if (!gaussians_ok(g, "g")) return FGS_ERR_INVALID_ARGUMENT;
   FGS_CHECK_ARG(tiling_ok(tiling), "fgs_project: unsupported tiling %dx%d/%d", tiling.tile_w,
                 tiling.tile_h, tiling.batch_depth);
@@ -407,7 +424,7 @@ extern "C" fgs_status fgs_project(const fgs_gaussians *g, const fgs_camera *cams
   const int64_t blocks = (g->n + threads - 1) / threads;
   pdl_launch(k_project, (unsigned)blocks, threads, 0, as_stream(stream), gauss_ptrs(g), g->n, g->d_n, vs,
              tiling.tile_w, tiling.tile_h, reinterpret_cast<float4 *>(out->splat), out->radius,
-             reinterpret_cast<uint2 *>(out->rect), out->stride);
+             reinterpret_cast<uint2 *>(out->rect), out->stride, d_status);
   count_launch();
   FGS_CHECK_LAUNCH("fgs_project");
   return FGS_OK;

@@ -35,26 +35,28 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Grid-wide barrier with a bounded wait.  Returns false (for every thread of the
-// CTA) when the wait timed out.
-__device__ __forceinline__ bool grid_barrier(const WindowArgs &w, int *s_flag) {
+// Grid-wide barrier with a bounded wait over the counters ctl[3] (arrivals) and
+// ctl[4] (generation) for a grid of nblocks CTAs.  Returns false (for every thread
+// of the CTA) when the wait gave up after timeout_ns; FGS_DEV_TIMEOUT is then set.
+__device__ __forceinline__ bool grid_barrier_bounded(uint32_t *ctl, int32_t *status, uint32_t nblocks,
+                                                     int64_t timeout_ns, int *s_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile uint32_t *gen = w.ctl + 4;
+    volatile uint32_t *gen = ctl + 4;
     const uint32_t g = *gen;
     __threadfence();
-    const uint32_t arrived = atomicAdd(w.ctl + 3, 1u);
+    const uint32_t arrived = atomicAdd(ctl + 3, 1u);
     int ok = 1;
-    if (arrived == w.nblocks - 1) {
-      w.ctl[3] = 0;
+    if (arrived == nblocks - 1) {
+      ctl[3] = 0;
       __threadfence();
-      atomicAdd(w.ctl + 4, 1u);
+      atomicAdd(ctl + 4, 1u);
     } else {
       const uint64_t t0 = global_ns();
       while (*gen == g) {
-        if (global_ns() - t0 > (uint64_t)kBarrierTimeoutNs) {
+        if (global_ns() - t0 > (uint64_t)timeout_ns) {
           ok = 0;
-          atomicOr(w.status, FGS_DEV_TIMEOUT);
+          atomicOr(status, FGS_DEV_TIMEOUT);
           break;
         }
         __nanosleep(100);
@@ -65,6 +67,18 @@ __device__ __forceinline__ bool grid_barrier(const WindowArgs &w, int *s_flag) {
   }
   __syncthreads();
   return *s_flag != 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(const WindowArgs &w, int *s_flag) {
+  return grid_barrier_bounded(w.ctl, w.status, w.nblocks, kBarrierTimeoutNs, s_flag);
+}
+
+// The barrier alone, for its self-test: every CTA arrives once at a barrier that
+// expects `expected` arrivals; the CTAs that got through count themselves.
+__global__ void k_barrier_probe(uint32_t *ctl, int32_t *status, uint32_t expected, int64_t timeout_ns,
+                                uint32_t *passed) {
+  __shared__ int s_flag;
+  if (grid_barrier_bounded(ctl, status, expected, timeout_ns, &s_flag) && threadIdx.x == 0) atomicAdd(passed, 1u);
 }
 
 __device__ __forceinline__ int claim(uint32_t *counter, int *s_item) {
@@ -173,6 +187,24 @@ static bool window_loss_views(const fgs_camera *cams, int32_t n_views, LossViews
 }  // namespace fgs
 
 using namespace fgs;
+
+extern "C" fgs_status fgs_grid_barrier_probe(int32_t n_blocks, int32_t n_expected, int64_t timeout_ns,
+                                             void *ws, size_t ws_bytes, uint32_t *d_passed, int32_t *d_status,
+                                             void *stream) {
+  FGS_CHECK_ARG(n_blocks >= 1 && n_blocks <= num_sms() && n_expected >= n_blocks,
+                "fgs_grid_barrier_probe: need 1 <= n_blocks <= SM count and n_expected >= n_blocks");
+  FGS_CHECK_ARG(timeout_ns >= 1000 && timeout_ns <= 5000000000ll, "fgs_grid_barrier_probe: timeout_ns");
+  FGS_CHECK_ARG(ws && ws_bytes >= 8 * sizeof(uint32_t) && d_passed && d_status, "fgs_grid_barrier_probe: NULL");
+  cudaStream_t st = as_stream(stream);
+  FGS_CUDA(cudaMemsetAsync(ws, 0, 8 * sizeof(uint32_t), st), "fgs_grid_barrier_probe memset");
+  uint32_t *ctl = static_cast<uint32_t *>(ws);
+  uint32_t expected = (uint32_t)n_expected;
+  void *args[] = {&ctl, &d_status, &expected, &timeout_ns, &d_passed};
+  FGS_CUDA(cudaLaunchCooperativeKernel((const void *)k_barrier_probe, dim3(n_blocks), dim3(32), args, 0, st),
+           "fgs_grid_barrier_probe launch");
+  count_launch();
+  return FGS_OK;
+}
 
 extern "C" size_t fgs_render_window_workspace_size(const fgs_camera *cams, int32_t n_views) {
   if (!cams || n_views < 1 || n_views > FGS_MAX_VIEWS) return 0;

@@ -169,6 +169,8 @@ _OPTIONAL = {
     "fgs_render_window_workspace_size": ([c_void_p, c_int32], c_size_t),
     "fgs_loss_noalloc": ([c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                           c_void_p, c_void_p], c_int32),
+    "fgs_grid_barrier_probe": ([c_int32, c_int32, c_int64, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p],
+                               c_int32),
 }
 
 
@@ -422,6 +424,13 @@ def fgs_loss_noalloc(cams: list, color, depth, color_gt, depth_gt, w_c, w_d, w_s
     _check(lib().fgs_loss_noalloc(camera_array(cams), len(cams), _ptr(color), _ptr(depth), _ptr(color_gt),
                                   _ptr(depth_gt), ctypes.byref(p), _ptr(dC), _ptr(dD), _ptr(loss_acc), _stream()),
            "fgs_loss_noalloc")
+
+
+def fgs_grid_barrier_probe(n_blocks: int, n_expected: int, timeout_ns: int, ws, passed, status):
+    """Self-test of the window's bounded grid barrier (see include/fgs.h)."""
+    _check(lib().fgs_grid_barrier_probe(int(n_blocks), int(n_expected), int(timeout_ns), _ptr(ws),
+                                        ws.numel() * ws.element_size(), _ptr(passed), _ptr(status), _stream()),
+           "fgs_grid_barrier_probe")
 
 
 def fgs_scale_reg_workspace_size(n: int) -> int:

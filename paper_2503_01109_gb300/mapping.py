@@ -140,6 +140,32 @@ class Mapper:
         if not self.use_dc:
             self.g.n = int(self.num_kept.item())
 
+    # ------------------------------------------------------------------------------
+    def state_dict(self) -> dict:
+        """The mapping state for checkpoint / resume (host tensors): the live Gaussians'
+        parameters and both Adam moments, the live count and the step counters."""
+        n = int(self.g.d_n.item()) if self.use_dc else self.g.n
+        return {"n": n, "params": self.g.buf[:, :n].cpu(), "m": self.m.buf[:, :n].cpu(),
+                "v": self.v.buf[:, :n].cpu(), "host_step": self.host_step, "d_step": int(self.d_step.item())}
+
+    def load_state_dict(self, st: dict):
+        """Restores a state_dict() into this mapper's buffers (same or larger capacity);
+        gradients and per-pixel state start clean, as after a completed iteration."""
+        n = int(st["n"])
+        if n > self.g.capacity:
+            raise ValueError(f"checkpoint holds {n} Gaussians, capacity is {self.g.capacity}")
+        for gm, key in ((self.g, "params"), (self.m, "m"), (self.v, "v")):
+            gm.buf.zero_()
+            gm.buf[:, :n].copy_(st[key])
+        for gm in (self.g, self.m, self.v, self.grads):
+            gm.n = n
+            gm.d_n.fill_(n)
+        self.host_step = int(st["host_step"])
+        self.d_step.fill_(int(st["d_step"]))
+        self.grads.buf.zero_()
+        self.grad2d.zero_()
+        self._clean = True
+
     def check_status(self):
         s = int(self.status.item())
         if s:
