@@ -1,6 +1,7 @@
 """Pins of the Fourier-seeding oracle (Sec. III-A) against library routines,
 closed forms and hand-built cases."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -79,23 +80,26 @@ def test_highpass_of_cosine_closed_form(k0, d0):
     assert np.abs(E - np.abs(h * g)).max() < 1e-12
 
 
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_lines(name):
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            lhs, rhs = line.split("->")
+            yield lhs.split(), rhs.strip()
+
+
 def test_triangle_threshold_hand_built():
-    # peak at 1 (10), far end at 6 (1): line (1,10)-(6,1); distance numerators
-    # |5 (h_i - 10) + 9 (i - 1)|: i=2: |5*-2+9|=1, i=3: |5*-4+18|=2, i=4: |5*-6+27|=3,
-    # i=5: |5*-8+36|=4 -> t = 5
-    h = np.zeros(256, int); h[1:7] = [10, 8, 6, 4, 2, 1]
-    assert osd.triangle_threshold(h) == 5
-    # convex decay: peak 0 (100), end 4 (1): |4 (h_i - 100) + 99 i|: i=1: |-320+99|=221 ...
-    h = np.zeros(256, int); h[0:5] = [100, 20, 10, 5, 1]
-    d = [abs(4 * (h[i] - 100) + 99 * i) for i in range(5)]
-    assert osd.triangle_threshold(h) == int(np.argmax(d)) == 1
-    # mirrored: peak 255 (10), far end 250 (1): |-5 (h_i - 10) + 9 (i - 255)|:
-    # i=254: 1, 253: 2, 252: 3, 251: 4, 250: 0 -> t = 251
-    h = np.zeros(256, int); h[250:256] = [1, 2, 4, 6, 8, 10]
-    assert osd.triangle_threshold(h) == 251
-    # single non-empty bin
-    h = np.zeros(256, int); h[7] = 5
-    assert osd.triangle_threshold(h) == 7
+    cases = list(_golden_lines("triangle_threshold.txt"))
+    assert len(cases) == 4
+    for bins, t in cases:
+        h = np.zeros(256, int)
+        for b in bins:
+            i, c = b.split(":")
+            h[int(i)] = int(c)
+        assert osd.triangle_threshold(h) == int(t), bins
     # far end ties resolve to the high side
     h = np.zeros(256, int); h[[3, 5, 7]] = [1, 9, 1]
     assert osd.triangle_threshold(h) in (5, 6, 7)
@@ -108,16 +112,15 @@ def test_bins_f32():
 
 
 def test_missing_mask_hand_built():
-    H, W = 1, 6
-    A = np.array([[0.4, 0.9, 0.9, 0.9, 0.0, 0.9]], np.float32)
-    D = np.array([[1.0, 2.0 * 0.9, 1.0 * 0.9, 1.0 * 0.9, 0.0, 1.0 * 0.9]], np.float32)
-    Dg = np.array([[1.0, 1.0, 1.0, 0.0, 1.0, 1.0]], np.float32)
+    cases = [([float(x) for x in lhs], int(rhs)) for lhs, rhs in _golden_lines("missing_mask.txt")]
+    assert len(cases) == 6
+    v = np.array([c[0] for c in cases], np.float32)
+    H, W = 1, len(cases)
+    A, D, Dg = v[:, 0][None], v[:, 1][None], v[:, 2][None]
     C = np.zeros((3, H, W), np.float32)
-    Cg = np.zeros((3, H, W), np.float32); Cg[:, 0, 5] = 0.2
+    Cg = np.broadcast_to(v[:, 3][None, None], (3, H, W)).astype(np.float32)
     M = osd.missing_mask_f32(C, D, A, Cg, Dg)
-    # px0: A<0.5; px1: rendered depth 2 vs 1 -> foreground; px2: consistent; px3: no gt depth;
-    # px4: A=0 -> M_i; px5: colour difference 0.6 > 0.3
-    assert list(M[0]) == [True, True, False, False, True, True]
+    assert [int(x) for x in M[0]] == [c[1] for c in cases]
 
 
 def test_seed_selection_order_grid_and_cap():
