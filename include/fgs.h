@@ -19,10 +19,11 @@
  *    from caller-given workspace (size queried with the *_workspace_size calls).
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Calls are asynchronous, never synchronise the host, and can be captured
- *    into a CUDA graph.  Kernels are launched with programmatic dependent launch
- *    (each waits for its predecessor on the stream before touching memory, so
- *    plain stream order holds); FGS_PDL=0 in the environment launches them
- *    without it.
+ *    into a CUDA graph.  The projection, binning, render, loss, Adam, seeding,
+ *    pruning, tracking and keyframe kernels are launched with programmatic
+ *    dependent launch (each waits for its predecessor on the stream before
+ *    touching memory, so plain stream order holds); FGS_PDL=0 in the
+ *    environment launches them without it.
  *  - The return value reports argument and launch errors (fgs_status).  On a
  *    non-zero return nothing was launched or the launch failed; the message is in
  *    fgs_last_error() (thread-local).  No C++ exception crosses the ABI.
