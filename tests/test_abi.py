@@ -52,3 +52,36 @@ def test_host_checks_need_no_gpu(lib):
     g.n, g.capacity = 5, 2
     rc = L.fgs_project(ctypes.byref(g), cams, 1, fgs.tiling(16, 16, 128), None, None, None)
     assert rc == 1 and b"capacity" in L.fgs_last_error()
+
+
+def test_barrier_probe_argument_checks(lib):
+    """fgs_grid_barrier_probe refuses unusable grids before any CUDA call."""
+    from paper_2503_01109_gb300 import fgs
+    L = fgs.lib()
+    ws = ctypes.create_string_buffer(64)
+    word = ctypes.c_int32(0)
+    ok_ptr = ctypes.cast(ws, ctypes.c_void_p)
+    p = ctypes.cast(ctypes.byref(word), ctypes.c_void_p)
+    for n_blocks, n_expected, timeout_ns in ((0, 1, 10**6), (8, 7, 10**6), (4, 4, 10), (4, 4, 6 * 10**9),
+                                             (100000, 100000, 10**6)):
+        rc = L.fgs_grid_barrier_probe(n_blocks, n_expected, timeout_ns, ok_ptr, 64, p, p, None)
+        assert rc == 1, (n_blocks, n_expected, timeout_ns)
+    rc = L.fgs_grid_barrier_probe(4, 4, 10**6, None, 64, p, p, None)
+    assert rc == 1 and b"NULL" in L.fgs_last_error()
+
+
+def test_kernel_timer_selects_spans():
+    """The bench's timer records only the spans it was enabled for (no events are
+    created for the others, so nothing here needs a GPU)."""
+    from paper_2503_01109_gb300.frames import KernelTimer
+    t = KernelTimer()
+    assert not t.active("render_bwd")
+    t.enable(("render_fwd", "render_bwd"))
+    assert t.active("render_bwd") and t.active("render_fwd") and not t.active("loss")
+    with t.span("loss"):
+        pass
+    assert t.events == {}
+    t.enable()
+    assert t.active("loss")
+    t.disable()
+    assert not t.active("render_bwd")
