@@ -1,0 +1,62 @@
+"""The keyframe window at the benchmark's size and launch configuration: 4 views
+at 640x480 (f = 525) and 4 at 1200x680 (f = 600) of the benchmark trajectory over
+the 1M-Gaussian room map, 16x32 tiles with batch depth 256.  A property that holds
+at any size: the one persistent launch equals the separate forward, loss and
+adjoint calls -- images, contributor counts and image gradients bit-identical,
+the loss to 1e-6, the atomically summed gradients within 1e-4 relative."""
+import pytest
+import torch
+
+from paper_2503_01109_gb300 import fgs, synthetic as syn
+from paper_2503_01109_gb300.frames import render_targets_views
+from paper_2503_01109_gb300.mapping import Mapper
+from paper_2503_01109_gb300.window import Window
+
+from gpu_helpers import grad_close
+
+pytestmark = pytest.mark.gpu
+
+
+def bench_window_views():
+    a = syn.trajectory(16, seed=100, width=640, height=480, f=525.0)
+    b = syn.trajectory(16, seed=100, width=1200, height=680, f=600.0)
+    return [a[0], a[4], a[8], a[12], b[2], b[6], b[10], b[14]]
+
+
+def test_full_size_window_equals_separate_calls(cuda_device):
+    cams = bench_window_views()
+    til = fgs.tiling(16, 32, 256)
+    cg, dg = render_targets_views(syn.room_scene(1_000_000, seed=1000, kind="gt"), cams)
+    sc = syn.room_scene(1_000_000, seed=0, kind="map")
+    ref = Mapper(fgs.GaussianMap.from_scene(sc), cams, til, reg_w=0.0, use_device_count=True)
+    ref.set_target(cg, dg)
+    ref.render()
+    fgs.fgs_memset_async(ref.loss_acc)
+    fgs.fgs_loss(cams, ref.frame.color, ref.frame.depth, cg, dg, 0.9, 0.1, 0.1, ref.dC, ref.dD, ref.loss_acc,
+                 ref.ws_loss)
+    ref.backward(ref.dC, ref.dD)
+    torch.cuda.synchronize()
+    ref_out = {k: getattr(ref.frame, k).clone() for k in ("color", "depth", "alpha", "t_final", "n_contrib")}
+    ref_dC, ref_dD, ref_loss = ref.dC.clone(), ref.dD.clone(), float(ref.loss_acc.item())
+    ref_grads = ref.grads.buf.cpu().numpy()
+    assert int(ref.status.item()) == 0
+    del ref
+    win = Window(fgs.GaussianMap.from_scene(sc), cams, til, reg_w=0.0)
+    win.set_target(cg, dg)
+    fgs.fgs_project(win.g, cams, til, win.proj, win.status, True)
+    fgs.fgs_bin_sort(win.proj, win.g.capacity, cams, til, win.ws_bin, win.tile_keys, win.ids, win.ranges,
+                     win.num_pairs, win.status)
+    for t in (win.grads.buf, win.grad2d, win.loss_acc):
+        fgs.fgs_memset_async(t)
+    fgs.fgs_render_window(win.g, win.proj, cams, til, win.ids, win.ranges, cg, dg, 0.9, 0.1, 0.1, win.frame, win.dC,
+                          win.dD, win.grad2d, win.grads, win.loss_acc, win.ws_win, win.status)
+    fgs.fgs_project_bwd(win.g, win.proj, cams, win.grad2d, win.grads, True)
+    torch.cuda.synchronize()
+    assert int(win.status.item()) == 0
+    assert int(win.num_pairs.item()) > 10_000_000
+    for k, v in ref_out.items():
+        assert torch.equal(getattr(win.frame, k), v), k
+    assert torch.equal(win.dC, ref_dC) and torch.equal(win.dD, ref_dD)
+    assert float(win.loss_acc.item()) == pytest.approx(ref_loss, rel=1e-6)
+    bad, _ = grad_close(win.grads.buf.cpu().numpy(), ref_grads, rel=1e-4)
+    assert bad.mean() < 1e-4, int(bad.sum())
