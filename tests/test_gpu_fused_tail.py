@@ -84,6 +84,49 @@ def test_fused_tail_equals_separate_calls(cuda_device, use_dc, reg_w):
     m.check_status()
 
 
+def test_fused_tail_full_size(cuda_device):
+    """The benchmark's size: the 1M-Gaussian room map at a 1200x680 frame of the
+    benchmark trajectory, 16x16 tiles, batch depth 128, device count."""
+    from paper_2503_01109_gb300.frames import render_targets
+    cam = syn.trajectory(1, seed=100, width=1200, height=680, f=600.0)[0]
+    colors, depths = render_targets(syn.room_scene(1_000_000, seed=1000, kind="gt"), [cam])
+    g = fgs.GaussianMap.from_scene(syn.room_scene(1_000_000, seed=0, kind="map"), 1_100_000, "cuda")
+    m = Mapper(g, [cam], fgs.tiling(16, 16, 128), use_device_count=True)
+    m.set_target(colors[0], depths[0])
+    _adjoint(m)
+    snap = {k: t.clone() for k, t in (("p", m.g.buf), ("m", m.m.buf), ("v", m.v.buf), ("g2", m.grad2d),
+                                      ("rgb", m.grads.plane("rgb")), ("loss", m.loss_acc))}
+    fgs.fgs_project_bwd(m.g, m.proj, m.cams, m.grad2d, m.grads, True)
+    fgs.fgs_scale_reg(m.g, m.reg_w, m.grads, m.loss_acc, m.ws_reg, True)
+    fgs.fgs_adam(m.g, m.grads, m.m, m.v, m.lr, step=1, d_step=m.d_step, use_device_count=True)
+    torch.cuda.synchronize()
+    n = 1_000_000
+    ref_g = m.grads.buf[:11, :n].cpu().numpy()
+    ref_p, ref_loss = m.g.buf[:, :n].cpu().numpy(), float(m.loss_acc.item())
+    m.g.buf.copy_(snap["p"])
+    m.m.buf.copy_(snap["m"])
+    m.v.buf.copy_(snap["v"])
+    m.grad2d.copy_(snap["g2"])
+    m.grads.buf.zero_()
+    m.grads.plane("rgb").copy_(snap["rgb"])
+    m.loss_acc.copy_(snap["loss"])
+    m.d_step.zero_()
+    fgs.fgs_project_bwd_adam(m.g, m.proj, m.cams, m.grad2d, m.grads, m.reg_w, m.loss_acc, m.m, m.v, m.lr,
+                             step=1, d_step=m.d_step, ws=m.ws_fused, use_device_count=True)
+    torch.cuda.synchronize()
+    m.check_status()
+    got_g = m.grads.buf[:11, :n].cpu().numpy()
+    assert np.allclose(got_g, ref_g, rtol=1e-6, atol=1e-6 * np.abs(ref_g).max())
+    x0 = snap["p"][:, :n].cpu().numpy().astype(np.float64)
+    x, y = ref_p.astype(np.float64), m.g.buf[:, :n].cpu().numpy().astype(np.float64)
+    big = np.maximum(np.maximum(np.abs(x0), np.abs(x)), np.abs(y)).astype(np.float32)
+    tol = 1e-5 * np.abs(x - x0) + 4.0 * np.spacing(big).astype(np.float64)
+    assert (np.abs(x - y) <= tol).mean() > 0.9999
+    assert abs(float(m.loss_acc.item()) - ref_loss) <= 1e-6 * abs(ref_loss)
+    assert float(m.grads.plane("rgb").abs().max().item()) == 0.0
+    assert float(m.grad2d.abs().max().item()) == 0.0
+
+
 def test_mapping_iterations_with_the_fused_tail(cuda_device):
     # a plain adjoint (RenderFn's path) between fused iterations leaves dirty gradients;
     # the next fused iteration clears them first and the loss keeps falling

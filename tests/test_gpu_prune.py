@@ -36,7 +36,7 @@ def _moments(cap, seed):
 
 
 @pytest.mark.parametrize("use_dc", [False, True])
-@pytest.mark.parametrize("n,cap", [(100_000, 120_003), (1, 8), (4097, 4097)])
+@pytest.mark.parametrize("n,cap", [(100_000, 120_003), (1, 8), (4097, 4097), (1_113_679, 2_200_000)])
 def test_prune_matches_oracle(cuda_device, use_dc, n, cap):
     g, planes = _random_map(n, cap, 3)
     m, v = _moments(cap, 4)
