@@ -85,3 +85,36 @@ def test_kernel_timer_selects_spans():
     assert t.active("loss")
     t.disable()
     assert not t.active("render_bwd")
+
+
+def test_fused_tail_argument_checks(lib):
+    """fgs_project_bwd_adam answers argument errors before any CUDA call: a short
+    workspace, a missing step number, grads that do not cover the parameters."""
+    from paper_2503_01109_gb300 import fgs, synthetic as syn
+    L = fgs.lib()
+    cams = fgs.camera_array([syn.pinhole(64, 48, 60.0)])
+
+    def gaussians(n, cap):
+        g = fgs.Gaussians()
+        g.n, g.capacity, g.d_n = n, cap, None
+        base = 1 << 20                     # never dereferenced: every call below fails its checks first
+        g.means, g.log_scales, g.quats = base, base + 12 * cap, base + 24 * cap
+        g.opacity_logits, g.rgb = base + 40 * cap, base + 44 * cap
+        return g
+
+    p, gr, m, v = (gaussians(1000, 1024) for _ in range(4))
+    proj = fgs.Projected(1024, 1 << 20, 1 << 21, 1 << 22)
+    hp = fgs.AdamParams()
+    hp.step = 1
+    need = L.fgs_project_bwd_adam_workspace_size(1000)
+    assert need >= 8 * 4
+    args = lambda grads, hp_, ws_bytes: (ctypes.byref(p), ctypes.byref(proj), cams, 1, ctypes.c_void_p(1 << 23),
+                                         ctypes.byref(grads), 0.01, ctypes.c_void_p(1 << 24), ctypes.byref(m),
+                                         ctypes.byref(v), ctypes.byref(hp_), None, ctypes.c_void_p(1 << 25),
+                                         ws_bytes, None)
+    assert L.fgs_project_bwd_adam(*args(gr, hp, need - 1)) == 1 and b"workspace" in L.fgs_last_error()
+    hp0 = fgs.AdamParams()
+    hp0.step = 0
+    assert L.fgs_project_bwd_adam(*args(gr, hp0, need)) == 1 and b"step" in L.fgs_last_error()
+    short = gaussians(500, 1024)
+    assert L.fgs_project_bwd_adam(*args(short, hp, need)) == 1 and b"cover" in L.fgs_last_error()
