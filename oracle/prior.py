@@ -18,6 +18,12 @@ differences are their FP32 accumulation order):
             dz1 = bf16(dh1 * gelu'(z1)); dW1 = dz1^T x; bias gradients are the
             column sums of dy, dz2, dz1.
   Adam on FP32 master weights, then BF16 copies.
+  use     : for a high-frequency seed the predicted opacity logit replaces
+            eq11's initial logit, and the predicted log-scales replace eq11's
+            radius unless one of the three lies further than max_dev from
+            eq11's log-scale (then all three stay eq11's: eq11 judges the
+            prediction's scale and says nothing about opacity); low-frequency
+            seeds keep eq11's values.  The distance test is taken in float32.
 GELU is the erf form x Phi(x); its derivative Phi(x) + x phi(x).
 """
 from __future__ import annotations
@@ -132,3 +138,21 @@ def adam_step(params: dict, grads: dict, m: dict, v: dict, t: int, lr=1e-3, b1=0
         vh = v[k] / (1 - b2 ** t)
         out[k] = np.asarray(params[k], np.float64) - lr * mh / (np.sqrt(vh) + eps)
     return out
+
+
+def apply_to_seeds(pred, log_scales_eq11, logits_eq11, is_high, max_dev):
+    """The learned prior's initialisation of freshly seeded Gaussians (an
+    extension of eq11 of Sec. III-A; see the module docstring).
+
+    pred[k][4] (log-scale x, y, z, opacity logit) per seed, log_scales_eq11[3][k]
+    and logits_eq11[k] as eq11 wrote them, is_high[k] the frequency class.
+    Returns (log_scales[3][k], logits[k]) as float32."""
+    pred = np.asarray(pred, np.float32)
+    ls = np.array(log_scales_eq11, np.float32, copy=True)
+    lg = np.array(logits_eq11, np.float32, copy=True)
+    hi = np.asarray(is_high, bool)
+    dev = np.abs(pred[:, :3] - ls.T)                      # float32 subtraction and magnitude
+    accept = hi & np.all(dev <= np.float32(max_dev), axis=1)
+    lg[hi] = pred[hi, 3]
+    ls[:, accept] = pred[accept, :3].T
+    return ls, lg

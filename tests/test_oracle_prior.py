@@ -71,3 +71,56 @@ def test_patch_features_constant_and_clamp():
     P = np.tile(ramp[0, cols], (16, 1))
     F = np.fft.fft2(P)
     assert f2[0, :256] == pytest.approx(np.log1p(np.abs(F)).ravel(), abs=1e-12)
+
+
+def test_adam_constant_gradient_closed_form():
+    """With a constant gradient g the bias-corrected moments are exactly g and g^2
+    at every step (m_t = (1 - b1^t) g, v_t = (1 - b2^t) g^2), so every step moves a
+    parameter by lr g / (|g| + eps): five steps move it by 5 lr sign(g) up to eps."""
+    p = {"w": np.array([0.5, -1.0, 2.0])}
+    g = {"w": np.array([0.25, -3e-3, 7.0])}
+    m = {"w": np.zeros(3)}
+    v = {"w": np.zeros(3)}
+    for t in range(1, 6):
+        p = op.adam_step(p, g, m, v, t, lr=0.01, eps=1e-8)
+    want = np.array([0.5, -1.0, 2.0]) - 5 * 0.01 * g["w"] / (np.abs(g["w"]) + 1e-8)
+    assert p["w"] == pytest.approx(want, rel=1e-12, abs=1e-15)
+
+
+def test_adam_two_steps_hand_values():
+    """Two steps with g1 = 0.5, g2 = -0.25 (lr 0.1, b1 0.9, b2 0.999, eps 1e-8),
+    worked by hand: step 1 moves by -0.1 * 0.5 / (0.5 + 1e-8); step 2 has
+    m = 0.045 - 0.025 = 0.02, m_hat = 0.02 / 0.19 = 0.10526315789473684,
+    v = 0.999 * 0.00025 + 0.001 * 0.0625 = 0.00031225,
+    v_hat = 0.00031225 / 0.001999 = 0.15620310155077539, sqrt = 0.39522538070166418,
+    so it moves by -0.1 * 0.10526315789473684 / (0.39522538070166418 + 1e-8)."""
+    p = {"w": np.array([1.0])}
+    m = {"w": np.zeros(1)}
+    v = {"w": np.zeros(1)}
+    p = op.adam_step(p, {"w": np.array([0.5])}, m, v, 1, lr=0.1, eps=1e-8)
+    p1 = 1.0 - 0.1 * 0.5 / (0.5 + 1e-8)
+    assert p["w"][0] == pytest.approx(p1, rel=1e-15)
+    p = op.adam_step(p, {"w": np.array([-0.25])}, m, v, 2, lr=0.1, eps=1e-8)
+    assert m["w"][0] == pytest.approx(0.02, rel=1e-14)
+    assert v["w"][0] == pytest.approx(0.00031225, rel=1e-14)
+    assert p["w"][0] == pytest.approx(p1 - 0.1 * 0.10526315789473684 / (0.39522538070166418 + 1e-8), rel=1e-13)
+
+
+def test_apply_to_seeds_hand_cases():
+    """The prior's use on seeds: high-frequency seeds take the predicted logit
+    always and the predicted log-scales only when all three lie within max_dev of
+    eq11's; low-frequency seeds keep eq11 entirely.  The boundary is inclusive."""
+    ls11 = np.array([[-5.0, -5.0, -5.0, -4.0]] * 3, np.float32)     # eq11: one value on all axes
+    lg11 = np.zeros(4, np.float32)
+    pred = np.array([[-5.5, -4.6, -5.0, 1.5],      # all within 1.0: accepted
+                     [-5.5, -6.5, -5.0, -2.0],     # y 1.5 away: eq11's scales, predicted logit
+                     [-5.5, -4.5, -5.0, 3.0],      # low-frequency: untouched
+                     [-5.0, -3.0, -4.0, 0.25]],    # 1.0 exactly away on y: inclusive, accepted
+                    np.float32)
+    hi = np.array([True, True, False, True])
+    ls, lg = op.apply_to_seeds(pred, ls11, lg11, hi, 1.0)
+    assert ls[:, 0].tolist() == np.float32([-5.5, -4.6, -5.0]).tolist()
+    assert ls[:, 1].tolist() == [-5.0, -5.0, -5.0]
+    assert ls[:, 2].tolist() == [-5.0, -5.0, -5.0]
+    assert ls[:, 3].tolist() == [-5.0, -3.0, -4.0]
+    assert lg.tolist() == [1.5, -2.0, 0.0, 0.25]

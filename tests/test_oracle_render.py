@@ -120,26 +120,139 @@ def test_two_gaussians_front_to_back():
     assert out["depth"][y, x] == pytest.approx(2.0 * a1 + 3.5 * a2 * (1 - a1), rel=1e-12)
 
 
-@pytest.mark.parametrize("W,H,tw,th", [(64, 48, 16, 16), (70, 45, 16, 16), (70, 45, 8, 8), (50, 70, 16, 32)])
-def test_binned_equals_brute_force(W, H, tw, th):
-    """Tile-binned lists + blending == per-pixel brute force over all Gaussians."""
-    sc = syn.tiny_scene(600, seed=W + H)
+def _three_sigma_rects(mean2d, conic, radius, cam, tw, th):
+    """Tile bounds of the plain 3-sigma boxes (the bounding box of the ellipse
+    {q <= 9} of the dilated 2D covariance, the inverse of the conic), computed here
+    from the splats and not by the oracle's projection; empty for culled splats."""
+    A, B, C = conic[:, 0], conic[:, 1], conic[:, 2]
+    det = A * C - B * B
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ex, ey = 3.0 * np.sqrt(C / det), 3.0 * np.sqrt(A / det)
+    tx, ty = orr.tiles_of(cam, tw, th)
+    x0 = np.maximum(np.ceil((mean2d[:, 0] - ex - (tw - 1)) / tw), 0)
+    x1 = np.minimum(np.floor((mean2d[:, 0] + ex) / tw), tx - 1)
+    y0 = np.maximum(np.ceil((mean2d[:, 1] - ey - (th - 1)) / th), 0)
+    y1 = np.minimum(np.floor((mean2d[:, 1] + ey) / th), ty - 1)
+    rect = np.stack([x0, y0, x1, y1], 1)
+    rect[radius <= 0] = [1, 1, 0, 0]
+    return np.ascontiguousarray(np.nan_to_num(rect, nan=0.0).astype(np.int32))
+
+
+@pytest.mark.parametrize("W,H,tw,th,kind", [(64, 48, 16, 16, "tiny"), (70, 45, 8, 8, "tiny"), (50, 70, 16, 32, "tiny"),
+                                            (70, 45, 16, 16, "clamp"), (64, 48, 16, 16, "saturate"),
+                                            (64, 48, 16, 16, "needle")])
+def test_binned_equals_three_sigma_brute_force(W, H, tw, th, kind):
+    """The opacity-aware cut of the projection's tile rect (the 3-sigma box cut to
+    the ellipse where alpha can reach 1/255) and the per-tile support test drop
+    only pairs that cannot blend: the tile-binned render equals, bit for bit, a
+    brute force over the plain 3-sigma tile boxes computed here from the conics
+    (every pixel of every tile in a Gaussian's box, no support test), ordered by
+    (float32 depth bits, id).  Low opacities (logits down to -3) make the cut
+    bite.  The 3-sigma box itself is the rasteriser's truncation of each splat,
+    part of the definition, not an approximation."""
+    if kind == "tiny":
+        sc = syn.tiny_scene(800, seed=W * H)
+        sc["logits"] = np.random.default_rng(W).normal(-0.5, 1.2, 800).astype(np.float32)
+    else:
+        sc = syn.edge_scene(kind, 800, seed=W + H)
     cam = syn.pinhole(W, H, 60.0)
     st = orr.render_views(sc, [cam], tw, th)
     pr, out = st["proj"][0], st["out"][0]
-    br = orr.render_brute(pr, st["scene_aos"]["rgb"], cam, pr["depth"].astype(np.float32), pr["radius"], pr["rect"],
+    rect3 = _three_sigma_rects(pr["mean2d"], pr["conic"], pr["radius"], cam, tw, th)
+    br = orr.render_brute(pr, st["scene_aos"]["rgb"], cam, pr["depth"].astype(np.float32), pr["radius"], rect3,
                           tw, th)
     assert np.array_equal(br["color"], out["color"])
     assert np.array_equal(br["depth"], out["depth"])
     assert np.array_equal(br["alpha"], out["alpha"])
-    # the binned lists drop tiles outside the opacity-aware support, the brute force
-    # does not: equal images show the dropped tiles held no blended pixel
-    supp = orr.support_f64(pr)
-    P = orr.lib().or_count_pairs(1, pr["radius"].size, orr._p(pr["radius"]), orr._p(pr["rect"]), orr._p(supp),
-                                 0, tw, th)
-    P_box = orr.lib().or_count_pairs(1, pr["radius"].size, orr._p(pr["radius"]), orr._p(pr["rect"]), None, 0,
-                                     tw, th)
-    assert len(st["ids"]) == P < P_box
+    # the cut removed something: fewer pairs than the plain 3-sigma boxes hold
+    P = len(st["ids"])
+    P_box = orr.lib().or_count_pairs(1, pr["radius"].size, orr._p(pr["radius"]), orr._p(rect3), None, 0, tw, th)
+    assert P < P_box
+
+
+def test_float32_support_drops_no_blending_pair():
+    """The float32 support test the kernels take (teacher-forced binning) is safe
+    too: on splats rounded to float32, lists binned over the plain 3-sigma boxes
+    with the float32 support decisions render exactly like the brute force over
+    those boxes (both blended in FP64 on the same float32-valued splats)."""
+    W, H, tw, th = 70, 45, 16, 16
+    sc = syn.tiny_scene(800, seed=9)
+    sc["logits"] = np.random.default_rng(2).normal(-0.5, 1.2, 800).astype(np.float32)
+    cam = syn.pinhole(W, H, 60.0)
+    pr = orr.project(orr.aos(sc), cam, tw, th)
+    rec = np.zeros((800, 8), np.float32)
+    rec[:, 0:2], rec[:, 2:5] = pr["mean2d"], pr["conic"]
+    rec[:, 5], rec[:, 6], rec[:, 7] = pr["opacity"], pr["depth"], pr["thr"]
+    rect3 = _three_sigma_rects(rec[:, 0:2].astype(np.float64), rec[:, 2:5].astype(np.float64), pr["radius"], cam,
+                               tw, th)
+    sp = orr.splats_from_gpu(rec, pr["radius"], rect3)
+    rgb = orr.aos(sc)["rgb"]
+    _, ids, ranges = orr.bin_sort([cam], tw, th, rec[:, 6][None], pr["radius"][None], rect3[None],
+                                  orr.support_f32(rec)[None])
+    out = orr.render_fwd(sp, rgb, cam, ids, ranges, 0, tw, th)
+    br = orr.render_brute(sp, rgb, cam, rec[:, 6], pr["radius"], rect3, tw, th)
+    assert np.array_equal(br["color"], out["color"]) and np.array_equal(br["alpha"], out["alpha"])
+    assert len(ids) < orr.lib().or_count_pairs(1, 800, orr._p(pr["radius"]), orr._p(rect3), None, 0, tw, th)
+
+
+def test_adjoint_central_differences_at_the_clamps():
+    """Central differences of the oracle's forward on the branches the plain scenes
+    seldom take: Gaussians beyond the Jacobian clamp in x and in y, and opaque ones
+    whose alpha saturates at 0.99 (their opacity and geometry gradients through the
+    clamped pairs are zero)."""
+    rng = np.random.default_rng(21)
+    n = 24
+    sc = {k: v.astype(np.float64) for k, v in syn.tiny_scene(n, seed=8).items()}
+    sc["means"][2] = rng.uniform(1.8, 2.6, n)
+    sc["log_scales"][:] = rng.normal(-2.4, 0.2, (3, n))
+    W, H, f = 40, 30, 40.0
+    limx, limy = 1.3 * 0.5 * W / f, 1.3 * 0.5 * H / f
+    for j in range(0, 4):          # beyond the x clamp, reaching into the image
+        sc["means"][0, j] = (limx + 0.08) * sc["means"][2, j] * (1 if j % 2 else -1)
+        sc["means"][1, j] = 0.1 * sc["means"][2, j]
+        sc["log_scales"][:, j] = -1.4
+    for j in range(4, 8):          # beyond the y clamp
+        sc["means"][1, j] = (limy + 0.08) * sc["means"][2, j] * (1 if j % 2 else -1)
+        sc["means"][0, j] = 0.1 * sc["means"][2, j]
+        sc["log_scales"][:, j] = -1.4
+    for j in range(8, 14):         # saturating opacity, centred on a pixel: o G = 0.9975 > 0.99 there
+        px, py = 6 + 4 * (j - 8), 10 + (j % 3) * 5
+        sc["means"][0, j] = (px - (W - 1) / 2) * sc["means"][2, j] / f
+        sc["means"][1, j] = (py - (H - 1) / 2) * sc["means"][2, j] / f
+        sc["logits"][j] = 6.0
+    cams = [syn.pinhole(W, H, f)]
+    wC = [rng.standard_normal((3, H, W))]
+    wD = [rng.standard_normal((H, W))]
+    wA = [rng.standard_normal((H, W))]
+    L0, st = _linear_objective(sc, cams, wC, wD, wA)
+    g = orr.grads_to_planes(orr.backward_views(st, cams, wC, wD, wA))
+    # the branches are taken: clamped Gaussians blend, saturated pairs exist
+    assert np.abs(g["rgb"][:, :8]).sum(0).min() > 0
+    out = st["out"][0]
+    assert (out["t_final"] < 0.02).any()
+    checked = skipped = 0
+    for key in ["means", "log_scales", "quats", "logits"]:
+        arr = sc[key]
+        for j in range(14):
+            idx = [(r, j) for r in range(arr.shape[0])] if arr.ndim == 2 else [(j,)]
+            for ix in idx:
+                fds = []
+                for h in (1e-6, 5e-7):
+                    old = arr[ix]
+                    arr[ix] = old + h
+                    Lp, _ = _linear_objective(sc, cams, wC, wD, wA)
+                    arr[ix] = old - h
+                    Lm, _ = _linear_objective(sc, cams, wC, wD, wA)
+                    arr[ix] = old
+                    fds.append((Lp - Lm) / (2 * h))
+                gv = g[key][ix]
+                scale = max(abs(gv), 1e-3)
+                if abs(fds[0] - fds[1]) > 1e-5 * scale + 1e-8:
+                    skipped += 1
+                    continue
+                checked += 1
+                assert abs(fds[0] - gv) <= 2e-5 * scale + 1e-8, (key, ix, fds[0], gv)
+    assert checked >= 0.9 * (checked + skipped), (checked, skipped)
 
 
 def test_blending_invariants():
