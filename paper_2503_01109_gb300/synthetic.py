@@ -51,6 +51,66 @@ def tiny_scene(n: int = 2000, seed: int = 0) -> dict:
                  rng.uniform(0, 1, (3, n)))
 
 
+EDGE_KINDS = ("clamp", "saturate", "near", "needle", "opaque")
+
+
+def edge_scene(kind: str, n: int = 1500, seed: int = 0) -> dict:
+    """Scenes for a 64x48 (or 70x45) camera with f = 60 at the identity pose that
+    exercise the rare branches of projection and blending, each mixed with a
+    tiny-scene background (means in [-1,1]^2 x [2,4]):
+
+    * "clamp":    a third of the Gaussians beyond the Jacobian clamp in x
+                  (|x/z| in [0.8, 1.1]), a third beyond it in y (|y/z| in
+                  [0.58, 0.85]), large enough (log-scales N(-1, 0.3)) that their
+                  footprints reach into the image;
+    * "saturate": opacity logits N(5.5, 1), so o * G exceeds the 0.99 alpha clamp
+                  near the centres;
+    * "near":     half the means at depths in [0.1, 0.45] around the 0.2 near
+                  plane (none within 1e-3 of it), small log-scales N(-5, 0.5);
+    * "needle":   half the Gaussians needle-like (log-scales -1.5, -6.5, -6.5 in a
+                  random axis order, random rotation): nearly degenerate 2D
+                  covariances before the dilation;
+    * "opaque":   a quarter large opaque Gaussians (log-scales N(-1.6, 0.2),
+                  logits N(4, 0.5)), so that many pixels stop early (T < 1e-4)."""
+    rng = np.random.default_rng(seed)
+    base = tiny_scene(n, seed + 1000)
+    means, ls, q = base["means"].astype(np.float64), base["log_scales"].astype(np.float64), base["quats"]
+    logits, rgb = base["logits"].astype(np.float64), base["rgb"]
+    if kind == "clamp":
+        k = n // 3
+        z = rng.uniform(2.0, 4.0, 2 * k)
+        side = rng.choice([-1.0, 1.0], (2, 2 * k))
+        u = rng.uniform(-0.5, 0.5, 2 * k)
+        v = rng.uniform(-0.35, 0.35, 2 * k)
+        u[:k] = side[0, :k] * rng.uniform(0.8, 1.1, k)           # beyond the x clamp
+        v[k:] = side[1, k:] * rng.uniform(0.58, 0.85, k)         # beyond the y clamp
+        both = rng.uniform(0, 1, 2 * k) < 0.2                    # some beyond both
+        v[:k][both[:k]] = side[1, :k][both[:k]] * rng.uniform(0.58, 0.85, both[:k].sum())
+        means[:, :2 * k] = np.stack([u * z, v * z, z])
+        ls[:, :2 * k] = rng.normal(-1.0, 0.3, (3, 2 * k))
+    elif kind == "saturate":
+        logits = rng.normal(5.5, 1.0, n)
+        ls = rng.normal(-2.6, 0.3, (3, n))
+    elif kind == "near":
+        k = n // 2
+        z = rng.uniform(0.1, 0.45, k)
+        z = np.where(np.abs(z - 0.2) < 1e-3, z + 2e-3, z)
+        means[:, :k] = np.stack([rng.uniform(-0.4, 0.4, k) * z, rng.uniform(-0.3, 0.3, k) * z, z])
+        ls[:, :k] = rng.normal(-5.0, 0.5, (3, k))
+    elif kind == "needle":
+        k = n // 2
+        axis = rng.integers(0, 3, k)
+        ls[:, :k] = -6.5
+        ls[axis, np.arange(k)] = -1.5
+    elif kind == "opaque":
+        k = n // 4
+        ls[:, :k] = rng.normal(-1.6, 0.2, (3, k))
+        logits[:k] = rng.normal(4.0, 0.5, k)
+    else:
+        raise ValueError(kind)
+    return _pack(means, ls, q, logits, rgb)
+
+
 def _pack(means, log_scales, quats, logits, rgb) -> dict:
     return {"means": np.ascontiguousarray(means, np.float32),
             "log_scales": np.ascontiguousarray(log_scales, np.float32),

@@ -51,3 +51,49 @@ def tile_origin(cams, tw, th):
         out.append(base)
         base += tx * ty
     return out
+
+
+GRAD_KEYS = ("means", "log_scales", "quats", "logits", "rgb")
+
+
+def oracle_flags(m: Mapper, cams, n: int, rgb_aos: np.ndarray, tw: int, th: int):
+    """Per-view decision-band flags [H][W] (bool) of the teacher-forced forward:
+    the oracle's FP64 blend of the GPU's float32 splats over the GPU's lists marks
+    every pixel where a float32 evaluation could take the other branch of a
+    threshold decision (alpha vs 1/255 or 0.99, T vs 1e-4, power vs 0)."""
+    _, ids, ranges = gpu_lists(m)
+    bases = tile_origin(cams, tw, th)
+    out = []
+    for v, cam in enumerate(cams):
+        gsp, _ = gpu_view_splats(m, v, n)
+        out.append(orr.render_fwd(gsp, rgb_aos, cam, ids, ranges, bases[v], tw, th)["flag"] != 0)
+    return out
+
+
+def masked(images, flags):
+    """Per-view image arrays ([3][H][W] or [H][W]) with the flagged pixels set to
+    zero: an upstream gradient masked this way on both sides removes the flagged
+    pixels' terms from every parameter gradient."""
+    out = []
+    for img, f in zip(images, flags):
+        a = np.array(img, np.float32, copy=True)
+        a[..., f] = 0.0
+        out.append(a)
+    return out
+
+
+def to_device(images):
+    return torch.cat([torch.as_tensor(np.ascontiguousarray(x)).reshape(-1) for x in images]).cuda()
+
+
+def assert_grads_exact(grads_gpu: fgs.GaussianMap, ref: dict, n: int, rel: float = GRAD_REL, keys=GRAD_KEYS):
+    """Every entry of every gradient plane within |g - g*| <= rel max(|g*|, 1e-3 max|g*|)."""
+    for key in keys:
+        got = grads_gpu.plane(key)[:, :n].cpu().numpy().reshape(ref[key].shape)
+        bad, r = grad_close(got, ref[key], rel)
+        assert not bad.any(), (key, int(bad.sum()), float(r.max()))
+
+
+def flag_fraction(flags) -> float:
+    tot = sum(f.size for f in flags)
+    return sum(int(f.sum()) for f in flags) / max(tot, 1)

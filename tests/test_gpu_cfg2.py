@@ -3,19 +3,22 @@ room, a 200k-Gaussian map, targets rendered from a 300k-Gaussian ground-truth
 scene, 100 mapping iterations (eq16 + eq15, Adam).  At iterations 0, 50 and 99
 the GPU's step is checked against one oracle step from the same state, teacher-
 forced on the GPU's float32 splats, tile lists and image gradient: the render
-within 1e-4, the loss value and its image gradient, all 14 parameter gradients
-within the 1e-3 relative bound, and the Adam update of those gradients within
-1e-5.  Over the run the loss falls; no end-state parity is asked of 100 chaotic
+within 1e-4, the loss value and its image gradient, every entry of the 14
+parameter gradients within the 1e-3 relative bound (decision-band pixels zeroed
+in the image gradient on both sides), and the Adam update of the GPU's gradients
+within 1e-5.  Over the run the loss falls; no end-state parity is asked of 100 chaotic
 steps."""
 import numpy as np
 import pytest
+import torch
 
 from oracle import render as orr
 from paper_2503_01109_gb300 import fgs, synthetic as syn
 from paper_2503_01109_gb300.frames import render_targets
 from paper_2503_01109_gb300.mapping import PAPER_LOSS, PAPER_REG
 
-from gpu_helpers import PIX_TOL, grad_close, gpu_lists, gpu_view_splats, make_mapper
+from gpu_helpers import (PIX_TOL, assert_grads_exact, gpu_lists, gpu_view_splats, make_mapper, masked,
+                         to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -54,18 +57,24 @@ def _check_step(m, pre, cam, color_gt, depth_gt):
     gdD = m.dD.cpu().numpy().reshape(H, W)
     assert np.abs(gdC - rdC).max() <= 1e-4 * np.abs(rdC).max()
     assert np.abs(gdD - rdD).max() <= 1e-6 * np.abs(rdD).max()
-    # adjoint of the blend and the projection from the GPU's image gradient, plus eq15
-    g2, grgb = orr.render_bwd(gsp, sa["rgb"], cam, ids, ranges, gdC.astype(np.float64), gdD.astype(np.float64),
-                              None)
+    # adjoint of the blend and the projection from the GPU's image gradient with the
+    # decision-band pixels zeroed on both sides, through the C ABI on the pre-step
+    # parameters and this step's splats and lists; eq15 on the pre-step log-scales
+    (mdC,), (mdD,) = masked([gdC], [~ok]), masked([gdD], [~ok])
+    g_pre = fgs.GaussianMap.from_scene(_scene_of(pre["p"], n), capacity=m.g.capacity)
+    grads_tf = g_pre.zeros_like()
+    grad2d = torch.zeros_like(m.grad2d)
+    fgs.fgs_render_bwd(g_pre, m.proj, [cam], m.til, m.ids, m.ranges, m.frame, to_device([mdC]), to_device([mdD]),
+                       None, grad2d, grads_tf)
+    acc = torch.zeros(1, device="cuda")
+    fgs.fgs_scale_reg(g_pre, PAPER_REG, grads_tf, acc, fgs.ws_tensor(fgs.fgs_scale_reg_workspace_size(g_pre.capacity)))
+    torch.cuda.synchronize()
+    g2, grgb = orr.render_bwd(gsp, sa["rgb"], cam, ids, ranges, mdC.astype(np.float64), mdD.astype(np.float64), None)
     grads = {"means": np.zeros((n, 3)), "log_scales": np.zeros((n, 3)), "quats": np.zeros((n, 4)),
              "logits": np.zeros(n), "rgb": grgb}
     orr.project_bwd(sa, cam, g2, grads)
     grads["log_scales"] += greg
-    ref_g = orr.grads_to_planes(grads)
-    for key in ("means", "log_scales", "quats", "logits", "rgb"):
-        got = m.grads.plane(key)[:, :n].cpu().numpy().reshape(ref_g[key].shape)
-        bad, _ = grad_close(got, ref_g[key])
-        assert bad.mean() < 0.003, (key, int(bad.sum()))
+    assert_grads_exact(grads_tf, orr.grads_to_planes(grads), n)
     # the Adam step of the GPU's gradients from the pre-step state
     P = np.asarray(pre["p"][:, :n], np.float64).copy()
     M = np.asarray(pre["m"][:, :n], np.float64).copy()

@@ -10,7 +10,7 @@ import torch
 from oracle import render as orr
 from paper_2503_01109_gb300 import fgs, synthetic as syn
 
-from gpu_helpers import PIX_TOL, grad_close, gpu_lists, gpu_view_splats, make_mapper
+from gpu_helpers import PIX_TOL, assert_grads_exact, gpu_lists, gpu_view_splats, make_mapper, masked, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -45,22 +45,18 @@ def test_full_size_render_and_gradients(cuda_device, full):
     ref = orr.render_fwd(gsp, sa["rgb"], cam, ids, ranges)
     out = m.frame.view(0)
     ok = ref["flag"] == 0
-    assert ok.mean() > 0.99
+    assert ok.mean() > 0.99         # hundreds of splats per pixel: about 1% of pixels hold a band decision
     assert np.abs(out["color"].cpu().numpy() - ref["color"])[:, ok].max() <= PIX_TOL
     assert np.abs(out["depth"].cpu().numpy() - ref["depth"])[ok].max() <= PIX_TOL * 10  # depth ~ 2 m: 5e-5 relative
     assert np.abs(out["alpha"].cpu().numpy() - ref["alpha"])[ok].max() <= PIX_TOL
     assert np.array_equal(out["n_contrib"].cpu().numpy()[ok], ref["n_contrib"][ok])
+    # upstream gradients with the decision-band pixels zeroed on both sides
     rg = syn.random_image_grads([cam], 7)
-    dC = torch.as_tensor(rg["dC"][0]).reshape(-1).cuda()
-    dD = torch.as_tensor(rg["dD"][0]).reshape(-1).cuda()
-    m.backward(dC, dD, None)
+    (dC,), (dD,) = masked(rg["dC"], [~ok]), masked(rg["dD"], [~ok])
+    m.backward(to_device([dC]), to_device([dD]), None)
     torch.cuda.synchronize()
-    g2, grgb = orr.render_bwd(gsp, sa["rgb"], cam, ids, ranges, rg["dC"][0], rg["dD"][0], None)
+    g2, grgb = orr.render_bwd(gsp, sa["rgb"], cam, ids, ranges, dC, dD, None)
     grads = {"means": np.zeros((n, 3)), "log_scales": np.zeros((n, 3)), "quats": np.zeros((n, 4)),
              "logits": np.zeros(n), "rgb": grgb}
     orr.project_bwd(sa, cam, g2, grads)
-    ref_g = orr.grads_to_planes(grads)
-    for key in ("means", "log_scales", "quats", "logits", "rgb"):
-        got = m.grads.plane(key)[:, :n].cpu().numpy().reshape(ref_g[key].shape)
-        bad, _ = grad_close(got, ref_g[key])
-        assert bad.mean() < 0.003, (key, int(bad.sum()))
+    assert_grads_exact(m.grads, orr.grads_to_planes(grads), n)

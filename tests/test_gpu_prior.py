@@ -73,8 +73,8 @@ def test_training_gradients_match_oracle(cuda_device):
         off += size
         ref = g[k]
         floor = 1e-3 * np.abs(ref).max()
-        bad = np.abs(got - ref) > 2e-2 * np.maximum(np.abs(ref), floor)
-        assert bad.mean() < 0.01, (k, bad.sum())
+        r = np.abs(got - ref) / np.maximum(np.abs(ref), floor)
+        assert r.max() <= 1e-3, (k, float(r.max()), int((r > 1e-3).sum()), float(np.quantile(r, 0.99)))
 
 
 def test_training_reduces_the_loss(cuda_device):
@@ -90,3 +90,62 @@ def test_training_reduces_the_loss(cuda_device):
         last = mlp.train_step(f, tt, lr=3e-3)
     torch.cuda.synchronize()
     assert float(last.item()) < 0.2 * first
+
+
+def test_prior_seeding_matches_oracle(cuda_device):
+    """fgs_fourier_seed with a learned prior: the same seeds as without it (seed
+    list, masks and means bit-exact), and -- teacher-forced on the GPU's
+    predictions at those seeds -- every high-frequency seed's log-scales and logit
+    exactly as the oracle's rule sets them (predicted logit; predicted log-scales
+    unless one lies further than max_dev from eq11's, then eq11's), low-frequency
+    seeds untouched.  max_dev is the median deviation, so both branches occur.
+    The GPU's predictions themselves match the oracle MLP on the same features."""
+    W, H = 200, 120
+    fr = syn.textured_frame(W, H, 7)
+    rr = syn.fake_render(W, H, 8)
+    cam = syn.pinhole(W, H, 180.0)
+    rgb = torch.as_tensor(fr["rgb"]).reshape(-1).cuda()
+    depth = torch.as_tensor(fr["depth"]).reshape(-1).cuda()
+    rc, rd, ra = (torch.as_tensor(rr[k]).reshape(-1).cuda() for k in ("color", "depth", "alpha"))
+    params = gp.init_params(6)
+    mlp = gp.PriorMLP(params)
+    max_new = 5000
+
+    def seed(prior, max_dev):
+        g = fgs.GaussianMap(max_new + 10, "cuda", 0)
+        prm = fgs.seed_params(max_new=max_new, prior_max_dev=max_dev)
+        ws = fgs.ws_tensor(fgs.fgs_fourier_seed_workspace_size(W, H, max_new))
+        mask = torch.zeros(H * W, dtype=torch.uint8, device="cuda")
+        num_new = torch.zeros(1, dtype=torch.int32, device="cuda")
+        thr = torch.zeros(1, dtype=torch.int32, device="cuda")
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        xy = torch.zeros(max_new, 2, dtype=torch.int32, device="cuda")
+        fgs.fgs_fourier_seed(rgb, depth, rc, rd, ra, cam, prm, prior, mask, None, g, num_new, thr, ws, status,
+                             seed_xy=xy)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        k = int(num_new.item())
+        return g.to_scene(k), mask.cpu().numpy().reshape(H, W), k, xy[:k]
+
+    g0, mask0, k, xy = seed(None, 1.0)
+    assert k > 500
+    xy_h = xy.cpu().numpy()
+    hi = (mask0[xy_h[:, 1], xy_h[:, 0]] & 1).astype(bool)
+    assert 0 < hi.sum() < k
+    feats = gp.features(rgb, depth, W, H, xy)
+    pred = mlp.infer(feats).cpu().numpy()
+    ls11, lg11 = g0["log_scales"], g0["logits"]
+    dev = np.abs(pred[:, :3].astype(np.float32) - ls11.T.astype(np.float32)).max(axis=1)
+    max_dev = float(np.float32(np.median(dev[hi])))
+    g1, mask1, k1, xy1 = seed(mlp.mlp_struct(), max_dev)
+    assert k1 == k and torch.equal(xy1, xy) and np.array_equal(mask1, mask0)
+    for key in ("means", "quats", "rgb"):
+        assert np.array_equal(g1[key], g0[key]), key
+    ls_ref, lg_ref = op.apply_to_seeds(pred, ls11, lg11, hi, max_dev)
+    assert np.array_equal(g1["log_scales"], ls_ref)
+    assert np.array_equal(g1["logits"], lg_ref)
+    accepted = hi & np.all(np.abs(pred[:, :3] - ls11.T) <= np.float32(max_dev), axis=1)
+    assert 0 < accepted.sum() < hi.sum()
+    x = op.from_bits(feats.cpu().numpy().view(np.uint16)).astype(np.float64)
+    ref_y = op.forward(params, x)["y"]
+    assert np.abs(pred - ref_y).max() <= 2e-3 * (1 + np.abs(ref_y).max())

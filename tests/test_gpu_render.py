@@ -8,7 +8,8 @@ from oracle import render as orr
 from paper_2503_01109_gb300 import fgs, synthetic as syn
 from paper_2503_01109_gb300.mapping import Mapper, render as diff_render
 
-from gpu_helpers import PIX_TOL, grad_close, gpu_lists, gpu_view_splats, make_mapper, tile_origin
+from gpu_helpers import (PIX_TOL, assert_grads_exact, flag_fraction, grad_close, gpu_lists, gpu_view_splats,
+                         make_mapper, masked, oracle_flags, tile_origin, to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -118,45 +119,48 @@ def test_render_end_to_end_from_fp64(cuda_device, W, H, tw, th, bd, n, views):
         err = np.abs(out["color"].cpu().numpy() - ref["color"]).max(axis=0)
         err = np.maximum(err, np.abs(out["depth"].cpu().numpy() - ref["depth"]))
         ok = ref["flag"] == 0
-        assert (err[ok] <= PIX_TOL).mean() >= 0.999
+        assert ok.mean() >= 0.998
+        assert err[ok].max() <= PIX_TOL
         assert np.median(err) < 1e-5
 
 
 def _bwd_case(sc, cams, tw, th, bd, seed):
+    """Adjoint of the blend and the projection on both sides from the same seeded
+    upstream gradients, teacher-forced on the GPU's splats and lists, with the
+    upstream gradient of every pixel in the oracle's decision band set to zero on
+    both sides (those pixels may take the other branch of a threshold in float32,
+    so their terms are the only ones allowed to differ)."""
     n = sc["means"].shape[1]
     m = make_mapper(sc, cams, (tw, th), bd)
     m.render()
+    torch.cuda.synchronize()
+    sa = orr.aos(sc)
+    flags = oracle_flags(m, cams, n, sa["rgb"], tw, th)
     rg = syn.random_image_grads(cams, seed)
-    dC = torch.cat([torch.as_tensor(x).reshape(-1) for x in rg["dC"]]).cuda()
-    dD = torch.cat([torch.as_tensor(x).reshape(-1) for x in rg["dD"]]).cuda()
-    dA = torch.cat([torch.as_tensor(x).reshape(-1) for x in rg["dA"]]).cuda()
-    m.backward(dC, dD, dA)
+    dCs, dDs, dAs = (masked(rg[k], flags) for k in ("dC", "dD", "dA"))
+    m.backward(to_device(dCs), to_device(dDs), to_device(dAs))
     torch.cuda.synchronize()
     _, ids, ranges = gpu_lists(m)
-    sa = orr.aos(sc)
     bases = tile_origin(cams, tw, th)
     grads = {"means": np.zeros((n, 3)), "log_scales": np.zeros((n, 3)), "quats": np.zeros((n, 4)),
              "logits": np.zeros(n), "rgb": np.zeros((n, 3))}
     for v, cam in enumerate(cams):
         gsp, _ = gpu_view_splats(m, v, n)
-        g2, grgb = orr.render_bwd(gsp, sa["rgb"], cam, ids, ranges, rg["dC"][v], rg["dD"][v], rg["dA"][v], bases[v],
-                                  tw, th)
+        g2, grgb = orr.render_bwd(gsp, sa["rgb"], cam, ids, ranges, dCs[v], dDs[v], dAs[v], bases[v], tw, th)
         grads["rgb"] += grgb
         orr.project_bwd(sa, cam, g2, grads)
-    return m, orr.grads_to_planes(grads)
+    return m, orr.grads_to_planes(grads), flags
 
 
 @pytest.mark.parametrize("W,H,tw,th,bd,n,views", CASES)
 def test_render_backward_matches_oracle(cuda_device, W, H, tw, th, bd, n, views):
-    """All 14 parameter gradients within 1e-3 relative (floor 1e-3 of the largest)."""
+    """All 14 parameter gradients, every entry, within 1e-3 relative (floor 1e-3 of
+    the largest); decision-band pixels (at most 0.2%) masked on both sides."""
     sc = syn.tiny_scene(n, seed=W + H + 3)
     cams = cams_for(W, H, views)
-    m, ref = _bwd_case(sc, cams, tw, th, bd, seed=17)
-    for key in ("means", "log_scales", "quats", "logits", "rgb"):
-        got = m.grads.plane(key)[:, :n].cpu().numpy().reshape(ref[key].shape)
-        bad, rel = grad_close(got, ref[key])
-        # decision flips at the float32 band move a handful of pixels' terms
-        assert bad.mean() < 0.003, (key, bad.sum(), rel.max())
+    m, ref, flags = _bwd_case(sc, cams, tw, th, bd, seed=17)
+    assert flag_fraction(flags) <= 0.002
+    assert_grads_exact(m.grads, ref, n)
 
 
 def test_autograd_function_uses_the_adjoint(cuda_device):
@@ -239,14 +243,25 @@ def test_scale_reg_and_adam_match_oracle(cuda_device):
     assert np.abs(g.buf[:, :3000].cpu().numpy() - P).max() < 1e-5
 
 
+def l1_sign_band(color, depth, color_gt, depth_gt, tol_c=1e-5, tol_d=1e-4):
+    """Pixels where an L1 term's sign could differ between float32 and FP64
+    (|C - C*| or |D - D*| within float32 reach of 0, but not both exactly 0 as on
+    pixels no Gaussian reaches in either render): the other decision of the loss."""
+    band = ((np.abs(color - color_gt) <= tol_c) & ~((color == 0) & (color_gt == 0))).any(axis=0)
+    return band | ((np.abs(depth - depth_gt) <= tol_d) & (depth_gt > 0))
+
+
 def test_mapping_iteration_tiny_config(cuda_device):
-    """The tiny configuration end to end: L1 colour + L1 depth against a second
-    seeded scene's render, one iteration; loss and every gradient vs the oracle."""
+    """The tiny configuration end to end from FP64: L1 colour + L1 depth against a
+    second seeded scene's render, one iteration.  Loss value within 1e-4; the
+    iteration's image gradient equals the oracle's outside the decision bands of
+    the blend and of the L1 signs; the adjoint of that image gradient (bands zeroed
+    on both sides) matches the oracle's in every entry."""
     cam = syn.pinhole(64, 48, 60.0)
     sc = syn.tiny_scene(2000, 0)
     tgt = syn.tiny_scene(2000, 1)
     st_t = orr.render_views(tgt, [cam])
-    Cg, Dg = st_t["out"][0]["color"], st_t["out"][0]["depth"]
+    Cg, Dg = st_t["out"][0]["color"].astype(np.float32), st_t["out"][0]["depth"].astype(np.float32)
     # the separate end of the iteration keeps the gradients for inspection (the
     # fused one consumes them; its parity with this path is tested on its own)
     m = make_mapper(sc, [cam], loss_w=(1.0, 1.0, 0.0), reg_w=0.0, fused_tail=False)
@@ -256,13 +271,22 @@ def test_mapping_iteration_tiny_config(cuda_device):
     torch.cuda.synchronize()
     st = orr.render_views(sc, [cam])
     out = st["out"][0]
-    L, dC, dD = orr.loss(out["color"], out["depth"], Cg.astype(np.float32), Dg.astype(np.float32), 1.0, 1.0, 0.0)
+    L, dC, dD = orr.loss(out["color"], out["depth"], Cg, Dg, 1.0, 1.0, 0.0)
     assert float(m.loss_acc.item()) == pytest.approx(L, rel=1e-4)
-    grads = orr.grads_to_planes(orr.backward_views(st, [cam], [dC], [dD]))
-    for key in ("means", "log_scales", "quats", "logits", "rgb"):
-        got = m.grads.plane(key)[:, :2000].cpu().numpy().reshape(grads[key].shape)
-        bad, _ = grad_close(got, grads[key])
-        assert bad.mean() < 0.01, key
+    band = (out["flag"] != 0) | l1_sign_band(out["color"], out["depth"], Cg, Dg)
+    assert band.mean() <= 0.002
+    gdC = m.dC.cpu().numpy().reshape(3, 48, 64)
+    gdD = m.dD.cpu().numpy().reshape(48, 64)
+    assert np.allclose(gdC[:, ~band], dC[:, ~band], rtol=1e-6, atol=0)
+    assert np.allclose(gdD[~band], dD[~band], rtol=1e-6, atol=0)
+    (mdC,), (mdD,) = masked([gdC], [band]), masked([gdD], [band])
+    m2 = make_mapper(sc, [cam])
+    m2.render()
+    m2.backward(to_device([mdC]), to_device([mdD]))
+    torch.cuda.synchronize()
+    (rdC,), (rdD,) = masked([dC], [band]), masked([dD], [band])
+    ref = orr.grads_to_planes(orr.backward_views(st, [cam], [rdC.astype(np.float64)], [rdD.astype(np.float64)]))
+    assert_grads_exact(m2.grads, ref, 2000)
 
 
 def test_graph_replay_equals_eager(cuda_device):

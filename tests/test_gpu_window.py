@@ -10,7 +10,8 @@ from paper_2503_01109_gb300 import fgs, synthetic as syn
 from paper_2503_01109_gb300.mapping import Mapper
 from paper_2503_01109_gb300.window import Window, autotune
 
-from gpu_helpers import grad_close
+from gpu_helpers import (assert_grads_exact, flag_fraction, gpu_lists, gpu_view_splats, grad_close, make_mapper,
+                         masked, oracle_flags, tile_origin, to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -62,30 +63,70 @@ def test_window_equals_separate_calls(cuda_device, tile, batch):
 
 
 def test_window_gradients_match_oracle(cuda_device):
-    """End to end against the FP64 oracle on the mixed-resolution window (eq16
-    with SSIM; gradients through the whole chain)."""
+    """The window iteration against the FP64 oracle on the mixed-resolution window
+    (eq16 with SSIM): the persistent launch's images and image gradients, and its
+    parameter gradients through the whole chain.  Checked as a chain of exact
+    links: (1) the window's images equal the oracle's outside the decision band and
+    its loss and image gradient match the oracle's loss of those images; (2) the
+    window's parameter gradients equal the separate adjoint calls' on its own image
+    gradient; (3) those calls, with the decision-band pixels of the image gradient
+    zeroed on both sides, match the oracle's adjoint in every entry."""
     cams = views()
-    sc = syn.tiny_scene(2000, seed=11)
+    n = 2000
+    sc = syn.tiny_scene(n, seed=11)
     frs = [syn.textured_frame(c["width"], c["height"], 20 + i) for i, c in enumerate(cams)]
     cg, dg = fgs.pack_images(cams, [f["rgb"] for f in frs], [f["depth"] for f in frs])
-    win = Window(fgs.GaussianMap.from_scene(sc), cams, fgs.tiling(16, 16, 128), reg_w=0.0, fused_tail=False)
+    til = fgs.tiling(16, 16, 128)
+    win = Window(fgs.GaussianMap.from_scene(sc), cams, til, reg_w=0.0, fused_tail=False)
     win.set_target(cg, dg)
     win.iteration()
     torch.cuda.synchronize()
     st = orr.render_views(sc, cams)
-    dCs, dDs, L = [], [], 0.0
+    sizes = fgs.image_sizes(cams)
+    L, o = 0.0, 0
+    gdCs, gdDs = [], []
     for v, f in enumerate(frs):
-        o = st["out"][v]
-        l, dC, dD = orr.loss(o["color"], o["depth"], f["rgb"], f["depth"], 0.9, 0.1, 0.1)
+        H, W = cams[v]["height"], cams[v]["width"]
+        ref = st["out"][v]
+        got = win.frame.view(v)
+        ok = ref["flag"] == 0
+        assert np.abs(got["color"].cpu().numpy() - ref["color"])[:, ok].max() <= 1e-4
+        assert np.abs(got["depth"].cpu().numpy() - ref["depth"])[ok].max() <= 1e-4
+        # eq16 of the window's own images (the loss is a smooth function of them)
+        l, rdC, rdD = orr.loss(got["color"].cpu().numpy(), got["depth"].cpu().numpy(), f["rgb"], f["depth"],
+                               0.9, 0.1, 0.1)
         L += l
-        dCs.append(dC)
-        dDs.append(dD)
-    assert float(win.loss_acc.item()) == pytest.approx(L, rel=1e-4)
-    ref = orr.grads_to_planes(orr.backward_views(st, cams, dCs, dDs))
-    for key in ("means", "log_scales", "quats", "logits", "rgb"):
-        got = win.grads.plane(key)[:, :2000].cpu().numpy().reshape(ref[key].shape)
-        bad, _ = grad_close(got, ref[key])
-        assert bad.mean() < 0.01, key
+        gdC = win.dC[3 * o:3 * (o + H * W)].cpu().numpy().reshape(3, H, W)
+        gdD = win.dD[o:o + H * W].cpu().numpy().reshape(H, W)
+        assert np.abs(gdC - rdC).max() <= 1e-4 * np.abs(rdC).max()
+        assert np.abs(gdD - rdD).max() <= 1e-6 * np.abs(rdD).max()
+        gdCs.append(gdC)
+        gdDs.append(gdD)
+        o += sizes[v]
+    assert float(win.loss_acc.item()) == pytest.approx(L, rel=1e-5)
+    # (2) the separate adjoint calls on the same image gradient
+    sep = make_mapper(sc, cams, (16, 16), 128)
+    sep.render()
+    sep.backward(win.dC, win.dD)
+    torch.cuda.synchronize()
+    bad, _ = grad_close(win.grads.buf[:, :n].cpu().numpy(), sep.grads.buf[:, :n].cpu().numpy(), rel=1e-4)
+    assert not bad.any()
+    # (3) the separate calls against the oracle, decision-band pixels zeroed
+    flags = oracle_flags(sep, cams, n, orr.aos(sc)["rgb"], 16, 16)
+    assert flag_fraction(flags) <= 0.002
+    mdC, mdD = masked(gdCs, flags), masked(gdDs, flags)
+    sep.backward(to_device(mdC), to_device(mdD))
+    torch.cuda.synchronize()
+    _, ids, ranges = gpu_lists(sep)
+    sa = orr.aos(sc)
+    grads = {"means": np.zeros((n, 3)), "log_scales": np.zeros((n, 3)), "quats": np.zeros((n, 4)),
+             "logits": np.zeros(n), "rgb": np.zeros((n, 3))}
+    for v, (cam, base) in enumerate(zip(cams, tile_origin(cams, 16, 16))):
+        gsp, _ = gpu_view_splats(sep, v, n)
+        g2, grgb = orr.render_bwd(gsp, sa["rgb"], cam, ids, ranges, mdC[v], mdD[v], None, base, 16, 16)
+        grads["rgb"] += grgb
+        orr.project_bwd(sa, cam, g2, grads)
+    assert_grads_exact(sep.grads, orr.grads_to_planes(grads), n)
 
 
 def test_window_graph_replay_and_autotune(cuda_device):
