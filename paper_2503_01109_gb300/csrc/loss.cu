@@ -32,9 +32,11 @@ __global__ void k_reduce_partials(const double *__restrict__ partials, int64_t c
   if (threadIdx.x == 0) *d_loss += (float)red[0];
 }
 
-static bool loss_views(const fgs_camera *cams, int32_t n_views, LossViews *lv, int *blocks) {
+// `who` names the entry point in the error message.
+static bool loss_views(const fgs_camera *cams, int32_t n_views, LossViews *lv, int *blocks,
+                       const char *who = "fgs_loss") {
   if (!cams || n_views < 1 || n_views > FGS_MAX_VIEWS) {
-    set_error("fgs_loss: n_views must be 1..%d", FGS_MAX_VIEWS);
+    set_error("%s: n_views must be 1..%d", who, FGS_MAX_VIEWS);
     return false;
   }
   lv->n = n_views;
@@ -42,7 +44,7 @@ static bool loss_views(const fgs_camera *cams, int32_t n_views, LossViews *lv, i
   int64_t pix = 0;
   for (int v = 0; v < n_views; ++v) {
     if (cams[v].width <= 0 || cams[v].height <= 0) {
-      set_error("fgs_loss: bad image size");
+      set_error("%s: bad image size", who);
       return false;
     }
     lv->v[v].W = cams[v].width;
@@ -294,7 +296,8 @@ extern "C" fgs_status fgs_adam(fgs_gaussians *params, const fgs_gaussians *grads
 // file-scope device array instead of caller workspace, for callers that may not
 // allocate device memory.  Host code must not pass the array's name to a kernel:
 // on the host that name is only a stand-in, so the device address is looked up
-// with cudaGetSymbolAddress once per device and cached.
+// with cudaGetSymbolAddress once per device and cached (a cudaDeviceReset
+// unloads the module, so the cached address is stale after one).
 namespace fgs {
 
 static __device__ __align__(256) double g_loss_scratch[FGS_LOSS_NOALLOC_MAX_TILES];
@@ -333,7 +336,7 @@ extern "C" fgs_status fgs_loss_noalloc(const fgs_camera *cams, int32_t n_views, 
                 "fgs_loss_noalloc: NULL argument");
   LossArgs a;
   int blocks = 0;
-  if (!loss_views(cams, n_views, &a.lv, &blocks)) return FGS_ERR_INVALID_ARGUMENT;
+  if (!loss_views(cams, n_views, &a.lv, &blocks, "fgs_loss_noalloc")) return FGS_ERR_INVALID_ARGUMENT;
   if (blocks > FGS_LOSS_NOALLOC_MAX_TILES) {
     set_error("fgs_loss_noalloc: %d loss tiles (16x16 px) exceed the built-in scratch of %d tiles; "
               "use fgs_loss with a workspace",
