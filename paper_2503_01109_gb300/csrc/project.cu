@@ -9,7 +9,7 @@
 namespace fgs {
 
 struct GaussLocal {
-  float mu[3], s[3], qn[4], qinv, R[9], Sigma[6], o;  // Sigma: xx, xy, xz, yy, yz, zz
+  float mu[3], s[3], qn[4], qinv, R[9], o;
 };
 
 __device__ __forceinline__ void load_gaussian(const GaussPtrs &g, int64_t i, GaussLocal &L) {
@@ -27,29 +27,34 @@ __device__ __forceinline__ void load_gaussian(const GaussPtrs &g, int64_t i, Gau
   L.R[6] = 2.f * (x * z - w * y); L.R[7] = 2.f * (y * z + w * x); L.R[8] = 1.f - 2.f * (x * x + y * y);
 #pragma unroll
   for (int k = 0; k < 3; ++k) L.s[k] = expf(g.log_scales[k * c + i]);
-  float M[9];
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) M[3 * r + k] = L.R[3 * r + k] * L.s[k];
-  L.Sigma[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
-  L.Sigma[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
-  L.Sigma[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
-  L.Sigma[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
-  L.Sigma[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
-  L.Sigma[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
   L.o = 1.0f / (1.0f + expf(-g.logits[i]));
+}
+
+// a d - b c with one rounding error of each product compensated (the FMA recovers
+// the exact error of b c), so that a small difference of two large products keeps
+// its relative accuracy.
+__device__ __forceinline__ float diff_of_products(float a, float d, float b, float c) {
+  const float bc = b * c;
+  const float err = fmaf(-b, c, bc);
+  return fmaf(a, d, -bc) + err;
 }
 
 struct ViewLocal {
   float p[3];
   float uc, vc;
   bool clamp_u, clamp_v;
-  float T[6];  // J R_cam, 2x3
+  float T[6];   // J R_cam, 2x3
+  float TR[6];  // J R_cam R, 2x3: the Gaussian's axes in the image plane (per unit scale)
+  float N[6];   // TR diag(s): Sigma' = N N^T + 0.3 I
   float a, b, c, det;
 };
 
 // Returns false when culled (behind the near plane or degenerate covariance).
+// The 2D covariance is formed as N N^T (N = J R_cam R diag(s), 2x3) rather than
+// through the 3D covariance, and its determinant by the Cauchy-Binet sum of the
+// squared 2x2 minors of N plus the dilation's terms -- all positive, so that a
+// needle-like Gaussian (one long axis) keeps an accurate determinant and conic
+// in float32, where a c - b^2 would cancel.
 __device__ __forceinline__ bool project_view(const GaussLocal &L, const DevCam &cm, ViewLocal &V) {
 #pragma unroll
   for (int r = 0; r < 3; ++r)
@@ -70,19 +75,23 @@ __device__ __forceinline__ bool project_view(const GaussLocal &L, const DevCam &
     V.T[k] = jx * (cm.R[k] - V.uc * cm.R[6 + k]);
     V.T[3 + k] = jy * (cm.R[3 + k] - V.vc * cm.R[6 + k]);
   }
-  const float *S = L.Sigma;
-  // rows of T Sigma
-  float t0[3], t1[3];
-  t0[0] = V.T[0] * S[0] + V.T[1] * S[1] + V.T[2] * S[2];
-  t0[1] = V.T[0] * S[1] + V.T[1] * S[3] + V.T[2] * S[4];
-  t0[2] = V.T[0] * S[2] + V.T[1] * S[4] + V.T[2] * S[5];
-  t1[0] = V.T[3] * S[0] + V.T[4] * S[1] + V.T[5] * S[2];
-  t1[1] = V.T[3] * S[1] + V.T[4] * S[3] + V.T[5] * S[4];
-  t1[2] = V.T[3] * S[2] + V.T[4] * S[4] + V.T[5] * S[5];
-  V.a = t0[0] * V.T[0] + t0[1] * V.T[1] + t0[2] * V.T[2] + kDilation;
-  V.b = t0[0] * V.T[3] + t0[1] * V.T[4] + t0[2] * V.T[5];
-  V.c = t1[0] * V.T[3] + t1[1] * V.T[4] + t1[2] * V.T[5] + kDilation;
-  V.det = V.a * V.c - V.b * V.b;
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      V.TR[3 * r + k] = V.T[3 * r] * L.R[k] + V.T[3 * r + 1] * L.R[3 + k] + V.T[3 * r + 2] * L.R[6 + k];
+      V.N[3 * r + k] = V.TR[3 * r + k] * L.s[k];
+    }
+  const float *N = V.N;
+  const float aa = N[0] * N[0] + N[1] * N[1] + N[2] * N[2];
+  const float cc = N[3] * N[3] + N[4] * N[4] + N[5] * N[5];
+  V.a = aa + kDilation;
+  V.b = N[0] * N[3] + N[1] * N[4] + N[2] * N[5];
+  V.c = cc + kDilation;
+  const float m01 = diff_of_products(N[0], N[4], N[1], N[3]);
+  const float m02 = diff_of_products(N[0], N[5], N[2], N[3]);
+  const float m12 = diff_of_products(N[1], N[5], N[2], N[4]);
+  V.det = (m01 * m01 + m02 * m02 + m12 * m12) + kDilation * (aa + cc) + kDilation * kDilation;
   return V.det > 0.0f;
 }
 
@@ -171,7 +180,10 @@ __device__ __forceinline__ uint32_t chain_rule(const GaussLocal &L, int64_t i, c
                                                int64_t stride, float *g) {
 #pragma unroll
   for (int k = 0; k < 11; ++k) g[k] = 0.f;
-  float GSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (symmetric, xx xy xz yy yz zz)
+  // Accumulated over views: dL/dlog s_k (gls) and the gradient of a rotation of
+  // the Gaussian about its own axes (gth, the tangent space of the quaternion).
+  float gls[3] = {0.f, 0.f, 0.f}, gth[3] = {0.f, 0.f, 0.f};
+  const float s2[3] = {L.s[0] * L.s[0], L.s[1] * L.s[1], L.s[2] * L.s[2]};
   float go = 0.f;
   uint32_t read = 0u;
 #pragma unroll 1
@@ -191,32 +203,41 @@ __device__ __forceinline__ uint32_t chain_rule(const GaussLocal &L, int64_t i, c
     const float gb = -(2.f * gA * A * B + gB * (A * C + B * B) + 2.f * gC * B * C);
     const float gc = -(gA * B * B + gB * B * C + gC * C * C);
     go += gB4.y;
-    // G' (2x2 symmetric, off-diagonal gb/2)
+    // G' = dL/dSigma' (2x2 symmetric, off-diagonal gb/2); Q = G' TR (2x3).  With
+    // Sigma' = N N^T, N = TR diag(s):
+    //   dL/dlog s_k = 2 N_k^T G' N_k = 2 s_k^2 (TR_k^T Q_k)          (N_k, TR_k: column k)
+    //   K = TR^T G' TR, and a rotation R -> R (I + [theta]x) of the Gaussian about
+    //   its own axes changes L by 2 K_12 (s_1^2 - s_2^2) theta_x
+    //   + 2 K_02 (s_2^2 - s_0^2) theta_y + 2 K_01 (s_0^2 - s_1^2) theta_z;
+    //   dL/dT = 2 G' T Sigma = 2 Q diag(s^2) R^T.
     const float G00 = ga, G01 = 0.5f * gb, G11 = gc;
-    // dL/dSigma += T^T G' T
-    const float *T = V.T;
-    float TG0[3], TG1[3];  // columns: (G' T)_{0,k}, (G' T)_{1,k}
+    float Q[6];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      TG0[k] = G00 * T[k] + G01 * T[3 + k];
-      TG1[k] = G01 * T[k] + G11 * T[3 + k];
+      Q[k] = G00 * V.TR[k] + G01 * V.TR[3 + k];
+      Q[3 + k] = G01 * V.TR[k] + G11 * V.TR[3 + k];
     }
-    GSig[0] += T[0] * TG0[0] + T[3] * TG1[0];
-    GSig[1] += T[0] * TG0[1] + T[3] * TG1[1];
-    GSig[2] += T[0] * TG0[2] + T[3] * TG1[2];
-    GSig[3] += T[1] * TG0[1] + T[4] * TG1[1];
-    GSig[4] += T[1] * TG0[2] + T[4] * TG1[2];
-    GSig[5] += T[2] * TG0[2] + T[5] * TG1[2];
-    // dL/dT = 2 G' T Sigma
-    const float *S = L.Sigma;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gls[k] += 2.f * s2[k] * (V.TR[k] * Q[k] + V.TR[3 + k] * Q[3 + k]);
+    const float K01 = V.TR[0] * Q[1] + V.TR[3] * Q[4];
+    const float K02 = V.TR[0] * Q[2] + V.TR[3] * Q[5];
+    const float K12 = V.TR[1] * Q[2] + V.TR[4] * Q[5];
+    gth[0] += 2.f * K12 * (s2[1] - s2[2]);
+    gth[1] += 2.f * K02 * (s2[2] - s2[0]);
+    gth[2] += 2.f * K01 * (s2[0] - s2[1]);
+    float QS[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      QS[k] = Q[k] * s2[k];
+      QS[3 + k] = Q[3 + k] * s2[k];
+    }
     float GT[6];
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-      const float *tg = rr == 0 ? TG0 : TG1;
-      GT[3 * rr + 0] = 2.f * (tg[0] * S[0] + tg[1] * S[1] + tg[2] * S[2]);
-      GT[3 * rr + 1] = 2.f * (tg[0] * S[1] + tg[1] * S[3] + tg[2] * S[4]);
-      GT[3 * rr + 2] = 2.f * (tg[0] * S[2] + tg[1] * S[4] + tg[2] * S[5]);
-    }
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        GT[3 * rr + j] =
+            2.f * (QS[3 * rr] * L.R[3 * j] + QS[3 * rr + 1] * L.R[3 * j + 1] + QS[3 * rr + 2] * L.R[3 * j + 2]);
     // T = J R_cam: dL/dJ = dL/dT R_cam^T (only J00, J02, J11, J12 are non-zero)
     const float *Rc = cm.R;
     const float GJ00 = GT[0] * Rc[0] + GT[1] * Rc[1] + GT[2] * Rc[2];
@@ -249,37 +270,18 @@ __device__ __forceinline__ uint32_t chain_rule(const GaussLocal &L, int64_t i, c
   }
   g[10] = go * L.o * (1.f - L.o);
   if (!read) return 0u;
-  // Sigma = M M^T, M = R diag(s): dL/dM = 2 GSig M
-  float M[9];
 #pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) M[3 * r + k] = L.R[3 * r + k] * L.s[k];
-  const float GS[9] = {GSig[0], GSig[1], GSig[2], GSig[1], GSig[3], GSig[4], GSig[2], GSig[4], GSig[5]};
-  float gR[9];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    float gs = 0.f;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const float gm = 2.f * (GS[3 * r] * M[k] + GS[3 * r + 1] * M[3 + k] + GS[3 * r + 2] * M[6 + k]);
-      gs += gm * L.R[3 * r + k];
-      gR[3 * r + k] = gm * L.s[k];
-    }
-    g[3 + k] = gs * L.s[k];
-  }
+  for (int k = 0; k < 3; ++k) g[3 + k] = gls[k];
+  // q_hat -> q_hat (x) (1, theta / 2) is the rotation R (I + [theta]x), so the
+  // gradient with respect to the raw quaternion (through its normalisation) is
+  // 2 (q_hat (x) (0, gth)) / |q| = (2 / |q|) (-v . gth, w gth + v x gth), already
+  // orthogonal to q: no projection that would cancel.
   const float w = L.qn[0], qx = L.qn[1], qy = L.qn[2], qz = L.qn[3];
-  float gq[4];
-  gq[0] = 2.f * (-gR[1] * qz + gR[2] * qy + gR[3] * qz - gR[5] * qx - gR[6] * qy + gR[7] * qx);
-  gq[1] = 2.f * (gR[1] * qy + gR[2] * qz + gR[3] * qy - 2.f * gR[4] * qx - gR[5] * w + gR[6] * qz +
-                 gR[7] * w - 2.f * gR[8] * qx);
-  gq[2] = 2.f * (-2.f * gR[0] * qy + gR[1] * qx + gR[2] * w + gR[3] * qx + gR[5] * qz - gR[6] * w +
-                 gR[7] * qz - 2.f * gR[8] * qy);
-  gq[3] = 2.f * (-2.f * gR[0] * qz - gR[1] * w + gR[2] * qx + gR[3] * w - 2.f * gR[4] * qz +
-                 gR[5] * qy + gR[6] * qx + gR[7] * qy);
-  const float dot = w * gq[0] + qx * gq[1] + qy * gq[2] + qz * gq[3];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) g[6 + k] = (gq[k] - L.qn[k] * dot) * L.qinv;
+  const float f2 = 2.f * L.qinv;
+  g[6] = -f2 * (qx * gth[0] + qy * gth[1] + qz * gth[2]);
+  g[7] = f2 * (w * gth[0] + (qy * gth[2] - qz * gth[1]));
+  g[8] = f2 * (w * gth[1] + (qz * gth[0] - qx * gth[2]));
+  g[9] = f2 * (w * gth[2] + (qx * gth[1] - qy * gth[0]));
   return read;
 }
 
