@@ -354,7 +354,8 @@ def run_ours(args):
     ms_max, value = aggregate(ms, iters_per_step * args.steps, world, dist if world > 1 else None)
     total_iters = iters_per_step * args.steps * world
     peaks = load_peaks()
-    roof = pipe.roofline(peaks, os.path.join(ROOT, "profiles"), total_ms=ms)
+    measured = fgs.measure_peaks()          # on-chip rates of this device, after the timed region
+    roof = pipe.roofline(peaks, os.path.join(ROOT, "profiles"), total_ms=ms, measured=measured)
     pipe.mapper.nc_snap.clear()
 
     e2e = None
@@ -403,6 +404,7 @@ def run_ours(args):
                    "final_gaussians": pipe.live_count(), "pairs_last": pipe.last_pairs(),
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
+        "peaks_measured": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in measured.items()},
         "kernels_ms_per_step": breakdown,
         "kernels_breakdown": f"separate pass of {bd_steps} steps after the timed region, events around every call",
         "window": window,

@@ -244,8 +244,11 @@ size_t fgs_loss_workspace_size(const fgs_camera *cams, int32_t n_views);
  *   Larger view sets return FGS_ERR_CAPACITY before anything is launched.
  *   Every device that loads the library holds the array until the process
  *   exits.  The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) and caches it, so make that first call before any
- *   stream capture on that device.  The call allocates nothing.
+ *   (cudaGetSymbolAddress) and caches it for the life of the process, so make
+ *   that first call before any stream capture on that device, and do not call
+ *   it again after cudaDeviceReset on that device (the reset unloads the
+ *   array; the cached address would then be stale).  The call allocates
+ *   nothing.
  *   All calls share the one array: calls whose kernels can overlap on the GPU
  *   (different streams without ordering) race on it and give wrong sums.
  *   Nothing in the array needs clearing: every call writes each partial it
@@ -524,6 +527,32 @@ fgs_status fgs_render_window(const fgs_gaussians *g, const fgs_projected *proj,
                              void *ws, size_t ws_bytes, int32_t *d_status, void *stream);
 size_t fgs_render_window_workspace_size(const fgs_camera *cams, int32_t n_views);
 
+/* fgs_autotune -- picks the tiling of the keyframe window above (the window of
+ * Sec. III-C; the paper gives no kernel design, so the tile shape and batch depth
+ * are measured rather than fixed): every supported tiling -- 8x8, 16x16 and 16x32
+ * tiles (w x h) times batch depths 32, 64, 128, 256, FGS_AUTOTUNE_CONFIGS in the
+ * order 8x8/32, 8x8/64, ..., 16x32/256 -- runs fgs_project, fgs_bin_sort,
+ * fgs_render_window and fgs_project_bwd on the caller's map g, views cams and
+ * targets (color_gt, depth_gt as for fgs_render_window, weights `loss`), once
+ * untimed and `reps` times timed with CUDA events; the fastest is written to
+ * *best and, when ms_out (host, FGS_AUTOTUNE_CONFIGS floats) is not NULL, the
+ * milliseconds per pass of every tiling (FLT_MAX for a tiling whose pass set a
+ * device status bit, e.g. more pairs than pair_capacity).
+ *   g is only read (its gradients and every intermediate go to ws).
+ *   ws: fgs_autotune_workspace_size(g, cams, n_views, pair_capacity) bytes,
+ *   256-byte aligned, caller-owned.
+ *   Unlike the other entry points this call synchronises the host with `stream`
+ *   (it reads its timings back) and cannot be captured in a CUDA graph.
+ * err: INVALID_ARGUMENT (bad views, NULLs, small workspace, reps outside
+ *   1..1000), CAPACITY when every tiling overflowed, CUDA. */
+#define FGS_AUTOTUNE_CONFIGS 12
+fgs_status fgs_autotune(const fgs_gaussians *g, const fgs_camera *cams, int32_t n_views,
+                        const float *color_gt, const float *depth_gt, const fgs_loss_params *loss,
+                        int64_t pair_capacity, int32_t reps, void *ws, size_t ws_bytes,
+                        fgs_tiling *best, float *ms_out, void *stream);
+size_t fgs_autotune_workspace_size(const fgs_gaussians *g, const fgs_camera *cams,
+                                   int32_t n_views, int64_t pair_capacity);
+
 /* ---------------------------------------------------------------------------------
  * Learned seeding prior (not in the paper; an extension).  Features per seed
  * pixel (x, y): the 16x16 grayscale patch with top-left (x-8, y-8), clamped to the
@@ -578,6 +607,23 @@ int64_t fgs_launch_count(void);
 fgs_status fgs_memset_async(void *dst, int32_t value, size_t bytes, void *stream);
 /* cudaMemcpyAsync of `bytes` bytes (any direction the pointers imply) on the stream. */
 fgs_status fgs_memcpy_async(void *dst, const void *src, size_t bytes, void *stream);
+
+/* Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount). */
+int32_t fgs_num_sms(void);
+
+/* fgs_peak_probe -- one launch of a microbenchmark of an on-chip rate that bounds
+ * the blend kernels (measurement infrastructure; the paper has none): kind
+ * FGS_PEAK_FFMA runs FP32 fused multiply-adds, FGS_PEAK_EX2 the ex2.approx MUFU
+ * instruction, FGS_PEAK_LDS 16-byte shared-memory loads, each as 16 independent
+ * chains per thread in fgs_num_sms() * blocks_per_sm blocks of 256 threads for
+ * `iters` rounds.  *ops (host) receives the operation count of the launch:
+ * floating-point operations (2 per FMA), ex2 evaluations, or bytes loaded.  The
+ * caller times the launch on `stream` (CUDA events) and divides.  sink: a device
+ * float per block that the kernels never write in practice (it keeps their
+ * results live).  blocks_per_sm 1..32, iters 1..2^32. */
+enum { FGS_PEAK_FFMA = 0, FGS_PEAK_EX2 = 1, FGS_PEAK_LDS = 2 };
+fgs_status fgs_peak_probe(int32_t kind, int32_t blocks_per_sm, int64_t iters, float *sink,
+                          int64_t *ops, void *stream);
 
 #ifdef __cplusplus
 }

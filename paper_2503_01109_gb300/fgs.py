@@ -151,6 +151,8 @@ _SIGS = {
     "fgs_launch_count": ([], c_int64),
     "fgs_memset_async": ([c_void_p, c_int32, c_size_t, c_void_p], c_int32),
     "fgs_memcpy_async": ([c_void_p, c_void_p, c_size_t, c_void_p], c_int32),
+    "fgs_num_sms": ([], c_int32),
+    "fgs_peak_probe": ([c_int32, c_int32, c_int64, c_void_p, ctypes.POINTER(c_int64), c_void_p], c_int32),
 }
 _OPTIONAL = {
     "fgs_fourier_seed": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -171,6 +173,9 @@ _OPTIONAL = {
                           c_void_p, c_void_p], c_int32),
     "fgs_grid_barrier_probe": ([c_int32, c_int32, c_int64, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p],
                                c_int32),
+    "fgs_autotune": ([c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p,
+                      c_size_t, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_autotune_workspace_size": ([c_void_p, c_void_p, c_int32, c_int64], c_size_t),
 }
 
 
@@ -570,6 +575,49 @@ def fgs_memcpy_async(dst: torch.Tensor, src: torch.Tensor):
     _check(lib().fgs_memcpy_async(_ptr(dst), _ptr(src), n, _stream()), "fgs_memcpy_async")
 
 
+FGS_PEAK_FFMA, FGS_PEAK_EX2, FGS_PEAK_LDS = 0, 1, 2
+
+
+def fgs_num_sms() -> int:
+    return int(lib().fgs_num_sms())
+
+
+def fgs_peak_probe(kind: int, blocks_per_sm: int, iters: int, sink: torch.Tensor) -> int:
+    """Launches one peak microbenchmark on the current stream; returns its operation count."""
+    ops = c_int64(0)
+    _check(lib().fgs_peak_probe(int(kind), int(blocks_per_sm), int(iters), _ptr(sink), ctypes.byref(ops), _stream()),
+           "fgs_peak_probe")
+    return int(ops.value)
+
+
+def measure_peaks(target_ms: float = 20.0, reps: int = 3) -> dict:
+    """Measured on-chip rates of the current device: FP32 FMA (TFLOP/s), MUFU ex2
+    (G evaluations/s) and shared-memory loads (TB/s), each the best of `reps`
+    launches timed with CUDA events and sized to about target_ms."""
+    sink = torch.zeros(fgs_num_sms() * 32, dtype=torch.float32, device="cuda")
+    out = {"sms": fgs_num_sms()}
+    names = {FGS_PEAK_FFMA: ("fp32_fma_tflops", 1e12), FGS_PEAK_EX2: ("mufu_ex2_gops", 1e9),
+             FGS_PEAK_LDS: ("smem_load_tbs", 1e12)}
+    for kind, (name, unit) in names.items():
+        iters, best = 1024, 0.0
+        for _ in range(12):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            rates = []
+            for _ in range(reps):
+                e0.record()
+                ops = fgs_peak_probe(kind, 8, iters, sink)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                rates.append(ops / (ms / 1e3))
+            best = max(rates)
+            if ms >= target_ms or iters >= (1 << 31):
+                break
+            iters = min(1 << 31, int(iters * max(2.0, target_ms / max(ms, 1e-3))))
+        out[name] = best / unit
+    return out
+
+
 def ws_tensor(nbytes: int, device="cuda") -> torch.Tensor:
     """Workspace of at least nbytes, 256-byte aligned (torch allocations are)."""
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
@@ -642,3 +690,26 @@ def fgs_render_window(g: GaussianMap, proj: Projection, cams: list, til: Tiling,
                                    _ptr(frame.n_contrib), _ptr(dC), _ptr(dD), _ptr(grad2d), ctypes.byref(gr),
                                    _ptr(loss_acc), _ptr(ws), ws.numel() * ws.element_size(), _ptr(status),
                                    _stream()), "fgs_render_window")
+
+
+AUTOTUNE_CONFIGS = 12
+AUTOTUNE_ORDER = [((tw, th), bd) for (tw, th) in ((8, 8), (16, 16), (16, 32)) for bd in (32, 64, 128, 256)]
+
+
+def fgs_autotune_workspace_size(g: GaussianMap, cams: list, pair_capacity: int, use_device_count: bool = True) -> int:
+    gs = g.struct(use_device_count)
+    return int(lib().fgs_autotune_workspace_size(ctypes.byref(gs), camera_array(cams), len(cams),
+                                                 int(pair_capacity)))
+
+
+def fgs_autotune(g: GaussianMap, cams: list, color_gt, depth_gt, w_c, w_d, w_s, pair_capacity: int, reps: int, ws,
+                 use_device_count: bool = True):
+    """Returns (best Tiling, [ms per tiling in AUTOTUNE_ORDER]); synchronises the stream."""
+    gs = g.struct(use_device_count)
+    lp = LossParams(float(w_c), float(w_d), float(w_s))
+    best = Tiling()
+    ms = (c_float * AUTOTUNE_CONFIGS)()
+    _check(lib().fgs_autotune(ctypes.byref(gs), camera_array(cams), len(cams), _ptr(color_gt), _ptr(depth_gt),
+                              ctypes.byref(lp), int(pair_capacity), int(reps), _ptr(ws), ws.numel() * ws.element_size(),
+                              ctypes.byref(best), ms, _stream()), "fgs_autotune")
+    return best, [float(x) for x in ms]

@@ -188,10 +188,10 @@ class FramePipeline:
         if from_host is None:       # frames already resident in HBM: point at them
             self.mapper.color_gt = self.colors[k]
             self.mapper.depth_gt = self.depths[k]
-        else:                       # end-to-end: copy this frame from pinned host memory
+        else:                       # end-to-end: copy this frame from pinned host memory (C ABI)
             c, d = from_host
-            self.stage_c.copy_(c, non_blocking=True)
-            self.stage_d.copy_(d, non_blocking=True)
+            fgs.fgs_memcpy_async(self.stage_c, c)
+            fgs.fgs_memcpy_async(self.stage_d, d)
             self.mapper.color_gt, self.mapper.depth_gt = self.stage_c, self.stage_d
 
     def mapping_step(self, k: int, from_host=None):
@@ -220,7 +220,8 @@ class FramePipeline:
 
     def e2e_measure(self, warmup: int, steps: int, step_fn):
         """The same steps with each frame's colour + depth copied from pinned host
-        memory and the loss read back to the host inside the timed region."""
+        memory and the loss read back to the host inside the timed region, both
+        through the library's fgs_memcpy_async with host pointers."""
         hosts = [(c.cpu().pin_memory(), d.cpu().pin_memory()) for c, d in zip(self.colors, self.depths)]
         h2d = hosts[0][0].numel() * 4 + hosts[0][1].numel() * 4
         stream = torch.cuda.current_stream()
@@ -229,7 +230,7 @@ class FramePipeline:
         e0.record(stream)
         for k in range(warmup, warmup + steps):
             step_fn(k, from_host=hosts[k % len(hosts)])
-            self.loss_host.copy_(self.mapper.loss_acc, non_blocking=True)
+            fgs.fgs_memcpy_async(self.loss_host, self.mapper.loss_acc)     # device -> pinned host
         e1.record(stream)
         torch.cuda.synchronize()
         return {"ms": e0.elapsed_time(e1), "h2d": h2d, "d2h": 4}
@@ -276,10 +277,18 @@ class FramePipeline:
             return None
         return float(m.group(1))
 
-    def roofline(self, peaks: dict, profiles_dir: str | None = None, total_ms: float | None = None):
-        """The dominant render kernel against the derived ALU peak, from the launches
+    # MUFU evaluations per pair: the forward's ex2; the adjoint's ex2 and 1 / (1 - alpha)
+    MUFU_FWD_PAIR = 1
+    MUFU_BWD_PAIR = 2
+
+    def roofline(self, peaks: dict, profiles_dir: str | None = None, total_ms: float | None = None,
+                 measured: dict | None = None):
+        """The dominant render kernel against the FP32 FMA rate, from the launches
         timed since the timer was enabled; share_of_step relative to total_ms (the
-        timed region) when given, else to the sum of the timed spans."""
+        timed region) when given, else to the sum of the timed spans.  `measured`
+        holds the on-chip rates fgs.measure_peaks() measured on this device (FP32
+        FMA, MUFU ex2); without it the FP32 peak is derived from the SM count the
+        library reports, 128 FP32 lanes, 2 FLOP per FMA and the maximum SM clock."""
         t = self.kernel_timer
         totals = {k: sum(t.durations(k)) for k in t.events}
         if not totals:
@@ -289,21 +298,33 @@ class FramePipeline:
         name = max(("render_fwd", "render_bwd"), key=lambda k: totals.get(k, 0.0))
         durs = fwd if name == "render_fwd" else bwd
         per_pair = self.FLOP_FWD_PAIR if name == "render_fwd" else self.FLOP_BWD_PAIR
+        mufu_pair = self.MUFU_FWD_PAIR if name == "render_fwd" else self.MUFU_BWD_PAIR
         # the bwd of iteration i walks the lists rendered by the fwd of iteration i;
         # the seeding render of a frame has no backward
         w = self.contributor_work(iterations_only=(name == "render_bwd"))
         n = min(len(w), len(durs))
         if n == 0:
             return None
-        flops = np.array(w[-n:], np.float64) * per_pair
+        pairs = np.array(w[-n:], np.float64)
         secs = np.array(durs[-n:], np.float64) / 1e3
-        achieved = float(np.mean(flops / secs)) / 1e12
-        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 FLOP x max SM clock
+        achieved = float(np.mean(pairs * per_pair / secs)) / 1e12
+        if measured and measured.get("fp32_fma_tflops"):
+            peak = float(measured["fp32_fma_tflops"])
+            source = (f"measured: fgs_peak_probe FP32 FMA on this device ({measured.get('sms')} SMs), "
+                      "best of 3 launches of ~20 ms")
+        else:
+            sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+            peak = fgs.fgs_num_sms() * 128 * 2 * sm_max * 1e6 / 1e12
+            source = "derived: SMs (library) x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)"
         traffic = self.profiled_traffic(name, profiles_dir) if profiles_dir else None
-        return {"kernel": name, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)",
-                "share_of_step": round(totals[name] / (total_ms or sum(totals.values())), 3),
-                "avg_launch_ms": round(float(np.mean(durs)), 4)}
+        out = {"kernel": name, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+               "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+               "traffic_unit": "bytes per launch (DRAM read + write, ncu)", "peak_source": source,
+               "flop_per_pair": per_pair, "pairs_per_launch": float(np.mean(pairs)),
+               "share_of_step": round(totals[name] / (total_ms or sum(totals.values())), 3),
+               "avg_launch_ms": round(float(np.mean(durs)), 4)}
+        if measured and measured.get("mufu_ex2_gops"):
+            mufu = float(np.mean(pairs * mufu_pair / secs)) / 1e9
+            out["mufu"] = {"achieved_gops": round(mufu, 1), "peak_gops": round(float(measured["mufu_ex2_gops"]), 1),
+                           "frac": round(mufu / float(measured["mufu_ex2_gops"]), 4), "per_pair": mufu_pair}
+        return out

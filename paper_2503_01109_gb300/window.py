@@ -13,9 +13,6 @@ import torch
 from . import fgs
 from .mapping import Mapper, PAPER_LOSS, PAPER_REG
 
-TILES = ((8, 8), (16, 16), (16, 32))
-BATCHES = (32, 64, 128, 256)
-
 
 class Window(Mapper):
     def __init__(self, g: fgs.GaussianMap, cams: list, til: fgs.Tiling | None = None, **kw):
@@ -65,33 +62,18 @@ class Window(Mapper):
         self.graph.replay()
 
 
-def time_config(g: fgs.GaussianMap, cams, color_gt, depth_gt, tile, batch, reps=5, warmup=2, **kw) -> float:
-    """Milliseconds per window iteration of one (tile, batch) choice, on a copy of
-    the map (the trial's Adam steps do not touch the caller's map)."""
-    trial = g.zeros_like()
-    trial.buf.copy_(g.buf)
-    w = Window(trial, cams, fgs.tiling(tile[0], tile[1], batch), **kw)
-    w.set_target(color_gt, depth_gt)
-    for _ in range(warmup):
-        w.iteration()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        w.iteration()
-    e1.record()
-    torch.cuda.synchronize()
-    w.check_status()
-    return e0.elapsed_time(e1) / reps
-
-
-def autotune(g: fgs.GaussianMap, cams, color_gt, depth_gt, tiles=TILES, batches=BATCHES, reps=5, **kw):
-    """Times every (tile, batch) choice and returns (best tiling, {(tile, batch): ms})."""
-    table = {}
-    for tile in tiles:
-        for batch in batches:
-            table[(tile, batch)] = time_config(g, cams, color_gt, depth_gt, tile, batch, reps=reps, **kw)
-    (tile, batch), _ = min(table.items(), key=lambda kv: kv[1])
-    return fgs.tiling(tile[0], tile[1], batch), table
+def autotune(g: fgs.GaussianMap, cams, color_gt, depth_gt, reps: int = 5, loss_w=PAPER_LOSS,
+             pair_capacity: int | None = None, use_device_count: bool = True):
+    """The library's tiling autotuner (``fgs_autotune``) on this window: times every
+    tile shape x batch depth (projection, binning, the persistent launch and the
+    projection adjoint; the map is only read) and returns (best tiling,
+    {(tile, batch): ms per pass})."""
+    if pair_capacity is None:
+        pair_capacity = min(2 ** 31 - 1, max(1 << 20, 64 * g.capacity * len(cams)))
+    ws = fgs.ws_tensor(fgs.fgs_autotune_workspace_size(g, cams, pair_capacity, use_device_count), g.buf.device)
+    best, ms = fgs.fgs_autotune(g, cams, color_gt, depth_gt, *loss_w, pair_capacity, reps, ws, use_device_count)
+    del ws
+    return best, dict(zip(fgs.AUTOTUNE_ORDER, ms))
 
 
 class KeyframeSelector:

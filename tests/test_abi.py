@@ -118,3 +118,39 @@ def test_fused_tail_argument_checks(lib):
     assert L.fgs_project_bwd_adam(*args(gr, hp0, need)) == 1 and b"step" in L.fgs_last_error()
     short = gaussians(500, 1024)
     assert L.fgs_project_bwd_adam(*args(short, hp, need)) == 1 and b"cover" in L.fgs_last_error()
+
+
+def test_peak_probe_argument_checks(lib):
+    """fgs_peak_probe refuses an unknown kind or an empty launch before any CUDA call."""
+    from paper_2503_01109_gb300 import fgs
+    L = fgs.lib()
+    ops = ctypes.c_int64(0)
+    sink = ctypes.c_void_p(16)
+    assert L.fgs_peak_probe(7, 1, 10, sink, ctypes.byref(ops), None) == 1
+    assert b"unknown kind" in L.fgs_last_error()
+    assert L.fgs_peak_probe(0, 0, 10, sink, ctypes.byref(ops), None) == 1
+    assert L.fgs_peak_probe(0, 1, 0, sink, ctypes.byref(ops), None) == 1
+
+
+def test_autotune_argument_checks(lib):
+    """fgs_autotune refuses a missing workspace or bad repetitions before any CUDA call,
+    and its workspace size answers on the host."""
+    from paper_2503_01109_gb300 import fgs, synthetic as syn
+    L = fgs.lib()
+    cams = fgs.camera_array([syn.pinhole(64, 48, 60.0), syn.pinhole(40, 30, 40.0)])
+    g = fgs.Gaussians()
+    g.n, g.capacity = 100, 128
+    for k in ("means", "log_scales", "quats", "opacity_logits", "rgb"):
+        setattr(g, k, 256)
+    need = L.fgs_autotune_workspace_size(ctypes.byref(g), cams, 2, 1 << 16)
+    assert need > 2 * (1 << 16) * 4
+    assert L.fgs_autotune_workspace_size(ctypes.byref(g), cams, 0, 1 << 16) == 0
+    lp = fgs.LossParams(0.9, 0.1, 0.1)
+    best = fgs.Tiling()
+    dummy = ctypes.c_void_p(256)
+    rc = L.fgs_autotune(ctypes.byref(g), cams, 2, dummy, dummy, ctypes.byref(lp), 1 << 16, 3, dummy, need - 1,
+                        ctypes.byref(best), None, None)
+    assert rc == 1 and b"workspace" in L.fgs_last_error()
+    rc = L.fgs_autotune(ctypes.byref(g), cams, 2, dummy, dummy, ctypes.byref(lp), 1 << 16, 0, dummy, need,
+                        ctypes.byref(best), None, None)
+    assert rc == 1 and b"reps" in L.fgs_last_error()
