@@ -90,6 +90,8 @@ def lib():
             L.or_scale_reg.restype = f64
             L.or_adam.argtypes = [i64, P, P, P, P, f64, f64, f64, f64, i32]
             L.or_num_threads.restype = ctypes.c_int
+            L.or_set_num_threads.argtypes = [ctypes.c_int]
+            L.or_set_num_threads.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -101,6 +103,11 @@ def _p(a: np.ndarray):
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_num_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP regions; returns the previous count."""
+    return int(lib().or_set_num_threads(int(n)))
 
 
 # ----------------------------------------------------------------------------------

@@ -807,3 +807,16 @@ int or_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads of the OpenMP regions above (the timed baseline runs on all host cores
+ * and on one); returns the previous setting. */
+int or_set_num_threads(int n) {
+#ifdef _OPENMP
+  int old = omp_get_max_threads();
+  if (n >= 1) omp_set_num_threads(n);
+  return old;
+#else
+  (void)n;
+  return 1;
+#endif
+}

@@ -42,7 +42,7 @@ class SlamLoop:
     def __init__(self, colors, depths, cams, capacity: int, prior: PriorMLP | None = None, window: int = 1,
                  tiling: fgs.Tiling | None = None, target_psnr: float = 30.0, max_iters: int = 60,
                  seed_params: fgs.SeedParams | None = None, record_seeds: bool = False,
-                 selector: KeyframeSelector | None = None):
+                 selector: KeyframeSelector | None = None, track_map: bool = False):
         """window > 1: optimise the current frame with earlier keyframes -- the
         window - 1 previous frames, or, with `selector`, the co-visible and random
         keyframes it picks among all earlier frames (at most window - 1)."""
@@ -55,6 +55,7 @@ class SlamLoop:
         self.seeder = Seeder(self.mapper, seed_params, prior)
         self.win = None
         self.record = record_seeds
+        self.track_map = track_map
         self.seed_log = []   # (first index, count, features [n][272])
         self.frames = []     # per frame: iterations, seconds, final psnr
 
@@ -62,7 +63,8 @@ class SlamLoop:
         ks = sorted(picked) + [k] if picked is not None else list(range(max(0, k - self.window + 1), k + 1))
         cams = [self.cams[j] for j in ks]
         if self.win is None or len(self.win.cams) != len(cams):
-            self.win = Window(self.g, cams, self.til)
+            self.win = None   # release the previous window's buffers first
+            self.win = Window(self.g, cams, self.til, pair_capacity=32_000_000 * len(cams))
         else:
             self.win.set_cameras(cams)
         self.win.color_gt = torch.cat([self.colors[j] for j in ks])
@@ -99,12 +101,15 @@ class SlamLoop:
                 self.mapper.iteration()
                 f = self.mapper.frame.color
             it += 1
-            p = psnr(f, self.colors[k])          # the render this iteration optimised
-            if p >= self.target:
-                break
+            if math.isfinite(self.target):
+                p = psnr(f, self.colors[k])      # the render this iteration optimised
+                if p >= self.target:
+                    break
         torch.cuda.synchronize()
         self.frames.append({"iters": it, "seconds": time.perf_counter() - t0, "psnr": p,
                             "gaussians": int(self.g.d_n.item())})
+        if self.track_map:   # the map's quality over every frame seen so far (not timed)
+            self.frames[-1]["map_psnr_seen"] = self.evaluate_all(k + 1)
 
     def run(self, n_frames: int | None = None):
         for k in range(n_frames or len(self.cams)):
@@ -112,10 +117,10 @@ class SlamLoop:
         self.mapper.check_status()
         return self.frames
 
-    def evaluate_all(self) -> float:
-        """Mean PSNR of the final map over every frame of the trajectory."""
+    def evaluate_all(self, n_frames: int | None = None) -> float:
+        """Mean PSNR of the map over the first n_frames frames (all by default)."""
         vals = []
-        for k, cam in enumerate(self.cams):
+        for k, cam in enumerate(self.cams[:n_frames]):
             self.mapper.set_cameras([cam])
             self.mapper.render()
             vals.append(psnr(self.mapper.frame.color, self.colors[k]))
@@ -175,6 +180,8 @@ def summarise(frames: list, target: float | None = None) -> dict:
            "gaussians": frames[-1]["gaussians"] if frames else 0}
     if target is not None:
         out["frames_reaching_target"] = int(sum(1 for f in frames if f["psnr"] >= target))
+    if frames and "map_psnr_seen" in frames[0]:
+        out["map_psnr_seen_mean"] = float(np.mean([f["map_psnr_seen"] for f in frames]))
     return out
 
 
@@ -194,38 +201,75 @@ def init_error(prior: PriorMLP, feats: torch.Tensor, targets: torch.Tensor, dept
             "eq11_logit": float(((eq11[:, 3] - targets[:, 3]) ** 2).mean().item())}
 
 
-def compare(gt_colors_train, gt_depths_train, cams_train, gt_colors_test, gt_depths_test, cams_test,
-            capacity: int, target_psnr: float = 30.0, train_iters: int = 40, max_iters: int = 100,
-            epochs: int = 12, window: int = 3) -> dict:
-    """The whole experiment: pairs from the plain loop on a training trajectory,
-    prior training on the GPU, then on a test trajectory of the same scene the
-    plain per-view loop, the per-view loop with the learned prior, the batched
-    window of the previous frames with the learned prior, and the batched window
-    of the co-visible and random keyframes (Sec. III-C) with the learned prior."""
+def collect_pairs(runs, capacity: int, train_iters: int, target_pairs: int, time_budget_s: float = 120.0):
+    """Training pairs of the learned prior from plain mapping runs: each run maps
+    its trajectory from an empty map (eq11 seeding, `train_iters` iterations per
+    frame) and yields the features of its high-frequency seeds and their
+    parameters at the end of the run.  Runs are taken in order until
+    `target_pairs` pairs or the time budget is reached.  Returns (features,
+    targets, per-run pair counts)."""
+    feats, targs, counts = [], [], []
+    total, t0 = 0, time.perf_counter()
+    for colors, depths, cams in runs:
+        rec = SlamLoop(colors, depths, cams, capacity, target_psnr=math.inf, max_iters=train_iters,
+                       record_seeds=True)
+        rec.run()
+        f, t = rec.training_pairs(high_only=True)
+        feats.append(f)
+        targs.append(t)
+        counts.append(int(f.shape[0]))
+        total += int(f.shape[0])
+        del rec
+        if total >= target_pairs or time.perf_counter() - t0 > time_budget_s:
+            break
+    return torch.cat(feats), torch.cat(targs), counts
+
+
+def compare(train_runs, gt_colors_test, gt_depths_test, cams_test, capacity: int, target_psnr: float = 30.0,
+            train_iters: int = 40, max_iters: int = 100, epochs: int = 8, window: int = 8,
+            target_pairs: int = 2_000_000, batch: int = 8192) -> dict:
+    """The whole experiment: pairs from plain mapping runs (configuration-2/3-like
+    trajectories, `train_runs` = [(colours, depths, cameras)]), prior training on
+    the GPU, then on a test trajectory of another scene four loops from an empty
+    map -- the plain per-view loop, the per-view loop with the learned prior, the
+    batched window of the current frame and up to window - 1 co-visible and
+    random keyframes (Sec. III-C) without and with the learned prior -- each run
+    until the current frame reaches target_psnr (at most max_iters iterations per
+    frame; a window iteration renders all its views).  Reported per loop: the
+    iterations and wall time to the target, and the map's PSNR over all frames
+    seen so far after each frame (its mean) and over the whole trajectory at the
+    end."""
     t0 = time.perf_counter()
-    rec = SlamLoop(gt_colors_train, gt_depths_train, cams_train, capacity, target_psnr=1e9, max_iters=train_iters,
-                   record_seeds=True)
-    rec.run()
-    feats, targs = rec.training_pairs(high_only=True)
+    feats, targs, counts = collect_pairs(train_runs, capacity, train_iters, target_pairs)
+    t_pairs = time.perf_counter() - t0
     fw, tw = opacity_weighted(feats, targs)
-    n_train = int(0.9 * fw.shape[0])
-    prior, hist = train_prior(fw[:n_train], tw[:n_train], epochs=epochs)
-    # held-out pairs: the depth feature (column 256) is the seed's depth in BF16
+    n_train = int(0.95 * fw.shape[0])
+    prior, hist = train_prior(fw[:n_train], tw[:n_train], epochs=epochs, batch=batch)
     held_f, held_t = fw[n_train:], tw[n_train:]
     d = held_f[:, 256].to(torch.int32).bitwise_left_shift(16).view(torch.float32)
-    cam = cams_train[0]
+    cam = cams_test[0]
     err = init_error(prior, held_f, held_t, d, 0.5 * (cam["fx"] + cam["fy"]))
     t_train = time.perf_counter() - t0
-    out = {"target_psnr": target_psnr, "pairs": int(feats.shape[0]), "train_loss": hist,
-           "init_mse_held_out": err, "train_seconds": t_train}
-    variants = (("plain", None, 1, None), ("learned_prior", prior, 1, None),
-                ("learned_prior_window", prior, window, None),
-                ("learned_prior_covis_window", prior, window, KeyframeSelector(seed=0)))
-    for name, pr, win, sel in variants:
+    out = {"target_psnr": target_psnr, "pairs": int(feats.shape[0]), "pairs_per_run": counts,
+           "pairs_seconds": t_pairs, "train_loss": hist, "init_mse_held_out": err, "train_seconds": t_train}
+    del feats, targs
+    variants = (("plain", None, 1), ("learned_prior", prior, 1), ("window", None, window),
+                ("learned_prior_window", prior, window))
+    for name, pr, win in variants:
+        sel = KeyframeSelector(seed=0, max_keyframes=window - 1) if win > 1 else None
         L = SlamLoop(gt_colors_test, gt_depths_test, cams_test, capacity, prior=pr, window=win,
-                     target_psnr=target_psnr, max_iters=max_iters, selector=sel)
+                     target_psnr=target_psnr, max_iters=max_iters, selector=sel, track_map=True)
         L.run()
         res = summarise(L.frames, target_psnr)
         res["psnr_all_frames_end"] = L.evaluate_all()
         out[name] = res
+        del L
+    p, lp, w, lw = (out[k] for k in ("plain", "learned_prior", "window", "learned_prior_window"))
+    out["verdict"] = {
+        "learned_vs_plain_iters": lp["iters_total"] / max(p["iters_total"], 1),
+        "learned_vs_plain_seconds": lp["seconds_total"] / max(p["seconds_total"], 1e-9),
+        "learned_window_vs_plain_iters": lw["iters_total"] / max(p["iters_total"], 1),
+        "learned_window_vs_plain_seconds": lw["seconds_total"] / max(p["seconds_total"], 1e-9),
+        "learned_window_vs_plain_map_psnr_db": lw["psnr_all_frames_end"] - p["psnr_all_frames_end"],
+        "window_vs_plain_map_psnr_db": w["psnr_all_frames_end"] - p["psnr_all_frames_end"]}
     return out
