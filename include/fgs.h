@@ -179,6 +179,22 @@ fgs_status fgs_render_fwd(const fgs_projected *proj, const fgs_gaussians *g,
                           float *depth, float *alpha, float *t_final, int32_t *n_contrib,
                           int32_t *d_status, void *stream);
 
+/* fgs_render_fwd_sampled -- fgs_render_fwd on the grid of pixels with
+ * x % s == 0 and y % s == 0 (s = sample_stride, which must be 2; tiling 16x16 or
+ * 16x32): those pixels get exactly fgs_render_fwd's values (the same arithmetic
+ * over the same lists), every other pixel the background (colour, depth and alpha
+ * 0, t_final 1, n_contrib 0).  For a consumer that reads the render only on such
+ * a grid: the seeding step (fgs_fourier_seed) places seeds only on the m- and
+ * n-grids of Sec. III-A, so with m and n even its seeds are those of a full render
+ * (its mask's bit 2, M_m, then reflects the background off the grid).  One thread
+ * per grid pixel: a quarter of the blending work. */
+fgs_status fgs_render_fwd_sampled(const fgs_projected *proj, const fgs_gaussians *g,
+                                  const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
+                                  const int32_t *ids, const int32_t *tile_ranges,
+                                  int32_t sample_stride, float *color, float *depth, float *alpha,
+                                  float *t_final, int32_t *n_contrib, int32_t *d_status,
+                                  void *stream);
+
 /* ---------------------------------------------------------------------------------
  * fgs_render_bwd -- reverse-mode adjoint of fgs_render_fwd and fgs_project: the
  * gradient of the mapping loss (eq16) with respect to every Gaussian parameter,
@@ -239,8 +255,8 @@ size_t fgs_loss_workspace_size(const fgs_camera *cams, int32_t n_views);
  *   Same arguments, layouts, outputs and device behaviour as fgs_loss (the loss
  *   value is ADDED to *d_loss).  The per-tile partial sums go to a scratch array
  *   compiled into the library: FGS_LOSS_NOALLOC_MAX_TILES doubles (512 KiB),
- *   i.e. at most that many 16x16 loss tiles over all views (sum over views of
- *   ceil(W/16) * ceil(H/16); 65536 tiles = 16.7 M pixels, 20 views of 1200x680).
+ *   i.e. at most that many 32x32 loss tiles over all views (sum over views of
+ *   ceil(W/32) * ceil(H/32); 65536 tiles = 67 M pixels, 78 views of 1200x680).
  *   Larger view sets return FGS_ERR_CAPACITY before anything is launched.
  *   Every device that loads the library holds the array until the process
  *   exits.  The first call on a device looks up the array's device address
@@ -563,7 +579,14 @@ size_t fgs_autotune_workspace_size(const fgs_gaussians *g, const fgs_camera *cam
  *
  * fgs_prior_features: rgb [3][H][W] (gray = BT.601 luma), depth [H][W],
  *   seed_xy [n][2] int32 -> features [n][272] BF16.
- * fgs_prior_infer: features -> out [n][4] float. */
+ * fgs_prior_infer: features -> out [n][4] float, on the fifth-generation tensor
+ *   cores: a persistent grid walks 128-row tiles; the three layers run as
+ *   tcgen05.mma chains (M = 128; N = 128, 128, 16; K = 272, 128, 128) with the
+ *   weights resident in shared memory and FP32 accumulators in tensor memory; the
+ *   bias, GELU and BF16 rounding are applied when the accumulator is read back.
+ *   features and out must be 16-byte aligned.  d_status (may be NULL): a tensor-core
+ *   completion wait that gives up or-es FGS_DEV_TIMEOUT into it and the rows of
+ *   that tile are left unwritten. */
 #define FGS_PRIOR_IN 272
 #define FGS_PRIOR_HID 128
 #define FGS_PRIOR_OUT 4
@@ -571,7 +594,7 @@ fgs_status fgs_prior_features(const float *rgb, const float *depth, int32_t widt
                               int32_t height, const int32_t *seed_xy, int64_t n,
                               uint16_t *features, void *stream);
 fgs_status fgs_prior_infer(const fgs_mlp *mlp, const uint16_t *features, int64_t n,
-                           float *out, void *stream);
+                           float *out, int32_t *d_status, void *stream);
 
 /* fgs_prior_train -- one Adam step of the prior on a batch: mean squared error
  * over the batch's n x 4 outputs against `targets`, gradients through the MLP,

@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(kSeedBlock) k_seed_write(SeedArgs a, GaussGrad
 fgs_status prior_apply_to_seeds(const fgs_mlp *mlp, const float *rgb, const float *depth, int W, int H,
                                 const int32_t *seed_xy, const uint8_t *seed_hi, const int64_t *base, int64_t max_new,
                                 float alpha_h, float alpha_l, float fx, float fy, float max_dev, void *ws,
-                                size_t ws_bytes, GaussGrads g, cudaStream_t st);
+                                size_t ws_bytes, GaussGrads g, int32_t *d_status, cudaStream_t st);
 size_t prior_apply_workspace_size(int64_t max_new);
 
 struct SeedWs {
@@ -637,7 +637,7 @@ extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_g
   if (prior) {
     return prior_apply_to_seeds(prior, rgb_gt, depth_gt, W, H, a.seed_xy, w.seed_hi, w.base, prm->max_new,
                                 prm->alpha_h, prm->alpha_l, cam->fx, cam->fy, prm->prior_max_dev, w.prior,
-                                w.prior_bytes, gauss_grads(g), st);
+                                w.prior_bytes, gauss_grads(g), d_status, st);
   }
   return FGS_OK;
 }

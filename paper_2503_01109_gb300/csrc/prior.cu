@@ -5,8 +5,10 @@
 // MLP 272 -> 128 -> 128 -> 4 (GELU, erf form), BF16 operands, FP32 accumulation,
 // activations rounded to BF16 before each product.
 //
-// Every GEMM runs on the tensor cores with mma.sync m16n8k16 (BF16 in, FP32 out).
-// Operands stay row-major in shared memory (activations [rows][features],
+// Inference (the per-frame hot call) runs on tcgen05 with TMEM accumulators, in
+// prior_tc.cu.  The training step here uses mma.sync m16n8k16 (BF16 in, FP32
+// out): its small per-CTA batches (32 rows) and the three GEMM orientations of the
+// backward pass favour register fragments.  Operands stay row-major in shared memory (activations [rows][features],
 // weights [out][in]); ldmatrix (plain or .trans) builds each fragment, so the
 // forward (X W^T), the input gradients (dZ W) and the weight gradients (dZ^T H)
 // all read the same tiles.  Row strides are padded (280 / 136 / 24 halves) so the
@@ -238,12 +240,9 @@ __global__ void __launch_bounds__(256) k_features(const float *__restrict__ rgb,
 }
 
 // ---------------------------------------------------------------------------------
-// inference: persistent CTAs, weights staged once, 4 warps x 16 rows per tile
+// weights staged in shared memory (padded rows for conflict-free fragment loads)
 
-constexpr int kInferWarps = 4;
 constexpr size_t kWeightSmem = sizeof(uint16_t) * (kHid * kXS + kHid * kHS + 16 * kHS) + sizeof(float) * (2 * kHid + kOutP);
-constexpr size_t kInferSmem =
-    kWeightSmem + (size_t)kInferWarps * 16 * sizeof(uint16_t) * (kXS + 2 * kHS);
 
 __device__ __forceinline__ void carve_weights(char *base, MlpSmem &s) {
   s.w1 = reinterpret_cast<uint16_t *>(base);
@@ -252,38 +251,6 @@ __device__ __forceinline__ void carve_weights(char *base, MlpSmem &s) {
   s.b1 = reinterpret_cast<float *>(s.w3 + 16 * kHS);
   s.b2 = s.b1 + kHid;
   s.b3 = s.b2 + kHid;
-}
-
-__global__ void __launch_bounds__(32 * kInferWarps) k_infer(fgs_mlp m, const uint16_t *__restrict__ feat, int64_t n,
-                                                            const int64_t *d_count, float *__restrict__ out) {
-  extern __shared__ __align__(16) char smem[];
-  MlpSmem s;
-  carve_weights(smem, s);
-  load_weights(m, s);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint16_t *x = reinterpret_cast<uint16_t *>(smem + kWeightSmem) + warp * 16 * (kXS + 2 * kHS);
-  uint16_t *h1 = x + 16 * kXS, *h2 = h1 + 16 * kHS;
-  __syncthreads();
-  const int64_t live = d_count ? min(*d_count, n) : n;
-  for (int64_t r0 = ((int64_t)blockIdx.x * kInferWarps + warp) * 16; r0 < live;
-       r0 += (int64_t)gridDim.x * kInferWarps * 16) {
-    for (int e = lane; e < 16 * (kIn / 2); e += 32) {
-      const int r = e / (kIn / 2), c = (e - r * (kIn / 2)) * 2;
-      const int64_t row = r0 + r;
-      const uint32_t v = row < live ? *reinterpret_cast<const uint32_t *>(feat + row * kIn + c) : 0u;
-      *reinterpret_cast<uint32_t *>(x + r * kXS + c) = v;
-    }
-    __syncwarp();
-    float y[1][4];
-    warp_forward(s, x, h1, h2, nullptr, nullptr, y);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      int row, col;
-      frag_pos(0, e, row, col);
-      if (col < kOut && r0 + row < live) out[(r0 + row) * kOut + col] = y[0][e];
-    }
-    __syncwarp();
-  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -506,20 +473,20 @@ size_t prior_apply_workspace_size(int64_t max_new) {
   return align_up((size_t)max_new * kIn * 2) + align_up((size_t)max_new * kOut * 4);
 }
 
-static int infer_grid(int64_t n) {
-  const int64_t tiles = (n + 16 * kInferWarps - 1) / (16 * kInferWarps);
-  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, num_sms()));
-}
 
 static fgs_status set_smem(const void *fn, size_t bytes) {
   FGS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes), "prior smem");
   return FGS_OK;
 }
 
+// Inference on the tensor cores (prior_tc.cu).
+fgs_status launch_infer_tc(const fgs_mlp *mlp, const uint16_t *feat, int64_t n, const int64_t *d_count, float *out,
+                           int32_t *d_status, cudaStream_t st);
+
 fgs_status prior_apply_to_seeds(const fgs_mlp *mlp, const float *rgb, const float *depth, int W, int H,
                                 const int32_t *seed_xy, const uint8_t *seed_hi, const int64_t *base, int64_t max_new,
                                 float alpha_h, float alpha_l, float fx, float fy, float max_dev, void *ws,
-                                size_t ws_bytes, GaussGrads g, cudaStream_t st) {
+                                size_t ws_bytes, GaussGrads g, int32_t *d_status, cudaStream_t st) {
   if (max_new == 0) return FGS_OK;
   FGS_CHECK_ARG(ws_bytes >= prior_apply_workspace_size(max_new), "prior workspace");
   uint16_t *feat = static_cast<uint16_t *>(ws);
@@ -527,12 +494,12 @@ fgs_status prior_apply_to_seeds(const fgs_mlp *mlp, const float *rgb, const floa
   const int64_t *count = base + 1;
   k_features<<<(unsigned)std::min<int64_t>(max_new, 8 * num_sms()), 256, 0, st>>>(rgb, depth, W, H, seed_xy,
                                                                                  max_new, count, feat);
-  fgs_status s = set_smem((const void *)k_infer, kInferSmem);
+  count_launch();
+  fgs_status s = launch_infer_tc(mlp, feat, max_new, count, pred, d_status, st);
   if (s != FGS_OK) return s;
-  k_infer<<<infer_grid(max_new), 32 * kInferWarps, kInferSmem, st>>>(*mlp, feat, max_new, count, pred);
   k_apply_prior<<<(unsigned)((max_new + 255) / 256), 256, 0, st>>>(pred, seed_xy, seed_hi, base, depth, W, alpha_h,
                                                                   alpha_l, 0.5f * (fx + fy), max_dev, g);
-  count_launch(3);
+  count_launch();
   FGS_CHECK_LAUNCH("prior on seeds");
   return FGS_OK;
 }
@@ -563,16 +530,11 @@ extern "C" fgs_status fgs_prior_features(const float *rgb, const float *depth, i
 }
 
 extern "C" fgs_status fgs_prior_infer(const fgs_mlp *mlp, const uint16_t *features, int64_t n, float *out,
-                                      void *stream) {
+                                      int32_t *d_status, void *stream) {
   FGS_CHECK_ARG(n >= 0, "fgs_prior_infer: n < 0");
   if (n == 0) return FGS_OK;
   FGS_CHECK_ARG(mlp_ok(mlp) && features && out, "fgs_prior_infer: bad argument");
-  fgs_status s = set_smem((const void *)k_infer, kInferSmem);
-  if (s != FGS_OK) return s;
-  k_infer<<<infer_grid(n), 32 * kInferWarps, kInferSmem, as_stream(stream)>>>(*mlp, features, n, nullptr, out);
-  count_launch();
-  FGS_CHECK_LAUNCH("fgs_prior_infer");
-  return FGS_OK;
+  return launch_infer_tc(mlp, features, n, nullptr, out, d_status, as_stream(stream));
 }
 
 extern "C" fgs_status fgs_prior_train(fgs_mlp *mlp, fgs_mlp_master *master, const uint16_t *features,

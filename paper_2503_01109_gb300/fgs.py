@@ -112,6 +112,8 @@ _SIGS = {
     "fgs_bin_sort_workspace_size": ([c_void_p, c_int32, Tiling, c_int64, c_int64], c_size_t),
     "fgs_render_fwd": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p, c_void_p,
                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_render_fwd_sampled": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_int32,
+                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "fgs_render_bwd": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p, c_void_p,
                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "fgs_render_bwd_splats": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p,
@@ -160,7 +162,7 @@ _OPTIONAL = {
                          c_int32),
     "fgs_fourier_seed_workspace_size": ([c_int32, c_int32, c_int32], c_size_t),
     "fgs_prior_features": ([c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p], c_int32),
-    "fgs_prior_infer": ([c_void_p, c_void_p, c_int64, c_void_p, c_void_p], c_int32),
+    "fgs_prior_infer": ([c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p], c_int32),
     "fgs_prior_train": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_size_t,
                          c_void_p], c_int32),
     "fgs_prior_train_workspace_size": ([c_int64], c_size_t),
@@ -383,6 +385,17 @@ def fgs_render_fwd(proj: Projection, g: GaussianMap, cams: list, til: Tiling, id
                                 _ptr(tile_ranges), _ptr(frame.color), _ptr(frame.depth), _ptr(frame.alpha),
                                 _ptr(frame.t_final), _ptr(frame.n_contrib), _ptr(status), _stream()),
            "fgs_render_fwd")
+
+
+def fgs_render_fwd_sampled(proj: Projection, g: GaussianMap, cams: list, til: Tiling, ids, tile_ranges,
+                           frame: Frame, sample_stride: int = 2, status=None):
+    ps = proj.struct()
+    gs = g.struct()
+    _check(lib().fgs_render_fwd_sampled(ctypes.byref(ps), ctypes.byref(gs), camera_array(cams), len(cams), til,
+                                        _ptr(ids), _ptr(tile_ranges), int(sample_stride), _ptr(frame.color),
+                                        _ptr(frame.depth), _ptr(frame.alpha), _ptr(frame.t_final),
+                                        _ptr(frame.n_contrib), _ptr(status), _stream()),
+           "fgs_render_fwd_sampled")
 
 
 def fgs_render_bwd(g: GaussianMap, proj: Projection, cams: list, til: Tiling, ids, tile_ranges, frame: Frame,
@@ -654,8 +667,9 @@ def fgs_prior_features(rgb, depth, width: int, height: int, seed_xy, n: int, fea
                                     _ptr(features), _stream()), "fgs_prior_features")
 
 
-def fgs_prior_infer(mlp: MLP, features, n: int, out):
-    _check(lib().fgs_prior_infer(ctypes.byref(mlp), _ptr(features), int(n), _ptr(out), _stream()), "fgs_prior_infer")
+def fgs_prior_infer(mlp: MLP, features, n: int, out, status=None):
+    _check(lib().fgs_prior_infer(ctypes.byref(mlp), _ptr(features), int(n), _ptr(out), _ptr(status), _stream()),
+           "fgs_prior_infer")
 
 
 def fgs_prior_train(mlp: MLP, master: MLPMaster, features, targets, n: int, hp: TrainParams, loss_acc, ws):

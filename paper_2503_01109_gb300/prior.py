@@ -67,10 +67,11 @@ class PriorMLP:
         return fgs.MLPMaster(ms["w1"].data_ptr(), ms["b1"].data_ptr(), ms["w2"].data_ptr(), ms["b2"].data_ptr(),
                              ms["w3"].data_ptr(), ms["b3"].data_ptr(), self.m.data_ptr(), self.v.data_ptr())
 
-    def infer(self, features: torch.Tensor) -> torch.Tensor:
+    def infer(self, features: torch.Tensor, status: torch.Tensor | None = None) -> torch.Tensor:
+        """Predictions [n][4]; device errors are or-ed into `status` when given."""
         n = features.shape[0]
         out = torch.zeros(n, OUT, dtype=torch.float32, device=self.device)
-        fgs.fgs_prior_infer(self.mlp_struct(), features, n, out)
+        fgs.fgs_prior_infer(self.mlp_struct(), features, n, out, status)
         return out
 
     def train_step(self, features: torch.Tensor, targets: torch.Tensor, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -53,6 +53,32 @@ def test_mlp_forward_matches_oracle(cuda_device):
     assert np.median(np.abs(y.cpu().numpy() - ref)) < 1e-4
 
 
+@pytest.mark.parametrize("tiles_per_sm, tail", [(0, 5), (0, 128), (3, 77)])
+def test_mlp_forward_tile_walk(cuda_device, tiles_per_sm, tail):
+    """Row counts below one 128-row tile, exactly one tile, and several tiles per
+    persistent CTA plus a ragged tail: every row matches the oracle, rows past n
+    stay untouched, and no device wait gives up."""
+    n = tiles_per_sm * fgs.fgs_num_sms() * 128 + tail
+    rng = np.random.default_rng(n)
+    x = np.zeros((n, fgs.PRIOR_IN), np.float64)
+    x[:, :256] = rng.gamma(2.0, 0.7, (n, 256))       # log(1 + |F|) magnitudes
+    x[:, 256] = rng.uniform(0.5, 6.0, n)             # depth; 15 zero pad columns
+    bits = op.bf16_bits(x)
+    params = gp.init_params(5)
+    mlp = gp.PriorMLP(params)
+    sentinel = 12345.0
+    out = torch.full((n + 3, fgs.PRIOR_OUT), sentinel, dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    fgs.fgs_prior_infer(mlp.mlp_struct(), torch.as_tensor(bits.view(np.int16)).cuda(), n, out, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.all(got[n:] == sentinel)
+    ref = op.forward(params, op.from_bits(bits))["y"]
+    assert np.abs(got[:n] - ref).max() <= 2e-3 * (1 + np.abs(ref).max())
+    assert np.median(np.abs(got[:n] - ref)) < 1e-4
+
+
 def test_training_gradients_match_oracle(cuda_device):
     fr, xy = _frame_and_seeds(n=777, seed=2)
     f = _gpu_features(fr, xy)
