@@ -1,7 +1,7 @@
 // loss.cu -- the mapping loss of eq16 (L1 colour, L1 depth, 1 - SSIM), the scale
 // regulariser of eq15, and the Adam step of the map optimisation (Sec. III-D).
 //
-// The loss kernel runs one fused tile pass (loss_tile.cuh) per 16x16 output tile.
+// The loss kernel runs one fused tile pass (loss_tile.cuh) per 32x32 output tile.
 // Loss values are reduced per CTA into a workspace and summed in a fixed order by
 // one CTA, so the value is reproducible bit for bit.
 #include <cmath>
@@ -11,10 +11,22 @@
 
 namespace fgs {
 
-__global__ void __launch_bounds__(kLThreads) k_loss(LossArgs a) {
+constexpr int kLT = 32;          // loss tile side
+constexpr int kLThreads = 384;   // 12 warps: one pass of each 11-tap stage covers the tile
+constexpr size_t kLossSmem = sizeof(float) * LossGeom<kLT>::SmemFloats;  // 88 KB: two CTAs per SM
+
+__global__ void __launch_bounds__(kLThreads, 2) k_loss(LossArgs a) {
   pdl_enter();
   extern __shared__ float sm[];
-  loss_tile(a, blockIdx.x, sm);
+  loss_tile<kLT>(a, blockIdx.x, sm);
+}
+
+// Raises k_loss's dynamic shared-memory limit (a host-side attribute of the
+// current device's context; set on every call so that a new context gets it too).
+static fgs_status loss_smem_attr() {
+  FGS_CUDA(cudaFuncSetAttribute(k_loss, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLossSmem),
+           "fgs_loss: shared-memory attribute");
+  return FGS_OK;
 }
 
 // Sums `count` partials in a fixed order and adds the total to *d_loss.
@@ -202,11 +214,10 @@ extern "C" fgs_status fgs_loss(const fgs_camera *cams, int32_t n_views, const fl
     gs += g[i];
   }
   for (int i = 0; i < 11; ++i) a.g[i] = (float)(g[i] / gs);
-  const size_t smem = sizeof(float) * (2 * kLIn * kLIn + 5 * kLIn * kLMid + 5 * kLMid * kLMid);
-  static_assert(sizeof(float) * (2 * kLIn * kLIn + 5 * kLIn * kLMid + 5 * kLMid * kLMid) <= 48 * 1024,
-                "loss tile must fit the default dynamic shared-memory limit");
+  const fgs_status sa = loss_smem_attr();
+  if (sa != FGS_OK) return sa;
   cudaStream_t st = as_stream(stream);
-  pdl_launch(k_loss, blocks, kLThreads, smem, st, a);
+  pdl_launch(k_loss, blocks, kLThreads, kLossSmem, st, a);
   pdl_launch(k_reduce_partials, 1, 256, 0, st, a.partials, blocks, d_loss);
   count_launch(2);
   FGS_CHECK_LAUNCH("fgs_loss");
@@ -338,7 +349,7 @@ extern "C" fgs_status fgs_loss_noalloc(const fgs_camera *cams, int32_t n_views, 
   int blocks = 0;
   if (!loss_views(cams, n_views, &a.lv, &blocks, "fgs_loss_noalloc")) return FGS_ERR_INVALID_ARGUMENT;
   if (blocks > FGS_LOSS_NOALLOC_MAX_TILES) {
-    set_error("fgs_loss_noalloc: %d loss tiles (16x16 px) exceed the built-in scratch of %d tiles; "
+    set_error("fgs_loss_noalloc: %d loss tiles (32x32 px) exceed the built-in scratch of %d tiles; "
               "use fgs_loss with a workspace",
               blocks, FGS_LOSS_NOALLOC_MAX_TILES);
     return FGS_ERR_CAPACITY;
@@ -362,9 +373,10 @@ extern "C" fgs_status fgs_loss_noalloc(const fgs_camera *cams, int32_t n_views, 
     gs += g[i];
   }
   for (int i = 0; i < 11; ++i) a.g[i] = (float)(g[i] / gs);
-  const size_t smem = sizeof(float) * (2 * kLIn * kLIn + 5 * kLIn * kLMid + 5 * kLMid * kLMid);
+  const fgs_status sa = loss_smem_attr();
+  if (sa != FGS_OK) return sa;
   cudaStream_t st = as_stream(stream);
-  pdl_launch(k_loss, blocks, kLThreads, smem, st, a);
+  pdl_launch(k_loss, blocks, kLThreads, kLossSmem, st, a);
   pdl_launch(k_reduce_partials, 1, 256, 0, st, scratch, blocks, d_loss);
   count_launch(2);
   FGS_CHECK_LAUNCH("fgs_loss_noalloc");

@@ -19,11 +19,11 @@
 namespace fgs {
 
 
-template <int TW, int TH, int BATCH, int PX>
-__global__ void __launch_bounds__(TW *TH / PX) k_render_fwd(RenderArgs a) {
+template <int TW, int TH, int BATCH, int PX, int S = 1>
+__global__ void __launch_bounds__((TW / S) * (TH / S) / PX) k_render_fwd(RenderArgs a) {
   pdl_enter();
   __shared__ __align__(16) char smem[TileSmem<BATCH>::fwd];
-  render_fwd_tile<TW, TH, BATCH, PX>(a, blockIdx.x, smem);
+  render_fwd_tile<TW, TH, BATCH, PX, S>(a, blockIdx.x, smem);
 }
 
 #ifndef FGS_BWD_MINB
@@ -40,6 +40,11 @@ template <int TW, int TH, int BATCH>
 static void launch_fwd(const RenderArgs &a, int blocks, cudaStream_t st) {
   constexpr int PX = PxPerThread<TW, TH>::fwd;
   pdl_launch(k_render_fwd<TW, TH, BATCH, PX>, blocks, TW * TH / PX, 0, st, a);
+}
+// The forward on the grid of every second pixel in x and y (one pixel per thread).
+template <int TW, int TH, int BATCH>
+static void launch_fwd_sampled(const RenderArgs &a, int blocks, cudaStream_t st) {
+  pdl_launch(k_render_fwd<TW, TH, BATCH, 1, 2>, blocks, (TW / 2) * (TH / 2), 0, st, a);
 }
 template <int TW, int TH, int BATCH>
 static void launch_bwd(const RenderBwdArgs &a, int blocks, cudaStream_t st) {
@@ -94,6 +99,42 @@ extern "C" fgs_status fgs_render_fwd(const fgs_projected *proj, const fgs_gaussi
   FGS_DISPATCH_TILING(tiling, launch_fwd, a, vs.total_tiles, as_stream(stream));
   count_launch();
   FGS_CHECK_LAUNCH("fgs_render_fwd");
+  return FGS_OK;
+}
+
+extern "C" fgs_status fgs_render_fwd_sampled(const fgs_projected *proj, const fgs_gaussians *g,
+                                             const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
+                                             const int32_t *ids, const int32_t *tile_ranges, int32_t sample_stride,
+                                             float *color, float *depth, float *alpha, float *t_final,
+                                             int32_t *n_contrib, int32_t *d_status, void *stream) {
+  (void)d_status;
+  FGS_CHECK_ARG(proj && proj->splat, "fgs_render_fwd_sampled: NULL projection");
+  if (!gaussians_ok(g, "g")) return FGS_ERR_INVALID_ARGUMENT;
+  FGS_CHECK_ARG(tiling_ok(tiling), "fgs_render_fwd_sampled: unsupported tiling");
+  FGS_CHECK_ARG(sample_stride == 2, "fgs_render_fwd_sampled: sample_stride must be 2");
+  FGS_CHECK_ARG(tiling.tile_w == 16, "fgs_render_fwd_sampled: needs 16x16 or 16x32 tiles");
+  FGS_CHECK_ARG(ids && tile_ranges && color && depth && alpha && t_final && n_contrib,
+                "fgs_render_fwd_sampled: NULL argument");
+  FGS_CHECK_ARG((reinterpret_cast<uintptr_t>(proj->splat) & 15) == 0, "fgs_render_fwd_sampled: splat alignment");
+  DevViews vs;
+  if (!make_views(cams, n_views, tiling.tile_w, tiling.tile_h, &vs)) return FGS_ERR_INVALID_ARGUMENT;
+  RenderArgs a{vs, reinterpret_cast<const float4 *>(proj->splat), proj->stride, g->rgb, g->capacity, ids,
+               reinterpret_cast<const int2 *>(tile_ranges), color, depth, alpha, t_final, n_contrib};
+  cudaStream_t st = as_stream(stream);
+  const int bd = tiling.batch_depth, blocks = vs.total_tiles;
+  if (tiling.tile_h == 16) {
+    if (bd == 32) launch_fwd_sampled<16, 16, 32>(a, blocks, st);
+    else if (bd == 64) launch_fwd_sampled<16, 16, 64>(a, blocks, st);
+    else if (bd == 128) launch_fwd_sampled<16, 16, 128>(a, blocks, st);
+    else launch_fwd_sampled<16, 16, 256>(a, blocks, st);
+  } else {
+    if (bd == 32) launch_fwd_sampled<16, 32, 32>(a, blocks, st);
+    else if (bd == 64) launch_fwd_sampled<16, 32, 64>(a, blocks, st);
+    else if (bd == 128) launch_fwd_sampled<16, 32, 128>(a, blocks, st);
+    else launch_fwd_sampled<16, 32, 256>(a, blocks, st);
+  }
+  count_launch();
+  FGS_CHECK_LAUNCH("fgs_render_fwd_sampled");
   return FGS_OK;
 }
 

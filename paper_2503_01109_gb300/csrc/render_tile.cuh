@@ -62,11 +62,15 @@ struct TileSmem {
   static constexpr int bwd = 48 * BATCH + 4 * BATCH + 40 * BATCH + 16;
 };
 
-// Forward of global tile t by the whole CTA (TW * TH / PX threads); `smem` holds
-// TileSmem<BATCH>::fwd bytes, 16-byte aligned.
-template <int TW, int TH, int BATCH, int PX>
+// Forward of global tile t by the whole CTA ((TW / S) * (TH / S) / PX threads);
+// `smem` holds TileSmem<BATCH>::fwd bytes, 16-byte aligned.  S > 1 blends only the
+// pixels with x % S == 0 and y % S == 0 (the same arithmetic per pixel, so the
+// same values there) and writes the background (colour, depth and alpha 0,
+// t_final 1, n_contrib 0) to the other pixels of the tile.
+template <int TW, int TH, int BATCH, int PX, int S = 1>
 __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int t, char *smem) {
-  constexpr int NT = TW * TH / PX;
+  static_assert(TW % S == 0 && TH % S == 0, "the sample grid must tile the tile");
+  constexpr int NT = (TW / S) * (TH / S) / PX;
   float4 *s_g0 = reinterpret_cast<float4 *>(smem);  // mean2d x, y, conic a, b
   float4 *s_g1 = s_g0 + BATCH;                       // conic c, opacity, depth, -
   float4 *s_rgb = s_g1 + BATCH;
@@ -75,9 +79,9 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int t, char
   const int lt = t - cm.tile_base;
   const int ty = lt / cm.tiles_x, tx = lt - ty * cm.tiles_x;
   int lx, ly0;
-  thread_pixel<TW, TH, PX>(lx, ly0);
-  const int px = tx * TW + lx;
-  const int py0 = ty * TH + ly0;
+  thread_pixel<TW / S, TH / S, PX>(lx, ly0);
+  const int px = tx * TW + S * lx;
+  const int py0 = ty * TH + S * ly0;  // the thread's rows: py0 + S q
   const float fpx = (float)px;
   const int2 range = a.ranges[t];
   const int n = range.y - range.x;
@@ -92,7 +96,7 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int t, char
     T[q] = 1.f;
     C0[q] = C1[q] = C2[q] = D[q] = A[q] = 0.f;
     last[q] = 0;
-    done[q] = !(px < cm.W && py0 + q < cm.H);
+    done[q] = !(px < cm.W && py0 + S * q < cm.H);
     all_done = all_done && done[q];
   }
   for (int base = 0; base < n; base += BATCH) {
@@ -142,7 +146,7 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int t, char
             if (done[q]) continue;
             any_live = true;
             float dx, dy;
-            const float power2 = splat_power2(g0.x, g0.y, g0.z, g0.w, g1.x, fpx, (float)(py0 + q), dx, dy);
+            const float power2 = splat_power2(g0.x, g0.y, g0.z, g0.w, g1.x, fpx, (float)(py0 + S * q), dx, dy);
             if (power2 > 0.f || power2 < g1.w) continue;
             const float alpha = fminf(kAlphaMax, __fmul_rn(g1.y, ex2_approx(power2)));
             const float Tn = T[q] * (1.f - alpha);
@@ -172,16 +176,23 @@ __device__ __forceinline__ void render_fwd_tile(const RenderArgs &a, int t, char
   float *col = a.color + 3 * cm.pix_base;
 #pragma unroll
   for (int q = 0; q < PX; ++q) {
-    const int py = py0 + q;
-    if (px < cm.W && py < cm.H) {
-      const int64_t pix = (int64_t)py * cm.W + px;
-      col[pix] = C0[q];
-      col[HW + pix] = C1[q];
-      col[2 * HW + pix] = C2[q];
-      a.depth[cm.pix_base + pix] = D[q];
-      a.alpha[cm.pix_base + pix] = A[q];
-      a.t_final[cm.pix_base + pix] = T[q];
-      a.n_contrib[cm.pix_base + pix] = last[q];
+#pragma unroll
+    for (int sy = 0; sy < S; ++sy) {
+#pragma unroll
+      for (int sx = 0; sx < S; ++sx) {
+        const bool sample = sx == 0 && sy == 0;
+        const int x = px + sx, py = py0 + S * q + sy;
+        if (x < cm.W && py < cm.H) {
+          const int64_t pix = (int64_t)py * cm.W + x;
+          col[pix] = sample ? C0[q] : 0.f;
+          col[HW + pix] = sample ? C1[q] : 0.f;
+          col[2 * HW + pix] = sample ? C2[q] : 0.f;
+          a.depth[cm.pix_base + pix] = sample ? D[q] : 0.f;
+          a.alpha[cm.pix_base + pix] = sample ? A[q] : 0.f;
+          a.t_final[cm.pix_base + pix] = sample ? T[q] : 1.f;
+          a.n_contrib[cm.pix_base + pix] = sample ? last[q] : 0;
+        }
+      }
     }
   }
 }

@@ -88,6 +88,10 @@ __device__ __forceinline__ int claim(uint32_t *counter, int *s_item) {
   return *s_item;
 }
 
+// Loss tile side inside the window: 16, so that the loss phase's shared memory
+// (38 KB) stays below the render phases' and does not lower the grid's residency.
+constexpr int kWinLT = 16;
+
 template <int TW, int TH, int BATCH>
 __global__ void __launch_bounds__(TW *TH / 2) k_window(WindowArgs w) {
   extern __shared__ __align__(16) char smem[];
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(TW *TH / 2) k_window(WindowArgs w) {
   for (;;) {
     const int t = claim(w.ctl + 1, &s_item);
     if (t >= w.n_loss_tiles) break;
-    loss_tile(w.l, t, reinterpret_cast<float *>(smem));
+    loss_tile<kWinLT>(w.l, t, reinterpret_cast<float *>(smem));
   }
   if (!grid_barrier(w, &s_flag)) return;
   for (;;) {
@@ -127,7 +131,7 @@ __global__ void k_window_reduce(const double *__restrict__ partials, int64_t cou
 template <int TW, int TH, int BATCH>
 static size_t window_smem() {
   size_t s = std::max<size_t>(TileSmem<BATCH>::fwd, TileSmem<BATCH>::bwd);
-  return std::max<size_t>(s, sizeof(float) * kLossSmemFloats);
+  return std::max<size_t>(s, sizeof(float) * LossGeom<kWinLT>::SmemFloats);
 }
 
 template <int TW, int TH, int BATCH>
@@ -174,10 +178,10 @@ static bool window_loss_views(const fgs_camera *cams, int32_t n_views, LossViews
   for (int v = 0; v < n_views; ++v) {
     lv->v[v].W = cams[v].width;
     lv->v[v].H = cams[v].height;
-    lv->v[v].tiles_x = (cams[v].width + kLT - 1) / kLT;
+    lv->v[v].tiles_x = (cams[v].width + kWinLT - 1) / kWinLT;
     lv->v[v].tile_base = t;
     lv->v[v].pix_base = pix;
-    t += lv->v[v].tiles_x * ((cams[v].height + kLT - 1) / kLT);
+    t += lv->v[v].tiles_x * ((cams[v].height + kWinLT - 1) / kWinLT);
     pix += (int64_t)cams[v].width * cams[v].height;
   }
   *tiles = t;

@@ -80,16 +80,16 @@ class TimedMapper(Mapper):
         self.nc_snap = []          # (render belongs to an iteration, n_contrib copy)
         self._in_iteration = False
 
-    def render(self):
+    def render(self, sample_stride: int = 1):
         with self.timer.span("project"):
             fgs.fgs_project(self.g, self.cams, self.til, self.proj, self.status, self.use_dc)
         n = self.g.capacity if self.use_dc else self.g.n
         with self.timer.span("bin_sort"):
             fgs.fgs_bin_sort(self.proj, n, self.cams, self.til, self.ws_bin, self.tile_keys, self.ids, self.ranges,
                              self.num_pairs, self.status)
-        with self.timer.span("render_fwd"):
-            fgs.fgs_render_fwd(self.proj, self.g, self.cams, self.til, self.ids, self.ranges, self.frame, self.status)
-        if self.timer.on:
+        with self.timer.span("render_fwd" if sample_stride == 1 else "render_fwd_sampled"):
+            self._blend(sample_stride)
+        if self.timer.on and sample_stride == 1:  # the roofline covers the full-frame renders
             snap = torch.empty_like(self.frame.n_contrib)
             fgs.fgs_memcpy_async(snap, self.frame.n_contrib)   # copy engine; summed after timing
             self.nc_snap.append((self._in_iteration, snap))

@@ -79,13 +79,25 @@ class Mapper:
         self.cams = list(cams)
         self.frame.cams = self.cams
 
-    def render(self):
-        """a1-a5: project, bin + sort, blend."""
+    def render(self, sample_stride: int = 1):
+        """a1-a5: project, bin + sort, blend (on every second pixel in x and y when
+        sample_stride is 2; the other pixels get the background)."""
         fgs.fgs_project(self.g, self.cams, self.til, self.proj, self.status, self.use_dc)
         n = self.g.capacity if self.use_dc else self.g.n
         fgs.fgs_bin_sort(self.proj, n, self.cams, self.til, self.ws_bin, self.tile_keys, self.ids, self.ranges,
                          self.num_pairs, self.status)
-        fgs.fgs_render_fwd(self.proj, self.g, self.cams, self.til, self.ids, self.ranges, self.frame, self.status)
+        self._blend(sample_stride)
+
+    def _blend(self, sample_stride: int):
+        if sample_stride == 1:
+            fgs.fgs_render_fwd(self.proj, self.g, self.cams, self.til, self.ids, self.ranges, self.frame, self.status)
+        else:
+            fgs.fgs_render_fwd_sampled(self.proj, self.g, self.cams, self.til, self.ids, self.ranges, self.frame,
+                                       sample_stride, self.status)
+
+    def can_sample(self, stride: int) -> bool:
+        """Whether render(sample_stride=stride) is available for this tiling."""
+        return stride == 1 or (stride == 2 and self.til.tile_w == 16)
 
     def backward(self, dC, dD, dA=None):
         """a7-a8 into self.grads (cleared first)."""

@@ -29,12 +29,21 @@ class Seeder:
         self.seed_xy = torch.zeros(max(self.params.max_new, 1), 2, dtype=torch.int32, device=dev)
         self.threshold = torch.zeros(1, dtype=torch.int32, device=dev)
 
-    def seed_frame(self, color_gt, depth_gt, cam: dict, render_first: bool = True, first_frame: bool = False):
-        """Render the map at `cam` (eq1 colour, depth, opacity), then seed."""
+    def sample_stride(self) -> int:
+        """2 when every seed pixel (the m- and n-grids of eq10) has even x and y and
+        the tiling allows it: the render at the frame's pose is then needed there
+        only (fgs_render_fwd_sampled), else 1."""
+        p = self.params
+        return 2 if (p.m % 2 == 0 and p.n % 2 == 0 and self.mapper.can_sample(2)) else 1
+
+    def seed_frame(self, color_gt, depth_gt, cam: dict, render_first: bool = True, first_frame: bool = False,
+                   full_render: bool = False):
+        """Render the map at `cam` (eq1 colour, depth, opacity) on the seed grid (every
+        pixel when full_render or the grid is not even), then seed."""
         m = self.mapper
         m.set_cameras([cam])
         if render_first and not first_frame:
-            m.render()
+            m.render(1 if full_render else self.sample_stride())
         f = m.frame
         mlp = None if self.prior is None else self.prior.mlp_struct()
         fgs.fgs_fourier_seed(color_gt, depth_gt, None if first_frame else f.color, None if first_frame else f.depth,

@@ -181,9 +181,14 @@ def test_autograd_function_uses_the_adjoint(cuda_device):
     assert not bad.any()
 
 
-def test_loss_matches_oracle(cuda_device):
+@pytest.mark.parametrize("sizes, weights", [
+    ([(70, 45), (33, 20)], (0.9, 0.1, 0.1)),      # two views, ragged 32x32 loss tiles
+    ([(200, 130)], (0.9, 0.1, 0.1)),              # 7 x 5 tiles: interior tile seams both ways
+    ([(70, 45)], (0.9, 0.1, 0.0)),                # no SSIM term: L1 colour and depth only
+])
+def test_loss_matches_oracle(cuda_device, sizes, weights):
     rng = np.random.default_rng(0)
-    cams = [syn.pinhole(70, 45, 60.0), syn.pinhole(33, 20, 40.0)]
+    cams = [syn.pinhole(w, h, 0.8 * w) for w, h in sizes]
     Cs = [rng.uniform(0, 1, (3, c["height"], c["width"])) for c in cams]
     Cg = [rng.uniform(0, 1, (3, c["height"], c["width"])) for c in cams]
     Ds = [rng.uniform(1, 3, (c["height"], c["width"])) for c in cams]
@@ -195,13 +200,13 @@ def test_loss_matches_oracle(cuda_device):
     dD = torch.zeros_like(depth)
     acc = torch.zeros(1, device="cuda")
     ws = fgs.ws_tensor(fgs.fgs_loss_workspace_size(cams))
-    fgs.fgs_loss(cams, color, depth, color_gt, depth_gt, 0.9, 0.1, 0.1, dC, dD, acc, ws)
+    fgs.fgs_loss(cams, color, depth, color_gt, depth_gt, *weights, dC, dD, acc, ws)
     torch.cuda.synchronize()
     Lref, off, offp = 0.0, 0, 0
     for v, c in enumerate(cams):
         H, W = c["height"], c["width"]
         C32 = [x.astype(np.float32) for x in (Cs[v], Ds[v], Cg[v], Dg[v])]
-        L, rdC, rdD = orr.loss(*C32, 0.9, 0.1, 0.1)
+        L, rdC, rdD = orr.loss(*C32, *weights)
         Lref += L
         gdc = dC[off:off + 3 * H * W].cpu().numpy().reshape(3, H, W)
         gdd = dD[offp:offp + H * W].cpu().numpy().reshape(H, W)

@@ -68,7 +68,7 @@ def test_noalloc_loss_matches_workspace_loss_twice_in_a_row():
 
 
 def test_noalloc_loss_rejects_view_sets_beyond_its_scratch():
-    cams = [syn.pinhole(4096, 4096, 1000.0)] * 2      # 2 x 65536 loss tiles > 65536
+    cams = [syn.pinhole(4096, 4096, 1000.0)] * 8      # 8 x 16384 loss tiles (32x32 px) > 65536
     dummy = torch.zeros(16, device="cuda")
     p = fgs.LossParams(0.9, 0.1, 0.1)
     rc = fgs.lib().fgs_loss_noalloc(fgs.camera_array(cams), len(cams), fgs._ptr(dummy), fgs._ptr(dummy),
