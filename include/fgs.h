@@ -149,9 +149,11 @@ int64_t fgs_num_tiles(const fgs_camera *cams, int32_t n_views, fgs_tiling tiling
  * Device errors: FGS_DEV_PAIR_OVERFLOW when the pair count, or the count of
  *   (record, tile row) entries of the rows' lists, exceeds pair_capacity;
  *   *d_num_pairs then holds the required count (for the rows: a lower bound) and
- *   the lists are not valid.
+ *   the lists are not valid.  The compaction and the depth sort chain their tiles
+ *   through decoupled look-backs whose waits are bounded (1 s): one that gives up
+ *   sets FGS_DEV_TIMEOUT and the lists are not valid.
  * err: INVALID_ARGUMENT for small workspace, pair_capacity outside 1..2^31-1, more
- *   than 4096 tile rows over all views. */
+ *   than 4096 tile rows over all views, n_views * n above 2^30 - 1. */
 fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const fgs_camera *cams,
                         int32_t n_views, fgs_tiling tiling, void *ws, size_t ws_bytes,
                         uint32_t *tile_keys, int32_t *ids, int64_t pair_capacity,

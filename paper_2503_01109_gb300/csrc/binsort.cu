@@ -9,10 +9,11 @@
 // tiles their support ellipse reaches -- write every pair straight to its place
 // in (tile, depth, id) order.
 //
-// The radix sort is LSD, 8-bit digits, reduce-then-scan: an upsweep histogram per
-// block chunk, a per-digit scan of the blocks' counts, and a downsweep that
-// ranks 2048-item tiles stably with per-bit warp ballots, reorders them in shared
-// memory and writes each digit run coalesced.  Every count the kernels need lives
+// The radix sort is LSD with 8-bit digits in one sweep per pass: one kernel
+// histograms every pass's digits, then each pass is one kernel whose CTAs rank a
+// 2048-item tile stably with per-bit warp ballots, learn the counts of the earlier
+// tiles by a decoupled look-back (bounded waits), reorder the tile in shared
+// memory and write each digit run coalesced.  Every count the kernels need lives
 // on the device, so the whole binning can be captured in a CUDA graph.
 #include "common.cuh"
 
@@ -21,23 +22,13 @@ namespace fgs {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
-constexpr int kSortMaxBlocks = 1024;
-constexpr int kScanThreads = 1024;  // also the largest block count of a sort pass
+constexpr int kSortMaxPasses = 4;
 
 __device__ __forceinline__ uint32_t item_count(const int64_t *d_count, int64_t host_count, int64_t cap) {
   int64_t c = d_count ? *d_count : host_count;
   if (c > cap) c = cap;
   if (c < 0) c = 0;
   return (uint32_t)c;
-}
-
-__device__ __forceinline__ void block_chunk(uint32_t count, uint32_t nb, uint32_t b, uint32_t &lo,
-                                            uint32_t &hi) {
-  uint32_t tiles = (count + kSortTile - 1) / kSortTile;
-  uint32_t per = (tiles + nb - 1) / nb;
-  uint64_t l = (uint64_t)b * per * kSortTile, h = l + (uint64_t)per * kSortTile;
-  lo = (uint32_t)(l < count ? l : count);
-  hi = (uint32_t)(h < count ? h : count);
 }
 
 // Lanes of the warp whose digit (the low `nbits` bits of d) equals this lane's,
@@ -80,180 +71,236 @@ __device__ __forceinline__ uint32_t block_scan256(uint32_t x, uint32_t *s_warp, 
   return before + incl - x;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
-                                                                const int64_t *d_count, int64_t host_count,
-                                                                int64_t cap, int shift, int nbits,
-                                                                uint32_t *__restrict__ counts) {
+// Digit histograms of every pass in one sweep over the keys: hist[p][d] = items
+// whose digit p ((key >> 8 p) & 255, the last pass masked to its bits) is d.
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t *__restrict__ keys,
+                                                            const int64_t *d_count, int64_t host_count,
+                                                            int64_t cap, int bits, uint32_t *__restrict__ hist) {
   pdl_enter();
-  __shared__ uint32_t hist[kSortThreads / 32][256];
-  const int warp = threadIdx.x >> 5;
-  for (int d = threadIdx.x & 31; d < 256; d += 32) hist[warp][d] = 0;
+  __shared__ uint32_t h[kSortMaxPasses][256];
+  for (int i = threadIdx.x; i < kSortMaxPasses * 256; i += kSortThreads) (&h[0][0])[i] = 0;
   __syncthreads();
+  const int passes = (bits + 7) / 8;
   const uint32_t count = item_count(d_count, host_count, cap);
-  uint32_t lo, hi;
-  block_chunk(count, gridDim.x, blockIdx.x, lo, hi);
-  const int lane = threadIdx.x & 31;
-  // kSortItems keys per thread in flight, warp-striped like the downsweep
-  for (uint32_t tile = lo; tile < hi; tile += kSortTile) {
-    uint32_t d[kSortItems];
-    bool valid[kSortItems];
+  const uint32_t stride = gridDim.x * kSortThreads;
+  // every lane walks the same number of rounds, so the warp-wide match below is safe
+  const uint32_t rounds = (count + stride - 1) / stride;
+  uint32_t i = blockIdx.x * kSortThreads + threadIdx.x;
+  for (uint32_t r = 0; r < rounds; ++r, i += stride) {
+    const bool valid = i < count;
+    const uint32_t k = valid ? keys[i] : 0u;
 #pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-      const uint32_t i = tile + warp * (32 * kSortItems) + it * 32 + lane;
-      valid[it] = i < hi;
-      d[it] = valid[it] ? (keys[i] >> shift) & 255u : 0u;
-    }
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-      const uint32_t peers = digit_peers(d[it], valid[it], nbits);
-      if (valid[it] && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][d[it]], (uint32_t)__popc(peers));
+    for (int p = 0; p < kSortMaxPasses; ++p) {
+      if (p < passes) {
+        const int nb = min(8, bits - 8 * p);
+        const uint32_t d = (k >> (8 * p)) & ((1u << nb) - 1u);
+        // lanes with the same digit add once (the high digits repeat across the warp)
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0xFFFFFFFFu);
+        if (valid && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+      }
     }
   }
   __syncthreads();
-  uint32_t s = 0;
-#pragma unroll
-  for (int w = 0; w < kSortThreads / 32; ++w) s += hist[w][threadIdx.x];
-  counts[threadIdx.x * gridDim.x + blockIdx.x] = s;  // digit-major
+  for (int e = threadIdx.x; e < passes * 256; e += kSortThreads) {
+    const uint32_t c = (&h[0][0])[e];
+    if (c) atomicAdd(hist + e, c);
+  }
 }
 
-// Per-digit exclusive scan over the blocks' counts (one CTA per digit, nb <= 1024),
-// in place; digit_total[d] receives the digit's item count.
-__global__ void __launch_bounds__(kScanThreads) k_digit_scan(uint32_t *__restrict__ counts, int nb,
-                                                             uint32_t *__restrict__ digit_total) {
-  pdl_enter();
-  __shared__ uint32_t warp_sum[kScanThreads / 32];
-  const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t *row = counts + (size_t)d * nb;
-  const uint32_t c = threadIdx.x < nb ? row[threadIdx.x] : 0u;
-  uint32_t incl = c;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) warp_sum[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const uint32_t w = warp_sum[lane];
-    uint32_t wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += t;
-    }
-    warp_sum[lane] = wi - w;
-    if (lane == 31) digit_total[d] = wi;
-  }
-  __syncthreads();
-  if (threadIdx.x < nb) row[threadIdx.x] = warp_sum[warp] + incl - c;
+// Look-back flags: one word per (tile, digit), the tile's count of the digit in
+// the low 30 bits and its state in the top two: 0 not yet known, kFlagAgg the
+// tile's own count, kFlagPrefix the count of this and every earlier tile.
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kFlagValue = (1u << 30) - 1u;
+constexpr uint64_t kLookbackTimeoutNs = 1000000000ull;  // 1 s
+constexpr int kLookback = 32;  // earlier tiles read per look-back step (loads in flight per thread)
+
+__device__ __forceinline__ uint32_t ld_flag(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_flag(uint32_t *p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t sort_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
-    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-    uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const int64_t *d_count,
-    int64_t host_count, int64_t cap, int shift, int nbits, const uint32_t *__restrict__ offsets,
-    const uint32_t *__restrict__ digit_total) {
+// One stable LSD pass over the digit (key >> shift) & (2^nbits - 1).  Each CTA
+// takes the next 2048-item tile by ticket (so every tile it waits for belongs to
+// a CTA that is already running), ranks the tile stably with per-bit warp ballots,
+// publishes its digit counts, and adds up the counts of the earlier tiles by a
+// decoupled look-back: thread d reads the flags of kLookback earlier tiles at a
+// time for digit d, summing own counts until it meets a running prefix.  A flag that
+// stays unknown for kLookbackTimeoutNs sets FGS_DEV_TIMEOUT (the pass's output is
+// then invalid) and the CTA goes on.  The tile is reordered in shared memory and
+// each digit run is written out coalesced.
+__global__ void __launch_bounds__(kSortThreads) k_sort_pass(
+    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
+    uint32_t *__restrict__ vals_out, const int64_t *d_count, int64_t host_count, int64_t cap, int shift, int nbits,
+    const uint32_t *__restrict__ hist, uint32_t *__restrict__ flags, uint32_t *__restrict__ ticket,
+    int32_t *d_status) {
   pdl_enter();
   constexpr int W = kSortThreads / 32;
   __shared__ uint32_t s_whist[W][256];  // per warp and digit: count, then the warp's offset in the tile's run
-  __shared__ uint32_t s_base[256];      // output position of this block's next item of each digit
+  __shared__ uint32_t s_base[256];      // output position of the tile's first item of each digit
   __shared__ uint32_t s_prefix[256];    // start of each digit's run in the reordered tile
   __shared__ uint32_t s_warp[W];
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const uint32_t count = item_count(d_count, host_count, cap);
-  uint32_t lo, hi;
-  block_chunk(count, gridDim.x, blockIdx.x, lo, hi);
-  // start of each digit in the output, plus this block's offset inside the digit
-  {
-    uint32_t all;
-    const uint32_t start = block_scan256(digit_total[threadIdx.x], s_warp, all);
-    s_base[threadIdx.x] = start + offsets[threadIdx.x * gridDim.x + blockIdx.x];
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  for (int d = lane; d < 256; d += 32) s_whist[warp][d] = 0;
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint32_t lo = t * (uint32_t)kSortTile;
+  if (lo >= count) return;  // past the last tile (the whole CTA)
+  const uint32_t hi = min(count, lo + (uint32_t)kSortTile);
+  uint32_t k[kSortItems], v[kSortItems], local[kSortItems], dig[kSortItems];
+  bool valid[kSortItems];
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    const uint32_t idx = lo + warp * (32 * kSortItems) + it * 32 + lane;
+    valid[it] = idx < hi;
+    k[it] = valid[it] ? keys_in[idx] : 0u;
+    v[it] = valid[it] ? vals_in[idx] : 0u;
+    dig[it] = (k[it] >> shift) & ((1u << nbits) - 1u);
+  }
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    const uint32_t peers = digit_peers(dig[it], valid[it], nbits);
+    uint32_t base = 0;
+    if (valid[it]) base = s_whist[warp][dig[it]];
+    __syncwarp();
+    if (valid[it] && lane == __ffs(peers) - 1) s_whist[warp][dig[it]] = base + __popc(peers);
+    __syncwarp();
+    local[it] = base + __popc(peers & lt_mask);
   }
   __syncthreads();
-  for (uint32_t tile = lo; tile < hi; tile += kSortTile) {
-    for (int d = lane; d < 256; d += 32) s_whist[warp][d] = 0;
-    __syncwarp();
-    uint32_t k[kSortItems], v[kSortItems], local[kSortItems], dig[kSortItems];
-    bool valid[kSortItems];
+  const int d = threadIdx.x;  // this thread's digit
+  uint32_t run = 0;           // items of digit d in the tile
 #pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-      const uint32_t idx = tile + warp * (32 * kSortItems) + it * 32 + lane;
-      valid[it] = idx < hi;
-      k[it] = valid[it] ? keys_in[idx] : 0u;
-      v[it] = valid[it] ? vals_in[idx] : 0u;
-      dig[it] = (k[it] >> shift) & 255u;
-    }
+  for (int w = 0; w < W; ++w) {
+    const uint32_t c = s_whist[w][d];
+    s_whist[w][d] = run;
+    run += c;
+  }
+  uint32_t *my_flags = flags + (size_t)t * 256;
+  st_flag(my_flags + d, (t == 0 ? kFlagPrefix : kFlagAgg) | run);
+  uint32_t tile_items, all;
+  s_prefix[d] = block_scan256(run, s_warp, tile_items);
+  __syncthreads();
+  const uint32_t digit_start = block_scan256(hist[d], s_warp, all);
+  // look-back over the earlier tiles for digit d
+  uint32_t excl = 0;
+  if (t > 0) {
+    int64_t j = (int64_t)t - 1;
+    const uint64_t t0 = sort_ns();
+    for (;;) {
+      uint32_t f[kLookback];
 #pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-      const uint32_t peers = digit_peers(dig[it], valid[it], nbits);
-      uint32_t base = 0;
-      if (valid[it]) base = s_whist[warp][dig[it]];
-      __syncwarp();
-      if (valid[it] && lane == __ffs(peers) - 1) s_whist[warp][dig[it]] = base + __popc(peers);
-      __syncwarp();
-      local[it] = base + __popc(peers & lt_mask);
-    }
-    __syncthreads();
-    uint32_t run = 0;  // this thread's digit: items in the tile
+      for (int q = 0; q < kLookback; ++q)
+        f[q] = j - q >= 0 ? ld_flag(flags + (size_t)(j - q) * 256 + d) : kFlagPrefix;
+      int q = 0;
+      bool done = false;
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-      const uint32_t c = s_whist[w][threadIdx.x];
-      s_whist[w][threadIdx.x] = run;
-      run += c;
-    }
-    uint32_t tile_items;
-    s_prefix[threadIdx.x] = block_scan256(run, s_warp, tile_items);
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-      if (valid[it]) {
-        const uint32_t pos = s_prefix[dig[it]] + s_whist[warp][dig[it]] + local[it];
-        s_keys[pos] = k[it];
-        s_vals[pos] = v[it];
+      for (; q < kLookback; ++q) {
+        const uint32_t st = f[q] & ~kFlagValue;
+        if (st == 0) break;  // not yet published: read again from here
+        excl += f[q] & kFlagValue;
+        if (st == kFlagPrefix) {
+          done = true;
+          break;
+        }
+      }
+      if (done) break;
+      j -= q;
+      if (q == 0 && sort_ns() - t0 > kLookbackTimeoutNs) {
+        if (d_status) atomicOr(d_status, FGS_DEV_TIMEOUT);
+        break;
       }
     }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < tile_items; i += kSortThreads) {
-      const uint32_t key = s_keys[i];
-      const uint32_t d = (key >> shift) & 255u;
-      const uint32_t out = s_base[d] + (i - s_prefix[d]);
+    st_flag(my_flags + d, kFlagPrefix | (excl + run));
+  }
+  s_base[d] = digit_start + excl;
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    if (valid[it]) {
+      const uint32_t pos = s_prefix[dig[it]] + s_whist[warp][dig[it]] + local[it];
+      s_keys[pos] = k[it];
+      s_vals[pos] = v[it];
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < tile_items; i += kSortThreads) {
+    const uint32_t key = s_keys[i];
+    const uint32_t dd = (key >> shift) & ((1u << nbits) - 1u);
+    const uint32_t out = s_base[dd] + (i - s_prefix[dd]);
+    if (out < count) {  // always, unless a look-back gave up
       keys_out[out] = key;
       vals_out[out] = s_vals[i];
     }
-    __syncthreads();
-    s_base[threadIdx.x] += run;
-    __syncthreads();
   }
 }
 
-// Stable LSD sort of (key, value) over bits [0, bits).  Result lands in (k0, v0)
-// when the number of passes is even, in (k1, v1) otherwise.
+// Scratch of a sort over at most `cap` items: the pass histograms and tickets, then
+// the look-back flags of every pass, cleared by one memset per sort.
+struct SortWs {
+  uint32_t *hist;    // [kSortMaxPasses][256]
+  uint32_t *ticket;  // [kSortMaxPasses] (+ padding)
+  uint32_t *flags;   // [kSortMaxPasses][tiles][256]
+  int64_t tiles;
+  size_t bytes;      // the whole block, cleared per sort
+};
+
+static size_t sort_ws_bytes(int64_t cap) {
+  const int64_t tiles = std::max<int64_t>(1, (cap + kSortTile - 1) / kSortTile);
+  return (size_t)kSortMaxPasses * 256 * 4 + 256 + (size_t)kSortMaxPasses * tiles * 256 * 4;
+}
+
+static SortWs sort_ws(void *base, int64_t cap) {
+  SortWs w;
+  w.tiles = std::max<int64_t>(1, (cap + kSortTile - 1) / kSortTile);
+  char *p = static_cast<char *>(base);
+  w.hist = reinterpret_cast<uint32_t *>(p);
+  w.ticket = reinterpret_cast<uint32_t *>(p + (size_t)kSortMaxPasses * 256 * 4);
+  w.flags = reinterpret_cast<uint32_t *>(p + (size_t)kSortMaxPasses * 256 * 4 + 256);
+  w.bytes = sort_ws_bytes(cap);
+  return w;
+}
+
+// Stable LSD sort of (key, value) over bits [0, bits) of at most `cap` items
+// (the count on the device when d_count is set).  Result lands in (k0, v0) when
+// the number of passes is even, in (k1, v1) otherwise.  clear = false when the
+// caller has already zeroed w's block.
 static fgs_status radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int64_t *d_count,
-                             int64_t host_count, int64_t cap, int bits, int nblocks, uint32_t *counts,
-                             uint32_t *digit_total, cudaStream_t st) {
+                             int64_t host_count, int64_t cap, int bits, const SortWs &w, int32_t *d_status,
+                             cudaStream_t st, bool clear = true) {
   const int passes = (bits + 7) / 8;
+  if (passes < 1 || passes > kSortMaxPasses || cap > (int64_t)kFlagValue) {
+    set_error("radix_sort: %d key bits over up to %lld items", bits, (long long)cap);
+    return FGS_ERR_INVALID_ARGUMENT;
+  }
+  if (clear) FGS_CUDA(cudaMemsetAsync(w.hist, 0, w.bytes, st), "radix_sort: clear");
+  const int hist_grid = (int)std::max<int64_t>(1, std::min<int64_t>(w.tiles, 2 * (int64_t)num_sms()));
+  pdl_launch(k_sort_hist, hist_grid, kSortThreads, 0, st, k0, d_count, host_count, cap, bits, w.hist);
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
     const int nbits = std::min(8, bits - shift);
     uint32_t *ki = (p & 1) ? k1 : k0, *vi = (p & 1) ? v1 : v0;
     uint32_t *ko = (p & 1) ? k0 : k1, *vo = (p & 1) ? v0 : v1;
-    pdl_launch(k_radix_upsweep, nblocks, kSortThreads, 0, st, ki, d_count, host_count, cap, shift, nbits, counts);
-    pdl_launch(k_digit_scan, 256, kScanThreads, 0, st, counts, nblocks, digit_total);
-    pdl_launch(k_radix_downsweep, nblocks, kSortThreads, 0, st, ki, vi, ko, vo, d_count, host_count, cap, shift,
-               nbits, counts, digit_total);
-    count_launch(3);
+    pdl_launch(k_sort_pass, (int)w.tiles, kSortThreads, 0, st, ki, vi, ko, vo, d_count, host_count, cap, shift,
+               nbits, w.hist + 256 * p, w.flags + (size_t)p * w.tiles * 256, w.ticket + p, d_status);
   }
+  count_launch(1 + passes);
   FGS_CHECK_LAUNCH("radix_sort");
   return FGS_OK;
-}
-
-static int sort_blocks(int64_t cap) {
-  int64_t tiles = (cap + kSortTile - 1) / kSortTile;
-  int64_t nb = std::min<int64_t>(std::min<int64_t>(tiles, kSortMaxBlocks), 4 * (int64_t)num_sms());
-  return (int)std::max<int64_t>(nb, 1);
 }
 
 // ---------------------------------------------------------------------------------
@@ -276,78 +323,102 @@ __device__ __forceinline__ int64_t record_of(int64_t j, int64_t n, int64_t strid
   return v * stride + (j - v * n);
 }
 
-__global__ void __launch_bounds__(kScanBlock) k_vis_count(const int32_t *__restrict__ radius,
-                                                          const uint2 *__restrict__ rect, int64_t n, int64_t stride,
-                                                          int64_t R, uint32_t *__restrict__ bsum) {
-  pdl_enter();
-  __shared__ uint32_t red[kScanBlock / 32];
-  const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
-  const bool vis = j < R && record_visible(radius, rect, record_of(j, n, stride));
-  const uint32_t b = __ballot_sync(0xffffffffu, vis);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = __popc(b);
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    uint32_t t = red[threadIdx.x];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = t;
-  }
-}
+// Ordered compaction of the visible records in one pass: each CTA takes the next
+// tile of kVisTile records by ticket (warp w holds records w * 256 .. + 255 of it,
+// eight per lane in record order), counts its visible records, publishes the
+// count, adds up the earlier tiles' counts by a decoupled look-back (its first
+// warp reads 32 earlier tiles' flags at a time; flags as in k_sort_pass, bounded
+// waits) and writes (depth bits, record) of its visible records in record order.
+// The CTA of the last tile stores the total.
+constexpr int kVisItems = 8;
+constexpr int kVisTile = kScanBlock * kVisItems;  // 8192 records: ~120 tiles for a 1M map, one wave
 
-// Exclusive scan of nb block counts in place by one CTA; *total = their sum.
-__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *__restrict__ bsum, int nb, int64_t *total) {
-  pdl_enter();
-  __shared__ unsigned long long part[1024];
-  const int per = (nb + 1023) / 1024;
-  const int lo = threadIdx.x * per, hi = min(nb, lo + per);
-  unsigned long long s = 0;
-  for (int i = lo; i < hi; ++i) s += bsum[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    const unsigned long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  unsigned long long run = part[threadIdx.x] - s;
-  for (int i = lo; i < hi; ++i) {
-    const uint32_t v = bsum[i];
-    bsum[i] = (uint32_t)run;
-    run += v;
-  }
-  if (threadIdx.x == 1023) *total = (int64_t)part[1023];
-}
-
-__global__ void __launch_bounds__(kScanBlock) k_vis_scatter(const float4 *__restrict__ splat,
+__global__ void __launch_bounds__(kScanBlock) k_vis_compact(const float4 *__restrict__ splat,
                                                             const int32_t *__restrict__ radius,
                                                             const uint2 *__restrict__ rect, int64_t n, int64_t stride,
-                                                            int64_t R, const uint32_t *__restrict__ bsum,
-                                                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                                                            int64_t R, uint32_t *__restrict__ flags,
+                                                            uint32_t *__restrict__ ticket, int64_t *__restrict__ total,
+                                                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                                            int32_t *d_status) {
   pdl_enter();
-  __shared__ uint32_t wsum[kScanBlock / 32];
-  const int64_t j = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+  constexpr int NW = kScanBlock / 32;
+  __shared__ uint32_t wsum[NW];
+  __shared__ uint32_t s_tile, s_excl, s_count;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t r = j < R ? record_of(j, n, stride) : 0;
-  const bool vis = j < R && record_visible(radius, rect, r);
-  const uint32_t b = __ballot_sync(0xffffffffu, vis);
-  if (lane == 0) wsum[warp] = __popc(b);
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const int64_t nt = (R + kVisTile - 1) / kVisTile;
+  if ((int64_t)t >= nt) return;  // (the whole CTA)
+  const int64_t j0 = (int64_t)t * kVisTile + warp * (32 * kVisItems) + lane;
+  int64_t r[kVisItems];
+  uint32_t bal[kVisItems];
+  uint32_t wcount = 0;
+#pragma unroll
+  for (int it = 0; it < kVisItems; ++it) {
+    const int64_t j = j0 + it * 32;
+    r[it] = j < R ? record_of(j, n, stride) : 0;
+    const bool vis = j < R && record_visible(radius, rect, r[it]);
+    bal[it] = __ballot_sync(0xffffffffu, vis);
+    wcount += __popc(bal[it]);
+  }
+  if (lane == 0) wsum[warp] = wcount;
   __syncthreads();
   if (warp == 0) {
     const uint32_t w = wsum[lane];
     uint32_t wi = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += t;
+      const uint32_t u = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += u;
     }
     wsum[lane] = wi - w;
+    const uint32_t count = __shfl_sync(0xffffffffu, wi, 31);  // this tile's visible records
+    if (lane == 0) st_flag(flags + t, (t == 0 ? kFlagPrefix : kFlagAgg) | count);
+    uint32_t excl = 0;
+    if (t > 0) {
+      int64_t jn = (int64_t)t - 1;  // nearest tile not yet added
+      const uint64_t t0 = sort_ns();
+      for (;;) {
+        const int64_t jj = jn - lane;
+        const uint32_t f = jj >= 0 ? ld_flag(flags + jj) : kFlagPrefix;
+        const uint32_t stat = f & ~kFlagValue;
+        const uint32_t stop = __ballot_sync(0xffffffffu, stat != kFlagAgg);  // unknown or running prefix
+        const int s = stop ? __ffs(stop) - 1 : 32;
+        const bool prefix = s < 32 && __shfl_sync(0xffffffffu, stat, s & 31) == kFlagPrefix;
+        uint32_t add = (lane < s || (prefix && lane == s)) ? (f & kFlagValue) : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+        excl += add;
+        if (prefix) break;
+        jn -= s;
+        if (s == 0 && sort_ns() - t0 > kLookbackTimeoutNs) {
+          if (lane == 0 && d_status) atomicOr(d_status, FGS_DEV_TIMEOUT);
+          break;
+        }
+      }
+      if (lane == 0) st_flag(flags + t, kFlagPrefix | (excl + count));
+    }
+    if (lane == 0) {
+      s_excl = excl;
+      s_count = count;
+    }
   }
   __syncthreads();
-  if (!vis) return;
-  const uint32_t pos = bsum[blockIdx.x] + wsum[warp] + __popc(b & ((1u << lane) - 1u));
-  keys[pos] = __float_as_uint(splat[2 * r + 1].z);  // depth > 0: its bits order like the value
-  vals[pos] = (uint32_t)r;
+  if ((int64_t)t == nt - 1 && threadIdx.x == 0) *total = (int64_t)s_excl + s_count;
+  uint32_t pos = s_excl + wsum[warp];
+  const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int it = 0; it < kVisItems; ++it) {
+    if ((bal[it] >> lane) & 1u) {
+      const uint32_t q = pos + __popc(bal[it] & lt);
+      if ((int64_t)q < R) {  // always, unless a look-back gave up
+        keys[q] = __float_as_uint(splat[2 * r[it] + 1].z);  // depth > 0: its bits order like the value
+        vals[q] = (uint32_t)r[it];
+      }
+    }
+    pos += __popc(bal[it]);
+  }
 }
 
 
@@ -877,9 +948,9 @@ __global__ void k_view_keys(const uint32_t *__restrict__ recs, const int64_t *__
 
 struct BinWs {
   uint32_t *dk0, *dv0, *dk1, *dv1;  // depth sort ping-pong, R each
-  uint32_t *bsum;                   // ceil(R / 1024) + 1
-  uint32_t *counts;                 // 256 * kSortMaxBlocks
-  uint32_t *digit_total;            // 256
+  uint32_t *vis_flags;              // ceil(R / kVisTile) look-back flags, then the ticket (cleared with `sort`)
+  void *sort;                       // SortWs block: sort_ws_bytes(R), right after vis_flags
+  size_t clear_bytes;               // vis_flags and sort, one memset per call
   int64_t *vis_count, *sort_count, *nchunks;
   uint32_t *rowcnt;                 // n_rows * nb_cap
   uint32_t *rowtot;                 // n_rows
@@ -913,9 +984,10 @@ static BinWs carve(void *base, int64_t R, int64_t cap, int n_rows, int tx_max) {
   w.dv0 = (uint32_t *)take(r4);
   w.dk1 = (uint32_t *)take(r4);
   w.dv1 = (uint32_t *)take(r4);
-  w.bsum = (uint32_t *)take((size_t)((R + kScanBlock - 1) / kScanBlock + 1) * 4);
-  w.counts = (uint32_t *)take((size_t)256 * kSortMaxBlocks * 4);
-  w.digit_total = (uint32_t *)take(256 * 4);
+  const size_t vis_bytes = align_up((size_t)((R + kVisTile - 1) / kVisTile + 1) * 4);
+  w.vis_flags = (uint32_t *)take(vis_bytes);
+  w.sort = take(sort_ws_bytes(R));
+  w.clear_bytes = vis_bytes + align_up(sort_ws_bytes(R));
   w.vis_count = (int64_t *)take(8);
   w.sort_count = (int64_t *)take(8);
   w.nchunks = (int64_t *)take(8);
@@ -988,6 +1060,8 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   RowGeom G;
   FGS_CHECK_ARG(row_geom(vs, proj->stride, &G), "fgs_bin_sort: more than %d tile rows", kMaxRows);
   const int64_t R = (int64_t)n_views * n;
+  FGS_CHECK_ARG(R <= (int64_t)kFlagValue, "fgs_bin_sort: %lld records (n_views * n) exceed %u", (long long)R,
+                kFlagValue);
   BinWs w = carve(ws, R, pair_capacity, G.n_rows, G.tx_max);
   FGS_CHECK_ARG(ws != nullptr && ws_bytes >= w.bytes, "fgs_bin_sort: workspace %zu < %zu bytes", ws_bytes,
                 w.bytes);
@@ -1000,24 +1074,22 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   }
   const float4 *splat = reinterpret_cast<const float4 *>(proj->splat);
   const uint2 *rect = reinterpret_cast<const uint2 *>(proj->rect);
-  const int64_t nb = (R + kScanBlock - 1) / kScanBlock;
+  const int64_t nb = (R + kVisTile - 1) / kVisTile;
   // ordered compaction of the visible records, then the depth sort over them
   // (4 passes, stable: equal depths keep record order = id order within a view)
-  pdl_launch(k_vis_count, (unsigned)nb, kScanBlock, 0, st, proj->radius, rect, n, proj->stride, R, w.bsum);
-  pdl_launch(k_scan_blocks, 1, 1024, 0, st, w.bsum, (int)nb, w.vis_count);
-  pdl_launch(k_vis_scatter, (unsigned)nb, kScanBlock, 0, st, splat, proj->radius, rect, n, proj->stride, R, w.bsum,
-             w.dk0, w.dv0);
-  count_launch(3);
-  fgs_status s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, w.vis_count, 0, R, 32, sort_blocks(R), w.counts,
-                            w.digit_total, st);
+  FGS_CUDA(cudaMemsetAsync(w.vis_flags, 0, w.clear_bytes, st), "fgs_bin_sort: clear");
+  pdl_launch(k_vis_compact, (unsigned)nb, kScanBlock, 0, st, splat, proj->radius, rect, n, proj->stride, R,
+             w.vis_flags, w.vis_flags + nb, w.vis_count, w.dk0, w.dv0, d_status);
+  count_launch();
+  const SortWs sw = sort_ws(w.sort, R);
+  fgs_status s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, w.vis_count, 0, R, 32, sw, d_status, st, false);
   if (s != FGS_OK) return s;
   const uint32_t *srec = w.dv0;
   if (n_views > 1) {
     // views made contiguous again (stable): rows of one view stay together
     pdl_launch(k_view_keys, 4 * num_sms(), 256, 0, st, w.dv0, w.vis_count, proj->stride, w.dk0);
     count_launch();
-    s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, w.vis_count, 0, R, bits_for(n_views), sort_blocks(R), w.counts,
-                   w.digit_total, st);
+    s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, w.vis_count, 0, R, bits_for(n_views), sw, d_status, st);
     if (s != FGS_OK) return s;
     srec = w.dv1;  // one pass: the result is in the second buffer
   }

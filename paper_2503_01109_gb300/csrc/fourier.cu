@@ -8,15 +8,18 @@
 //   k_hist          256-bin histogram of E / max E (float32 decision per pixel); a
 //                   frame whose max E is at most 1e-5 of its peak gray has no
 //                   high-frequency region (E is rounding noise there)
-//   k_triangle      triangle threshold t in exact integer arithmetic
-//   k_seed_count    masks M_h / M_l / M_m (eq9, eq10) and the equidistant samples;
-//                   per-CTA counts of high / low seeds
+//   k_triangle      triangle threshold t in exact integer arithmetic (one thread
+//                   per bin, block reductions)
+//   k_seed_count    masks M_h / M_l / M_m (eq9, eq10) and the equidistant samples,
+//                   kept per pixel in the mask byte; per-CTA counts of high / low seeds
 //   k_seed_scan     scan of the CTA counts, capped seed count, append base
-//   k_seed_write    ordered compaction (high seeds then low, row-major) and eq11:
+//   k_seed_write    from the mask bytes: ordered compaction (high seeds then low,
+//                   row-major), the seeded bit, and eq11:
 //                   back-projected mean, log-scale log(alpha d / f), identity
 //                   rotation, frame colour, initial logit
 //
-// The FFT is a mixed-radix Stockham autosort transform: each stage of radix p
+// The FFT is a mixed-radix Stockham autosort transform with the twiddle factors
+// of its length tabulated in shared memory once per CTA: each stage of radix p
 // combines p interleaved sub-transforms of length L into one of length L p with
 // twiddles exp(-+2 pi i r k / (L p)) and a direct p-point DFT, ping-ponging between
 // two shared-memory buffers; the output is in natural order.  Radices: 8, 4, 2
@@ -30,7 +33,8 @@ namespace fgs {
 
 constexpr int kFftMaxStages = 16;
 constexpr int kFftThreads = 256;
-constexpr int kColGroup = 4;  // columns per CTA in the column pass
+constexpr int kColGroup = 4;  // columns per CTA in the column pass (fewer for very tall frames)
+constexpr size_t kSmemMax = 227 * 1024;
 
 struct FftPlan {
   int n, stages;
@@ -65,39 +69,53 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 
 // One radix-P stage for butterfly `b` of a length-N transform whose finished
-// sub-transforms have length L.  sign = -1 forward, +1 inverse.
+// sub-transforms have length L.  sign = -1 forward, +1 inverse.  tw[j] holds
+// (cos, sin)(2 pi j / N); a twiddle exp(sign 2 pi i e / M) for M dividing N is
+// tw[e N / M] with the sine's sign set by `sign`.
 // Not inlined: each radix gets its own register allocation instead of the
 // union of all radices' arrays inside the calling kernel.
 template <int P>
 __device__ __noinline__ void fft_butterfly(const float2 *__restrict__ src, float2 *__restrict__ dst, int N,
-                                              int L, int b, float sign, int sstride) {
+                                              int L, int b, float sign, int sstride, const float2 *__restrict__ tw) {
   const int s = b / L, k = b - s * L;
   const int Lp = L * P;
   const int NP = N / P;
+  const int tstep = N / Lp;
   float2 v[P];
 #pragma unroll
   for (int r = 0; r < P; ++r) {
     float2 x = src[(b + r * NP) * sstride];
     if (r > 0 && k > 0) {
-      float sn, cs;
-      sincospif(sign * 2.0f * (float)((r * k) % Lp) / (float)Lp, &sn, &cs);
-      x = cmul(x, make_float2(cs, sn));
+      float2 t = tw[r * k * tstep];  // r k < P L: no reduction needed
+      t.y *= sign;
+      x = cmul(x, t);
     }
     v[r] = x;
   }
-  float2 w[P];
+  // the P-point DFT's roots of unity: in registers for the small radices, read
+  // from the table for the large odd primes (fewer live registers)
+  constexpr bool kRegRoots = P <= 8;
+  float2 w[kRegRoots ? P : 1];
+  if constexpr (kRegRoots) {
 #pragma unroll
-  for (int m = 0; m < P; ++m) {
-    float sn, cs;
-    sincospif(sign * 2.0f * (float)m / (float)P, &sn, &cs);
-    w[m] = make_float2(cs, sn);
+    for (int m = 0; m < P; ++m) {
+      w[m] = tw[m * NP];
+      w[m].y *= sign;
+    }
   }
 #pragma unroll
   for (int q = 0; q < P; ++q) {
     float2 acc = v[0];
 #pragma unroll
     for (int r = 1; r < P; ++r) {
-      const float2 t = cmul(v[r], w[(r * q) % P]);
+      float2 root;
+      if constexpr (kRegRoots) {
+        root = w[(r * q) % P];
+      } else {
+        root = tw[((r * q) % P) * NP];
+        root.y *= sign;
+      }
+      const float2 t = cmul(v[r], root);
       acc.x += t.x;
       acc.y += t.y;
     }
@@ -106,24 +124,34 @@ __device__ __noinline__ void fft_butterfly(const float2 *__restrict__ src, float
 }
 
 __device__ __forceinline__ void fft_stage(int P, const float2 *src, float2 *dst, int N, int L, int b, float sign,
-                                          int sstride) {
+                                          int sstride, const float2 *tw) {
   switch (P) {
-    case 2: fft_butterfly<2>(src, dst, N, L, b, sign, sstride); break;
-    case 3: fft_butterfly<3>(src, dst, N, L, b, sign, sstride); break;
-    case 4: fft_butterfly<4>(src, dst, N, L, b, sign, sstride); break;
-    case 5: fft_butterfly<5>(src, dst, N, L, b, sign, sstride); break;
-    case 7: fft_butterfly<7>(src, dst, N, L, b, sign, sstride); break;
-    case 8: fft_butterfly<8>(src, dst, N, L, b, sign, sstride); break;
-    case 11: fft_butterfly<11>(src, dst, N, L, b, sign, sstride); break;
-    case 13: fft_butterfly<13>(src, dst, N, L, b, sign, sstride); break;
-    default: fft_butterfly<17>(src, dst, N, L, b, sign, sstride); break;
+    case 2: fft_butterfly<2>(src, dst, N, L, b, sign, sstride, tw); break;
+    case 3: fft_butterfly<3>(src, dst, N, L, b, sign, sstride, tw); break;
+    case 4: fft_butterfly<4>(src, dst, N, L, b, sign, sstride, tw); break;
+    case 5: fft_butterfly<5>(src, dst, N, L, b, sign, sstride, tw); break;
+    case 7: fft_butterfly<7>(src, dst, N, L, b, sign, sstride, tw); break;
+    case 8: fft_butterfly<8>(src, dst, N, L, b, sign, sstride, tw); break;
+    case 11: fft_butterfly<11>(src, dst, N, L, b, sign, sstride, tw); break;
+    case 13: fft_butterfly<13>(src, dst, N, L, b, sign, sstride, tw); break;
+    default: fft_butterfly<17>(src, dst, N, L, b, sign, sstride, tw); break;
+  }
+}
+
+// The table tw[j] = (cos, sin)(2 pi j / N), j < N, by the whole CTA; the caller
+// synchronises before it is read.
+__device__ __forceinline__ void fft_twiddles(float2 *tw, int N) {
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    float sn, cs;
+    sincospif(2.0f * (float)j / (float)N, &sn, &cs);
+    tw[j] = make_float2(cs, sn);
   }
 }
 
 // Transforms `lanes` independent sequences stored interleaved in shared memory
 // (element i of sequence c at (i * lanes + c)); all threads of the CTA take part.
-// Returns the buffer that holds the result.
-__device__ float2 *fft_smem(float2 *a, float2 *b, const FftPlan &plan, int lanes, float sign) {
+// tw: fft_twiddles(tw, plan.n).  Returns the buffer that holds the result.
+__device__ float2 *fft_smem(float2 *a, float2 *b, const FftPlan &plan, int lanes, float sign, const float2 *tw) {
   const int N = plan.n;
   float2 *src = a, *dst = b;
   int L = 1;
@@ -132,7 +160,7 @@ __device__ float2 *fft_smem(float2 *a, float2 *b, const FftPlan &plan, int lanes
     const int nb = N / P;
     for (int e = threadIdx.x; e < nb * lanes; e += blockDim.x) {
       const int c = e % lanes, bf = e / lanes;
-      fft_stage(P, src + c, dst + c, N, L, bf, sign, lanes);
+      fft_stage(P, src + c, dst + c, N, L, bf, sign, lanes, tw);
     }
     __syncthreads();
     float2 *t = src;
@@ -165,9 +193,10 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows(const float *__restric
                                                           float2 *__restrict__ spec, uint32_t *__restrict__ gray_max) {
   pdl_enter();
   extern __shared__ float2 sm2[];
-  float2 *a = sm2, *b = sm2 + W;
+  float2 *a = sm2, *b = sm2 + W, *tw = sm2 + 2 * W;
   const int y = blockIdx.x;
   const int64_t HW = (int64_t)W * H;
+  fft_twiddles(tw, W);
   float gm = 0.f;
   for (int x = threadIdx.x; x < W; x += blockDim.x) {
     const int64_t p = (int64_t)y * W + x;
@@ -178,29 +207,30 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows(const float *__restric
   }
   block_max_to(gm, gray_max);
   __syncthreads();
-  const float2 *r = fft_smem(a, b, plan, 1, -1.f);
+  const float2 *r = fft_smem(a, b, plan, 1, -1.f, tw);
   for (int x = threadIdx.x; x < W; x += blockDim.x) spec[(int64_t)y * W + x] = r[x];
 }
 
-// Along y for kColGroup columns: forward DFT, eq5/eq7 high-pass at the centred
+// Along y for cg columns: forward DFT, eq5/eq7 high-pass at the centred
 // frequency (eq3 read as the spectrum shift), inverse DFT.
-__global__ void __launch_bounds__(kFftThreads) k_fft_cols(float2 *__restrict__ spec, int W, int H, FftPlan plan,
-                                                          float d0) {
+__global__ void __launch_bounds__(kFftThreads, 3) k_fft_cols(float2 *__restrict__ spec, int W, int H, FftPlan plan,
+                                                          float d0, int cg) {
   pdl_enter();
   extern __shared__ float2 sm2[];
-  float2 *a = sm2, *b = sm2 + H * kColGroup;
-  const int x0 = blockIdx.x * kColGroup;
-  const int ncol = min(kColGroup, W - x0);
-  for (int e = threadIdx.x; e < H * kColGroup; e += blockDim.x) {
-    const int y = e / kColGroup, c = e - y * kColGroup;
+  float2 *a = sm2, *b = sm2 + H * cg, *tw = sm2 + 2 * H * cg;
+  const int x0 = blockIdx.x * cg;
+  const int ncol = min(cg, W - x0);
+  fft_twiddles(tw, H);
+  for (int e = threadIdx.x; e < H * cg; e += blockDim.x) {
+    const int y = e / cg, c = e - y * cg;
     a[e] = c < ncol ? spec[(int64_t)y * W + x0 + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  float2 *f = fft_smem(a, b, plan, kColGroup, -1.f);
+  float2 *f = fft_smem(a, b, plan, cg, -1.f, tw);
   const float inv2d2 = 1.0f / (2.0f * d0 * d0);
   const float hw = 0.5f * (float)W, hh = 0.5f * (float)H;
-  for (int e = threadIdx.x; e < H * kColGroup; e += blockDim.x) {
-    const int v = e / kColGroup, c = e - v * kColGroup;
+  for (int e = threadIdx.x; e < H * cg; e += blockDim.x) {
+    const int v = e / cg, c = e - v * cg;
     const int u = x0 + c;
     // centred coordinates of frequency (u, v): ((u + W/2) mod W) - W/2
     const float du = (float)((u + W / 2) % W - W / 2) / hw;
@@ -211,9 +241,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_cols(float2 *__restrict__ s
   }
   __syncthreads();
   float2 *other = (f == a) ? b : a;
-  float2 *g = fft_smem(f, other, plan, kColGroup, 1.f);
-  for (int e = threadIdx.x; e < H * kColGroup; e += blockDim.x) {
-    const int y = e / kColGroup, c = e - y * kColGroup;
+  float2 *g = fft_smem(f, other, plan, cg, 1.f, tw);
+  for (int e = threadIdx.x; e < H * cg; e += blockDim.x) {
+    const int y = e / cg, c = e - y * cg;
     if (c < ncol) spec[(int64_t)y * W + x0 + c] = g[e];
   }
 }
@@ -225,11 +255,12 @@ __global__ void __launch_bounds__(kFftThreads) k_ifft_rows(const float2 *__restr
                                                            uint32_t *__restrict__ max_bits) {
   pdl_enter();
   extern __shared__ float2 sm2[];
-  float2 *a = sm2, *b = sm2 + W;
+  float2 *a = sm2, *b = sm2 + W, *tw = sm2 + 2 * W;
   const int y = blockIdx.x;
+  fft_twiddles(tw, W);
   for (int x = threadIdx.x; x < W; x += blockDim.x) a[x] = spec[(int64_t)y * W + x];
   __syncthreads();
-  const float2 *r = fft_smem(a, b, plan, 1, 1.f);
+  const float2 *r = fft_smem(a, b, plan, 1, 1.f, tw);
   const float scale = 1.0f / ((float)W * (float)H);
   float mx = 0.f;
   for (int x = threadIdx.x; x < W; x += blockDim.x) {
@@ -266,48 +297,73 @@ __global__ void k_hist(const float *__restrict__ energy, int64_t HW, const uint3
     if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
+// Maximum of a 64-bit key over the 256-thread CTA (every thread gets it).
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long k, unsigned long long *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, k, o);
+    k = t > k ? t : k;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = k;
+  __syncthreads();
+  unsigned long long m = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) m = red[w] > m ? red[w] : m;
+  __syncthreads();
+  return m;
+}
+
 // Triangle method between the peak and the far non-empty end; exact integers.
-__global__ void k_triangle(const uint32_t *__restrict__ hist, int32_t *__restrict__ d_threshold) {
+// One thread per bin: the peak is the first bin of maximal count, lo / hi the
+// first and last non-empty bins, e the end further from the peak (hi on a tie);
+// t is the first bin, walking from the peak towards e, of maximal distance
+// |(e - p)(h[k] - h[p]) - (k - p)(h[e] - h[p])| to the line from (p, h[p]) to
+// (e, h[e]) (255 for an empty histogram).
+__global__ void __launch_bounds__(256) k_triangle(const uint32_t *__restrict__ hist, int32_t *__restrict__ d_threshold) {
   pdl_enter();
-  __shared__ int64_t hv[256];
-  __shared__ int s_p, s_lo, s_hi;
+  __shared__ unsigned long long red[8];
+  __shared__ uint32_t hv[256];
+  __shared__ int s_lo, s_hi;
   const int i = threadIdx.x;
-  hv[i] = hist[i];
-  __syncthreads();
+  const uint32_t h = hist[i];
+  hv[i] = h;
   if (i == 0) {
-    int p = 0, lo = -1, hi = -1;
-    for (int k = 0; k < 256; ++k) {
-      if (hv[k] > hv[p]) p = k;
-      if (hv[k] > 0) {
-        if (lo < 0) lo = k;
-        hi = k;
-      }
-    }
-    s_p = p;
-    s_lo = lo;
-    s_hi = hi;
+    s_lo = 256;
+    s_hi = -1;
   }
   __syncthreads();
-  if (i != 0) return;
-  const int p = s_p, lo = s_lo, hi = s_hi;
-  int t = 255;
-  if (lo >= 0) {
-    const int e = (hi - p) >= (p - lo) ? hi : lo;
-    t = p;
-    if (e != p) {
-      const int step = e > p ? 1 : -1;
-      int64_t best = -1;
-      for (int k = p; k != e + step; k += step) {
-        int64_t d = (int64_t)(e - p) * (hv[k] - hv[p]) - (int64_t)(k - p) * (hv[e] - hv[p]);
-        if (d < 0) d = -d;
-        if (d > best) {
-          best = d;
-          t = k;
-        }
-      }
-    }
+  if (h > 0) {
+    atomicMin(&s_lo, i);
+    atomicMax(&s_hi, i);
   }
-  *d_threshold = t;
+  // peak: maximal count, then the smallest index
+  const unsigned long long pk = block_max_u64(((unsigned long long)h << 8) | (unsigned)(255 - i), red);
+  const int p = 255 - (int)(pk & 255u), lo = s_lo, hi = s_hi;
+  if (hi < 0) {  // empty histogram
+    if (i == 0) *d_threshold = 255;
+    return;
+  }
+  const int e = (hi - p) >= (p - lo) ? hi : lo;
+  if (e == p) {
+    if (i == 0) *d_threshold = p;
+    return;
+  }
+  const int step = e > p ? 1 : -1;
+  const bool on_walk = step > 0 ? (i >= p && i <= e) : (i <= p && i >= e);
+  unsigned long long key = 0;
+  if (on_walk) {
+    const int64_t hp = hv[p], he = hv[e];
+    int64_t d = (int64_t)(e - p) * ((int64_t)h - hp) - (int64_t)(i - p) * (he - hp);
+    if (d < 0) d = -d;
+    // +1 keeps the peak's own d = 0 above the threads off the walk; ties go to the
+    // bin nearest the peak
+    key = (((unsigned long long)d + 1ull) << 8) | (unsigned)(step > 0 ? 255 - i : i);
+  }
+  const unsigned long long best = block_max_u64(key, red);
+  if (i == 0) {
+    const int r = (int)(best & 255u);
+    *d_threshold = step > 0 ? 255 - r : r;
+  }
 }
 
 struct SeedArgs {
@@ -363,7 +419,7 @@ __global__ void __launch_bounds__(kSeedBlock) k_seed_count(SeedArgs a) {
   uint32_t f = 0;
   if (p < HW) {
     f = pixel_flags(a, p, *a.threshold, __uint_as_float(a.max_bits[0]), energy_floor(a.max_bits));
-    a.mask[p] = (uint8_t)(f & 7u);
+    a.mask[p] = (uint8_t)f;  // the seed bits 4 and 5 stay until k_seed_write replaces them by bit 3
   }
   const uint32_t bh = __ballot_sync(0xffffffffu, f & 16u), bl = __ballot_sync(0xffffffffu, f & 32u);
   if ((threadIdx.x & 31) == 0) {
@@ -438,7 +494,7 @@ __global__ void __launch_bounds__(kSeedBlock) k_seed_write(SeedArgs a, GaussGrad
   const int64_t p = blockIdx.x * (int64_t)kSeedBlock + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t f = 0;
-  if (p < HW) f = pixel_flags(a, p, *a.threshold, __uint_as_float(a.max_bits[0]), energy_floor(a.max_bits));
+  if (p < HW) f = a.mask[p];  // k_seed_count's flags
   const bool hs = f & 16u, ls = f & 32u;
   const uint32_t bh = __ballot_sync(0xffffffffu, hs), bl = __ballot_sync(0xffffffffu, ls);
   if (lane == 0) {
@@ -468,8 +524,9 @@ __global__ void __launch_bounds__(kSeedBlock) k_seed_write(SeedArgs a, GaussGrad
     idx = (int64_t)a.bsum_hi[blockIdx.x] + wh[warp] + __popc(bh & lt);
   else
     idx = a.base[2] + (int64_t)a.bsum_lo[blockIdx.x] + wl[warp] + __popc(bl & lt);
-  if (idx >= a.base[1]) return;  // beyond the cap (or the map's room)
-  a.mask[p] |= 8u;
+  const bool kept = idx < a.base[1];  // else beyond the cap (or the map's room)
+  a.mask[p] = (uint8_t)((f & 7u) | (kept ? 8u : 0u));
+  if (!kept) return;
   const int x = (int)(p % a.W), y = (int)(p / a.W);
   a.seed_xy[2 * idx] = x;
   a.seed_xy[2 * idx + 1] = y;
@@ -579,8 +636,10 @@ extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_g
   const int64_t HW = (int64_t)W * H;
   float *E = energy ? energy : w.energy;
   FGS_CUDA(cudaMemsetAsync(w.hist, 0, 258 * 4, st), "memset hist");
-  const size_t smem_row = 2 * (size_t)W * sizeof(float2);
-  const size_t smem_col = 2 * (size_t)H * kColGroup * sizeof(float2);
+  const size_t smem_row = 3 * (size_t)W * sizeof(float2);  // two buffers + twiddles
+  int cg = kColGroup;
+  while (cg > 1 && (2 * (size_t)H * cg + H) * sizeof(float2) > kSmemMax) cg >>= 1;
+  const size_t smem_col = (2 * (size_t)H * cg + H) * sizeof(float2);
   if (smem_row > 48 * 1024) {
     FGS_CUDA(cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row), "attr");
     FGS_CUDA(cudaFuncSetAttribute(k_ifft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row), "attr");
@@ -588,7 +647,7 @@ extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_g
   if (smem_col > 48 * 1024)
     FGS_CUDA(cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col), "attr");
   pdl_launch(k_fft_rows, H, kFftThreads, smem_row, st, rgb_gt, W, H, px, w.spec, w.max_bits + 1);
-  pdl_launch(k_fft_cols, (W + kColGroup - 1) / kColGroup, kFftThreads, smem_col, st, w.spec, W, H, py, prm->d0);
+  pdl_launch(k_fft_cols, (W + cg - 1) / cg, kFftThreads, smem_col, st, w.spec, W, H, py, prm->d0, cg);
   pdl_launch(k_ifft_rows, H, kFftThreads, smem_row, st, w.spec, W, H, px, E, w.max_bits);
   pdl_launch(k_hist, 4 * num_sms(), 256, 0, st, E, HW, w.max_bits, w.hist);
   pdl_launch(k_triangle, 1, 256, 0, st, w.hist, d_threshold);
