@@ -341,9 +341,11 @@ fgs_status fgs_grid_barrier_probe(int32_t n_blocks, int32_t n_expected, int64_t 
  * parameters themselves: Gaussian i is removed when
  *   opacity_logits[i] < p->min_logit   (opacity below sigmoid(min_logit)), or
  *   max_k log_scales[k][i] > p->max_log_scale   (largest scale above exp(max_log_scale)).
- * The survivors keep their order and are compacted in place in g and, when not
- * NULL, in the Adam moments m and v (same capacity as g); planes past the new
- * count are left as they were.
+ * With K survivors, those below index K keep their slots; the removed slots
+ * below K, lowest first, receive the survivors at index K and above, highest
+ * first (only as many Gaussians move as were removed below K).  The same moves
+ * are made in the Adam moments m and v when they are not NULL (same capacity as
+ * g); slots from K on are left as they were.
  * Count: the live count is g->d_n ? *g->d_n : g->n; the new count is written to
  *   *d_num_kept and, when g->d_n is set, to *g->d_n (so a captured graph can
  *   replay it); the host g->n is not changed.

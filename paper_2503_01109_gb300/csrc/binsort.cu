@@ -11,7 +11,7 @@
 //
 // The radix sort is LSD with 8-bit digits in one sweep per pass: one kernel
 // histograms every pass's digits, then each pass is one kernel whose CTAs rank a
-// 2048-item tile stably with per-bit warp ballots, learn the counts of the earlier
+// 1024-item tile stably with per-bit warp ballots, learn the counts of the earlier
 // tiles by a decoupled look-back (bounded waits), reorder the tile in shared
 // memory and write each digit run coalesced.  Every count the kernels need lives
 // on the device, so the whole binning can be captured in a CUDA graph.
@@ -20,8 +20,8 @@
 namespace fgs {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
+constexpr int kSortItems = 4;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 1024: ~150 tiles for 150k records, every SM busy
 constexpr int kSortMaxPasses = 4;
 
 __device__ __forceinline__ uint32_t item_count(const int64_t *d_count, int64_t host_count, int64_t cap) {
@@ -129,7 +129,7 @@ __device__ __forceinline__ uint64_t sort_ns() {
 }
 
 // One stable LSD pass over the digit (key >> shift) & (2^nbits - 1).  Each CTA
-// takes the next 2048-item tile by ticket (so every tile it waits for belongs to
+// takes the next 1024-item tile by ticket (so every tile it waits for belongs to
 // a CTA that is already running), ranks the tile stably with per-bit warp ballots,
 // publishes its digit counts, and adds up the counts of the earlier tiles by a
 // decoupled look-back: thread d reads the flags of kLookback earlier tiles at a
@@ -330,10 +330,11 @@ __device__ __forceinline__ int64_t record_of(int64_t j, int64_t n, int64_t strid
 // warp reads 32 earlier tiles' flags at a time; flags as in k_sort_pass, bounded
 // waits) and writes (depth bits, record) of its visible records in record order.
 // The CTA of the last tile stores the total.
+constexpr int kVisThreads = 512;
 constexpr int kVisItems = 8;
-constexpr int kVisTile = kScanBlock * kVisItems;  // 8192 records: ~120 tiles for a 1M map, one wave
+constexpr int kVisTile = kVisThreads * kVisItems;  // 4096 records: ~250 tiles for a 1M map, one wave
 
-__global__ void __launch_bounds__(kScanBlock) k_vis_compact(const float4 *__restrict__ splat,
+__global__ void __launch_bounds__(kVisThreads) k_vis_compact(const float4 *__restrict__ splat,
                                                             const int32_t *__restrict__ radius,
                                                             const uint2 *__restrict__ rect, int64_t n, int64_t stride,
                                                             int64_t R, uint32_t *__restrict__ flags,
@@ -341,8 +342,8 @@ __global__ void __launch_bounds__(kScanBlock) k_vis_compact(const float4 *__rest
                                                             uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
                                                             int32_t *d_status) {
   pdl_enter();
-  constexpr int NW = kScanBlock / 32;
-  __shared__ uint32_t wsum[NW];
+  constexpr int NW = kVisThreads / 32;
+  __shared__ uint32_t wsum[32];
   __shared__ uint32_t s_tile, s_excl, s_count;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
@@ -352,20 +353,28 @@ __global__ void __launch_bounds__(kScanBlock) k_vis_compact(const float4 *__rest
   if ((int64_t)t >= nt) return;  // (the whole CTA)
   const int64_t j0 = (int64_t)t * kVisTile + warp * (32 * kVisItems) + lane;
   int64_t r[kVisItems];
-  uint32_t bal[kVisItems];
-  uint32_t wcount = 0;
+  int32_t rad[kVisItems];
+  uint2 rc[kVisItems];
+  // every item's radius and rect are requested before any is tested: 16 loads in flight
 #pragma unroll
   for (int it = 0; it < kVisItems; ++it) {
     const int64_t j = j0 + it * 32;
     r[it] = j < R ? record_of(j, n, stride) : 0;
-    const bool vis = j < R && record_visible(radius, rect, r[it]);
+    rad[it] = j < R ? radius[r[it]] : 0;
+    rc[it] = j < R ? rect[r[it]] : make_uint2(1u, 0u);
+  }
+  uint32_t bal[kVisItems];
+  uint32_t wcount = 0;
+#pragma unroll
+  for (int it = 0; it < kVisItems; ++it) {
+    const bool vis = rad[it] > 0 && (rc[it].x & 0xFFFFu) <= (rc[it].y & 0xFFFFu) && (rc[it].x >> 16) <= (rc[it].y >> 16);
     bal[it] = __ballot_sync(0xffffffffu, vis);
     wcount += __popc(bal[it]);
   }
   if (lane == 0) wsum[warp] = wcount;
   __syncthreads();
   if (warp == 0) {
-    const uint32_t w = wsum[lane];
+    const uint32_t w = lane < NW ? wsum[lane] : 0u;
     uint32_t wi = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1078,7 +1087,7 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   // ordered compaction of the visible records, then the depth sort over them
   // (4 passes, stable: equal depths keep record order = id order within a view)
   FGS_CUDA(cudaMemsetAsync(w.vis_flags, 0, w.clear_bytes, st), "fgs_bin_sort: clear");
-  pdl_launch(k_vis_compact, (unsigned)nb, kScanBlock, 0, st, splat, proj->radius, rect, n, proj->stride, R,
+  pdl_launch(k_vis_compact, (unsigned)nb, kVisThreads, 0, st, splat, proj->radius, rect, n, proj->stride, R,
              w.vis_flags, w.vis_flags + nb, w.vis_count, w.dk0, w.dv0, d_status);
   count_launch();
   const SortWs sw = sort_ws(w.sort, R);

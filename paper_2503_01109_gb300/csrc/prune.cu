@@ -1,18 +1,19 @@
 // prune.cu -- Gaussian pruning (Sec. III-A, "Gaussian Pruning"): the Gaussians
 // that grew too large in some dimension or whose opacity fell below a threshold
-// are removed and the survivors compacted in place, in order, together with their
-// Adam moments.
+// are removed, together with their Adam moments.  With K survivors, the
+// survivors below index K stay in place and each removed slot below K, lowest
+// first, receives a survivor from index K on, highest first: only as many
+// Gaussians move as there are slots to fill (the paper fixes no storage order).
 //
-//   k_prune_count   per block of 1024 Gaussians: survivors, and the first removed
-//                   index (atomicMin)
-//   k_prune_scan    one CTA: exclusive scan of the block counts, the new count
-//   k_prune_index   source index of every survivor at or after the first removed
-//                   one (survivors before it do not move)
-//   k_prune_gather  each plane's moving survivors into scratch ...
-//   k_prune_copy    ... and back into the plane, from the first removed slot on
+//   k_prune_count   per block of 1024 Gaussians: survivors
+//   k_prune_scan    one CTA: exclusive scan of the block counts, the new count K
+//   k_prune_index   survivors before each Gaussian give its rank among the removed
+//                   slots below K (hole list) or among the survivors from K on
+//                   (mover list, counted from the top)
+//   k_prune_move    mover h -> hole h for every plane of the map and its moments
 //
-// A survivor only moves to a lower index, so the move goes through scratch: a
-// parallel in-place gather could read a slot another thread already overwrote.
+// A mover sits at or above K and its hole below K, so the moves never overlap
+// and need no scratch copy.
 #include "common.cuh"
 
 namespace fgs {
@@ -21,9 +22,9 @@ constexpr int kPruneBlock = 1024;
 
 struct PruneScratch {
   uint32_t *bsum;   // ceil(cap / 1024) + 1
-  int64_t *ctl;     // [0] new count, [1] first removed index, [2] live count before
-  uint32_t *src;    // cap
-  float *scratch;   // 14 * cap
+  int64_t *ctl;     // [0] new count K, [1] slots to fill, [2] live count before
+  uint32_t *hole;   // cap: removed slots below K, lowest first
+  uint32_t *mover;  // cap: survivors from K on, highest first
   size_t bytes;
 };
 
@@ -39,8 +40,8 @@ static PruneScratch prune_carve(void *base, int64_t cap) {
   cap = std::max<int64_t>(cap, 1);
   w.bsum = (uint32_t *)take((size_t)((cap + kPruneBlock - 1) / kPruneBlock + 1) * 4);
   w.ctl = (int64_t *)take(24);
-  w.src = (uint32_t *)take((size_t)cap * 4);
-  w.scratch = (float *)take((size_t)cap * 14 * 4);
+  w.hole = (uint32_t *)take((size_t)cap * 4);
+  w.mover = (uint32_t *)take((size_t)cap * 4);
   w.bytes = off;
   return w;
 }
@@ -61,7 +62,6 @@ __global__ void __launch_bounds__(kPruneBlock) k_prune_count(const float *__rest
   const int64_t i = blockIdx.x * (int64_t)kPruneBlock + threadIdx.x;
   const bool in = i < live;
   const bool keep = in && survives(ls, logit, cap, i, min_logit, max_log_scale);
-  if (in && !keep) atomicMin(reinterpret_cast<unsigned long long *>(ctl + 1), (unsigned long long)i);
   const uint32_t b = __ballot_sync(0xffffffffu, keep);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = __popc(b);
   __syncthreads();
@@ -73,12 +73,12 @@ __global__ void __launch_bounds__(kPruneBlock) k_prune_count(const float *__rest
   }
 }
 
-// ctl[1] starts at INT64_MAX (no Gaussian removed) and is lowered by k_prune_count;
-// ctl[2] keeps the live count the whole call works on.
+// ctl[1] (slots to fill) is counted by k_prune_index; ctl[2] keeps the live count
+// the whole call works on.
 __global__ void k_prune_init(const int64_t *d_n, int64_t n, int64_t *ctl) {
   pdl_enter();
   ctl[0] = 0;
-  ctl[1] = INT64_MAX;
+  ctl[1] = 0;
   ctl[2] = live_count(d_n, n);
 }
 
@@ -120,15 +120,16 @@ __global__ void __launch_bounds__(kPruneBlock) k_prune_index(const float *__rest
                                                              const float *__restrict__ logit, int64_t cap,
                                                              float min_logit, float max_log_scale,
                                                              const uint32_t *__restrict__ bsum,
-                                                             const int64_t *__restrict__ ctl,
-                                                             uint32_t *__restrict__ src) {
+                                                             int64_t *__restrict__ ctl, uint32_t *__restrict__ hole,
+                                                             uint32_t *__restrict__ mover) {
   pdl_enter();
   __shared__ uint32_t wsum[kPruneBlock / 32];
   const int64_t live = ctl[2];
-  const int64_t first = ctl[1];
+  const int64_t K = ctl[0];
   const int64_t i = blockIdx.x * (int64_t)kPruneBlock + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool keep = i < live && survives(ls, logit, cap, i, min_logit, max_log_scale);
+  const bool in = i < live;
+  const bool keep = in && survives(ls, logit, cap, i, min_logit, max_log_scale);
   const uint32_t b = __ballot_sync(0xffffffffu, keep);
   if (lane == 0) wsum[warp] = __popc(b);
   __syncthreads();
@@ -143,37 +144,28 @@ __global__ void __launch_bounds__(kPruneBlock) k_prune_index(const float *__rest
     wsum[lane] = wi - w;
   }
   __syncthreads();
-  if (!keep || i < first) return;
-  const uint32_t pos = bsum[blockIdx.x] + wsum[warp] + __popc(b & ((1u << lane) - 1u));
-  src[pos] = (uint32_t)i;
+  const bool is_hole = in && !keep && i < K;
+  const uint32_t hb = __ballot_sync(0xffffffffu, is_hole);
+  if (hb && lane == __ffs(hb) - 1)
+    atomicAdd(reinterpret_cast<unsigned long long *>(ctl + 1), (unsigned long long)__popc(hb));
+  if (!in) return;
+  const int64_t S = (int64_t)bsum[blockIdx.x] + wsum[warp] + __popc(b & ((1u << lane) - 1u));  // survivors below i
+  if (is_hole) hole[i - S] = (uint32_t)i;
+  if (keep && i >= K) mover[K - 1 - S] = (uint32_t)i;
 }
 
 struct PlaneSet {
-  float *p[14];
+  float *p[42];  // up to the 14 planes of the map and of each Adam moment
 };
 
-__global__ void k_prune_gather(PlaneSet P, const uint32_t *__restrict__ src, const int64_t *__restrict__ ctl,
-                               int64_t cap, float *__restrict__ scratch) {
+// Mover h goes to hole h in every plane; blockIdx.y selects the plane.
+__global__ void k_prune_move(PlaneSet P, const uint32_t *__restrict__ hole, const uint32_t *__restrict__ mover,
+                             const int64_t *__restrict__ ctl) {
   pdl_enter();
-  const int64_t kept = ctl[0], first = ctl[1];
-  if (first >= kept) return;  // nothing moves
-  const float *__restrict__ plane = P.p[blockIdx.y];
-  float *__restrict__ out = scratch + (int64_t)blockIdx.y * cap;
-  for (int64_t j = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < kept;
-       j += (int64_t)gridDim.x * blockDim.x)
-    out[j] = plane[src[j]];
-}
-
-__global__ void k_prune_copy(PlaneSet P, const int64_t *__restrict__ ctl, int64_t cap,
-                             const float *__restrict__ scratch) {
-  pdl_enter();
-  const int64_t kept = ctl[0], first = ctl[1];
-  if (first >= kept) return;
+  const int64_t H = ctl[1];
   float *__restrict__ plane = P.p[blockIdx.y];
-  const float *__restrict__ in = scratch + (int64_t)blockIdx.y * cap;
-  for (int64_t j = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < kept;
-       j += (int64_t)gridDim.x * blockDim.x)
-    plane[j] = in[j];
+  for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < H; h += (int64_t)gridDim.x * blockDim.x)
+    plane[hole[h]] = plane[mover[h]];
 }
 
 static PlaneSet planes_of(fgs_gaussians *g) {
@@ -223,17 +215,20 @@ extern "C" fgs_status fgs_prune(fgs_gaussians *g, fgs_gaussians *m, fgs_gaussian
              p->max_log_scale, w.bsum, w.ctl);
   pdl_launch(k_prune_scan, 1, 1024, 0, st, w.bsum, (int)nb, w.ctl, d_num_kept);
   pdl_launch(k_prune_index, (unsigned)nb, kPruneBlock, 0, st, g->log_scales, g->opacity_logits, cap, p->min_logit,
-             p->max_log_scale, w.bsum, w.ctl, w.src);
+             p->max_log_scale, w.bsum, w.ctl, w.hole, w.mover);
   count_launch(4);
-  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2 * num_sms()));
+  // the moves of all 42 planes in one launch: blockIdx.y = buffer * 14 + plane
+  PlaneSet P;
+  int planes = 0;
   fgs_gaussians *bufs[3] = {g, m, v};
   for (int b = 0; b < 3; ++b) {
     if (!bufs[b]) continue;
-    const PlaneSet P = planes_of(bufs[b]);
-    pdl_launch(k_prune_gather, dim3(gx, 14), 256, 0, st, P, w.src, w.ctl, cap, w.scratch);
-    pdl_launch(k_prune_copy, dim3(gx, 14), 256, 0, st, P, w.ctl, cap, w.scratch);
-    count_launch(2);
+    const PlaneSet Q = planes_of(bufs[b]);
+    for (int k = 0; k < 14; ++k) P.p[planes++] = Q.p[k];
   }
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8));
+  pdl_launch(k_prune_move, dim3(gx, planes), 256, 0, st, P, w.hole, w.mover, w.ctl);
+  count_launch();
   if (g->d_n) {
     pdl_launch(k_prune_finish, 1, 1, 0, st, w.ctl, g->d_n);
     count_launch();

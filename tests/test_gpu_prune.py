@@ -1,5 +1,6 @@
 """Gaussian pruning on the GPU against the oracle: the surviving Gaussians and
-their Adam moments bit-exact and in order, with the host count and with the
+their Adam moments bit-exact and in the oracle's storage order (removed slots
+below the new count filled from the top), with the host count and with the
 device count, the degenerate cases, and a mapping iteration after pruning."""
 import math
 
@@ -52,8 +53,9 @@ def test_prune_matches_oracle(cuda_device, use_dc, n, cap):
     assert int(g.d_n.item()) == (k if use_dc else n)
     out = g.buf.cpu().numpy()
     assert np.array_equal(out[:, :k], ref)
-    assert np.array_equal(m.buf.cpu().numpy()[:, :k], m0[:, :n][:, keep])
-    assert np.array_equal(v.buf.cpu().numpy()[:, :k], v0[:, :n][:, keep])
+    order = op.fill_order(keep)
+    assert np.array_equal(m.buf.cpu().numpy()[:, :k], m0[:, :n][:, order])
+    assert np.array_equal(v.buf.cpu().numpy()[:, :k], v0[:, :n][:, order])
     assert np.array_equal(out[:, n:], planes[:, n:])    # columns past the old count untouched
 
 

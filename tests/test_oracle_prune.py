@@ -1,6 +1,7 @@
 """Pins of the pruning oracle (Sec. III-A, "Gaussian Pruning"): hand-built
 Gaussians on both sides of each threshold, the strictness of the comparisons,
-order preservation, and the invariants every result must satisfy."""
+the storage order (survivors below the new count stay, removed slots are filled
+from the top), and the invariants every result must satisfy."""
 import math
 
 import numpy as np
@@ -30,7 +31,18 @@ def test_hand_cases_on_both_sides_of_each_threshold():
     kept, keep = op.prune(planes, n, t_o, t_s)
     # equal to a threshold stays (strict comparisons); one ulp past it goes; both reasons together go
     assert keep.tolist() == [True, True, False, True, False, False, False]
+    # three survivors: 0 and 1 stay, removed slot 2 takes survivor 3
     assert kept[0].tolist() == [0.0, 1.0, 3.0]
+
+
+def test_fill_order_by_hand():
+    # K = 4 survivors (0, 3, 5, 6): slot 0 stays, removed slots 1 and 2 take 6 and then 5, slot 3 stays
+    keep = np.array([True, False, False, True, False, True, True, False])
+    assert op.fill_order(keep).tolist() == [0, 6, 5, 3]
+    # the survivors are already packed: nothing moves
+    assert op.fill_order(np.array([True, True, False, False])).tolist() == [0, 1]
+    # only the last one survives: it moves to slot 0
+    assert op.fill_order(np.array([False, False, True])).tolist() == [2]
 
 
 def test_opacity_threshold_is_the_sigmoid_reading():
@@ -58,8 +70,20 @@ def test_invariants_and_order_on_random_maps():
     assert np.all(kept[10] >= t_o) and np.all(kept[3:6].max(axis=0) <= t_s)
     gone = planes[:, :n][:, ~keep]
     assert np.all((gone[10] < t_o) | (gone[3:6].max(axis=0) > t_s))
-    assert np.all(np.diff(kept[0]) > 0)          # survivors keep their order
-    assert np.array_equal(kept, planes[:, :n][:, keep])
+    k = kept.shape[1]
+    src = kept[0].astype(np.int64)               # means.x holds the original index
+    assert np.array_equal(np.sort(src), np.flatnonzero(keep))   # each survivor exactly once
+    stay = keep[:k]
+    assert np.array_equal(src[stay], np.arange(k)[stay])      # survivors below K do not move
+    # the removed slots below K, lowest first, hold the survivors from K on, highest first: a loop
+    # that fills each hole with the last survivor not yet moved
+    moved = [i for i in range(n - 1, k - 1, -1) if keep[i]]
+    expect = np.arange(k)
+    for slot in range(k):
+        if not keep[slot]:
+            expect[slot] = moved.pop(0)
+    assert np.array_equal(src, expect)
+    assert np.array_equal(kept, planes[:, :n][:, expect])
 
 
 def test_nothing_and_everything_removed():
