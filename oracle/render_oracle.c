@@ -240,8 +240,30 @@ static int in_support(const void *supp, int supp_f32, int64_t rec, int tx, int t
   return support_f64(s[0], s[1], s[2], s[3], s[4], s[5], tx, ty, tw, th);
 }
 
+/* The tiles of rect row ty that a splat keeps: from the first tile of [x0, x1]
+ * that passes in_support to the last one (found by testing inward from each end).
+ * The support ellipse is convex and every tile spans the full height of the row,
+ * so in exact arithmetic the tiles that meet it are exactly this interval; taking
+ * the interval makes the decision one cheap scan from each end.  Returns 0 (and
+ * leaves *first > *last) when no tile of the row passes. */
+static int row_interval(const void *supp, int supp_f32, int64_t rec, int ty, int x0, int x1, int tw, int th,
+                        int *first, int *last) {
+  int a = x0, b = x1;
+  while (a <= x1 && !in_support(supp, supp_f32, rec, a, ty, tw, th)) ++a;
+  if (a > x1) {
+    *first = 1;
+    *last = 0;
+    return 0;
+  }
+  while (b > a && !in_support(supp, supp_f32, rec, b, ty, tw, th)) --b;
+  *first = a;
+  *last = b;
+  return 1;
+}
+
 /* ---------------------------------------------------------------------------------
- * Binning: every (tile, Gaussian) pair whose tile lies in the Gaussian's rect and support,
+ * Binning: every (tile, Gaussian) pair whose tile lies in the Gaussian's rect and
+ * in the kept interval of its row (row_interval),
  * ordered by (global tile, float32 depth bits, id).  Depth order is the
  * front-to-back order eq1's product runs over.  depth_f32 is the float32 depth
  * the kernels key on; it is given, so the order is a pure integer question. */
@@ -267,9 +289,10 @@ int64_t or_count_pairs(int32_t n_views, int64_t n, const int32_t *radius, const 
     for (int64_t i = 0; i < n; ++i) {
       const int32_t *r = rect + 4 * (v * n + i);
       if (radius[v * n + i] <= 0 || r[0] > r[2] || r[1] > r[3]) continue;
-      for (int32_t ty = r[1]; ty <= r[3]; ++ty)
-        for (int32_t tx = r[0]; tx <= r[2]; ++tx)
-          total += in_support(supp, supp_f32, v * n + i, tx, ty, tile_w, tile_h);
+      for (int32_t ty = r[1]; ty <= r[3]; ++ty) {
+        int a, b;
+        if (row_interval(supp, supp_f32, v * n + i, ty, r[0], r[2], tile_w, tile_h, &a, &b)) total += b - a + 1;
+      }
     }
   return total;
 }
@@ -290,14 +313,16 @@ int64_t or_bin_sort(int32_t n_views, int64_t n, const int32_t *tiles_x, const in
       if (radius[v * n + i] <= 0 || r[0] > r[2] || r[1] > r[3]) continue;
       uint32_t dbits;
       memcpy(&dbits, &depth_f32[v * n + i], 4);
-      for (int32_t ty = r[1]; ty <= r[3]; ++ty)
-        for (int32_t tx = r[0]; tx <= r[2]; ++tx) {
-          if (!in_support(supp, supp_f32, v * n + i, tx, ty, tile_w, tile_h)) continue;
+      for (int32_t ty = r[1]; ty <= r[3]; ++ty) {
+        int a, b;
+        if (!row_interval(supp, supp_f32, v * n + i, ty, r[0], r[2], tile_w, tile_h, &a, &b)) continue;
+        for (int32_t tx = a; tx <= b; ++tx) {
           pairs[k].tile = tile_base + (uint32_t)(ty * tiles_x[v] + tx);
           pairs[k].dbits = dbits;
           pairs[k].id = (int32_t)i;
           ++k;
         }
+      }
     }
     tile_base += (uint32_t)(tiles_x[v] * tiles_y[v]);
   }

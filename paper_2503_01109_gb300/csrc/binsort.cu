@@ -308,7 +308,6 @@ static fgs_status radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
 // order before the depth sort, so the sort touches only them: a block count, a
 // scan of the block counts, and an ordered scatter of (depth bits, record).
 
-constexpr int kScanBlock = 1024;
 
 __device__ __forceinline__ bool record_visible(const int32_t *__restrict__ radius, const uint2 *__restrict__ rect,
                                                int64_t r) {
@@ -693,16 +692,33 @@ __device__ __forceinline__ TileChunk tile_chunk(const RowGeom &G, const uint32_t
   return k;
 }
 
-// One row-list entry as the tile writing pass needs it: Gaussian id, the rect's
-// tile columns x0 | x1 << 16, and the tiles of x0 .. x0 + 63 the support keeps
-// (bit i = tile x0 + i; valid when the rect is at most 64 tiles wide).
+// One row-list entry as the tile writing pass needs it: Gaussian id and the kept
+// tile columns a | b << 16 (a > b: none).
 struct EntryInfo {
-  uint32_t id, xr, m0, m1;
+  uint32_t id, xr;
 };
+
+// The tiles of rect columns [x0, x1] in tile row y that a splat keeps: from the
+// first one that passes tile_in_support to the last one, found by testing inward
+// from each end.  The support ellipse is convex and a tile spans the row's full
+// height, so in exact arithmetic these are exactly the tiles it meets; the
+// interval needs two short scans instead of a test per tile.  a > b when none.
+__device__ __forceinline__ void kept_interval(const SupportSplat &sp, int x0, int x1, int y, int tw, int th, int &a,
+                                              int &b) {
+  a = x0;
+  while (a <= x1 && !tile_in_support(sp, a, y, tw, th)) ++a;
+  b = x1;
+  if (a > x1) {
+    a = 1;
+    b = 0;
+    return;
+  }
+  while (b > a && !tile_in_support(sp, b, y, tw, th)) --b;
+}
 
 // Tiles, counting pass: per chunk c of a row list, the number of its records that
 // keep tile x of the row, into tcnt[c * tx_max + x], and every entry's EntryInfo.
-// A thread tests its own record's tiles.
+// A thread finds its own record's kept interval.
 __global__ void __launch_bounds__(kTileChunk) k_tile_count(RowGeom G, const float4 *__restrict__ splat,
                                                            const uint32_t *__restrict__ srec,
                                                            const uint2 *__restrict__ rect, int tw, int th,
@@ -725,16 +741,10 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_count(RowGeom G, const floa
       const uint32_t rec = srec[rowlist[e]];
       const uint2 rc = rect[rec];
       const SupportSplat sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
-      const int x0 = (int)(rc.x & 0xFFFFu), x1 = (int)(rc.y & 0xFFFFu);
-      uint64_t mk = 0;
-      for (int x = x0; x <= x1; ++x) {
-        if (tile_in_support(sp, x, k.y, tw, th)) {
-          atomicAdd(&s_cnt[x], 1u);
-          if (x - x0 < 64) mk |= 1ull << (x - x0);
-        }
-      }
-      einfo[e] = EntryInfo{rec - (uint32_t)k.v * (uint32_t)G.stride, rc.x & 0xFFFFu | (rc.y << 16),
-                           (uint32_t)mk, (uint32_t)(mk >> 32)};
+      int a, b;
+      kept_interval(sp, (int)(rc.x & 0xFFFFu), (int)(rc.y & 0xFFFFu), k.y, tw, th, a, b);
+      for (int x = a; x <= b; ++x) atomicAdd(&s_cnt[x], 1u);
+      einfo[e] = EntryInfo{rec - (uint32_t)k.v * (uint32_t)G.stride, (uint32_t)a | ((uint32_t)b << 16)};
     }
     __syncthreads();
     for (int x = threadIdx.x; x < k.tx; x += kTileChunk) tcnt[c * G.tx_max + x] = s_cnt[x];
@@ -744,37 +754,70 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_count(RowGeom G, const floa
 
 // Tiles, scan over chunks: one CTA per row; tpre[c][x] = pairs of tile x in the
 // row's chunks before c, ttot[g][x] = the tile's total, rowp[g] = the row's total.
+// Lane L of every warp takes columns L, L + 32, ...; the eight warps split the
+// row's chunks into eight consecutive ranges: each warp sums its range per column
+// (all its loads in flight together), the ranges' sums are scanned across warps in
+// shared memory, and each warp writes its range's prefixes.
 __global__ void __launch_bounds__(256) k_tile_chunk_scan(RowGeom G, const uint32_t *__restrict__ chunk_start,
                                                          const uint32_t *__restrict__ tcnt,
                                                          uint32_t *__restrict__ tpre, uint32_t *__restrict__ ttot,
                                                          unsigned long long *__restrict__ rowp) {
   pdl_enter();
-  __shared__ unsigned long long red[8];
+  constexpr int NW = 8;
+  __shared__ uint32_t s_part[NW][128];  // per warp and column (columns in slices of 128)
   const int g = blockIdx.x;
   const int v = view_of_row(G, g);
   const int tx = G.tiles_x[v];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t c0 = chunk_start[g], c1 = chunk_start[g + 1];
+  const uint32_t nc = c1 - c0, per = (nc + NW - 1) / NW;
+  const uint32_t ca = c0 + min(nc, warp * per), cb = c0 + min(nc, (warp + 1) * per);
   unsigned long long row_sum = 0;
-  for (int x = threadIdx.x; x < tx; x += 256) {
-    uint32_t run = 0;
-#pragma unroll 8
-    for (uint32_t c = c0; c < c1; ++c) {
-      const uint32_t t = tcnt[(int64_t)c * G.tx_max + x];
-      tpre[(int64_t)c * G.tx_max + x] = run;
-      run += t;
+  for (int xs = 0; xs < tx; xs += 128) {  // column slices of 128 (4 per lane)
+    uint32_t sum[4] = {0u, 0u, 0u, 0u};
+#pragma unroll 4
+    for (uint32_t c = ca; c < cb; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int x = xs + lane + 32 * k;
+        if (x < tx) sum[k] += tcnt[(int64_t)c * G.tx_max + x];
+      }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s_part[warp][lane + 32 * k] = sum[k];
+    __syncthreads();
+    uint32_t run[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      uint32_t before = 0, all = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t t = s_part[w][lane + 32 * k];
+        before += w < warp ? t : 0u;
+        all += t;
+      }
+      run[k] = before;
+      const int x = xs + lane + 32 * k;
+      if (warp == 0 && x < tx) {
+        ttot[(int64_t)g * G.tx_max + x] = all;
+        row_sum += all;
+      }
     }
-    ttot[(int64_t)g * G.tx_max + x] = run;
-    row_sum += run;
+#pragma unroll 4
+    for (uint32_t c = ca; c < cb; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int x = xs + lane + 32 * k;
+        if (x < tx) {
+          const uint32_t t = tcnt[(int64_t)c * G.tx_max + x];
+          tpre[(int64_t)c * G.tx_max + x] = run[k];
+          run[k] += t;
+        }
+      }
+    __syncthreads();
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) row_sum += __shfl_xor_sync(0xffffffffu, row_sum, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = row_sum;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long t = 0;
-    for (int w = 0; w < 8; ++w) t += red[w];
-    rowp[g] = t;
-  }
+  if (threadIdx.x == 0) rowp[g] = row_sum;
 }
 
 // Tiles, row starts (one CTA): exclusive scan of the rows' pair totals; the total
@@ -863,10 +906,8 @@ __global__ void __launch_bounds__(256) k_tile_ranges_rows(RowGeom G, const unsig
 // Tiles, writing pass: the chunk's records in order, 32 tiles of the row at a time;
 // pair (tile x, record) goes to tstart[g][x] + tpre[c][x] + the pairs of x kept by
 // the chunk's earlier warps + its rank among the warp's lanes that keep x.  The
-// kept tiles come from the counting pass (rects over 64 tiles wide test again).
-__global__ void __launch_bounds__(kTileChunk) k_tile_emit(RowGeom G, const float4 *__restrict__ splat,
-                                                          int tw, int th,
-                                                          const uint32_t *__restrict__ row_start,
+// kept intervals come from the counting pass.
+__global__ void __launch_bounds__(kTileChunk) k_tile_emit(RowGeom G, const uint32_t *__restrict__ row_start,
                                                           const uint32_t *__restrict__ chunk_start,
                                                           const uint32_t *__restrict__ chunk_row,
                                                           const int64_t *__restrict__ d_nchunks,
@@ -895,37 +936,24 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_emit(RowGeom G, const float
     for (int x = threadIdx.x; x < k.tx; x += kTileChunk) s_base[x] = tstart[trow + x] + tpre[crow + x];
     __syncthreads();
     const uint32_t e = k.e0 + threadIdx.x;
-    int x0 = 0, x1 = -1;
-    EntryInfo inf{0u, 0u, 0u, 0u};
+    int x0 = 1, x1 = 0;
+    EntryInfo inf{0u, 1u};
     if (e < k.e1) {
       inf = einfo[e];
       x0 = (int)(inf.xr & 0xFFFFu);
       x1 = (int)(inf.xr >> 16);
-      atomicMin(&s_lo, x0);
-      atomicMax(&s_hi, x1);
-    }
-    const bool wide = x1 - x0 + 1 > 64;
-    SupportSplat sp{};
-    if (wide) {
-      const int64_t rec = (int64_t)k.v * G.stride + inf.id;
-      sp = support_splat(splat[2 * rec], splat[2 * rec + 1]);
+      if (x0 <= x1) {
+        atomicMin(&s_lo, x0);
+        atomicMax(&s_hi, x1);
+      }
     }
     __syncthreads();
     const int lo = s_lo, hi = s_hi;
     const uint32_t tbase = (uint32_t)(G.tile_base[k.v] + k.y * k.tx);
     for (int xb = lo; xb <= hi; xb += 32) {
-      uint32_t m = 0;  // tiles xb .. xb + 31 this record keeps
+      uint32_t m = 0;  // tiles xb .. xb + 31 this record keeps: bits a - xb .. b - xb
       const int a = max(x0, xb), b = min(x1, xb + 31);
-      if (a <= b) {
-        if (!wide) {
-          const uint64_t mk = ((uint64_t)inf.m1 << 32) | inf.m0;  // bit i: tile x0 + i
-          const int sh = xb - x0;
-          m = (uint32_t)(sh >= 0 ? (mk >> sh) : (mk << -sh));
-        } else {
-          for (int x = a; x <= b; ++x)
-            if (tile_in_support(sp, x, k.y, tw, th)) m |= 1u << (x - xb);
-        }
-      }
+      if (a <= b) m = (b - xb == 31 ? 0xFFFFFFFFu : ((1u << (b - xb + 1)) - 1u)) & ~((1u << (a - xb)) - 1u);
       const uint32_t col = warp_bin_counts(m, lane, s_wc[warp]);
       __syncthreads();
       uint32_t before = xb + lane < k.tx ? s_base[xb + lane] : 0u;
@@ -1126,7 +1154,7 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   pdl_launch(k_tile_row_starts, 1, 1024, 0, st, G, w.rowp, pair_capacity, d_num_pairs, d_status, w.sort_count);
   pdl_launch(k_tile_ranges_rows, NR, 256, 0, st, G, w.rowp, w.ttot, w.sort_count, w.tstart,
              reinterpret_cast<int2 *>(tile_ranges));
-  pdl_launch(k_tile_emit, grid, kTileChunk, tx_smem, st, G, splat, tw, th, w.row_start, w.chunk_start, w.chunk_row,
+  pdl_launch(k_tile_emit, grid, kTileChunk, tx_smem, st, G, w.row_start, w.chunk_start, w.chunk_row,
              w.nchunks, w.einfo, w.tpre, w.tstart, w.sort_count, tile_keys, reinterpret_cast<uint32_t *>(ids));
   count_launch(5);
   FGS_CHECK_LAUNCH("fgs_bin_sort tiles");

@@ -33,7 +33,8 @@ namespace fgs {
 
 constexpr int kFftMaxStages = 16;
 constexpr int kFftThreads = 256;
-constexpr int kColGroup = 4;  // columns per CTA in the column pass (fewer for very tall frames)
+constexpr int kColGroup = 2;    // columns per CTA in the column pass (1 for very tall frames)
+constexpr int kColThreads = 128;  // six column CTAs per SM hide the stages' latency
 constexpr size_t kSmemMax = 227 * 1024;
 
 struct FftPlan {
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows(const float *__restric
 
 // Along y for cg columns: forward DFT, eq5/eq7 high-pass at the centred
 // frequency (eq3 read as the spectrum shift), inverse DFT.
-__global__ void __launch_bounds__(kFftThreads, 3) k_fft_cols(float2 *__restrict__ spec, int W, int H, FftPlan plan,
+__global__ void __launch_bounds__(kColThreads, 6) k_fft_cols(float2 *__restrict__ spec, int W, int H, FftPlan plan,
                                                           float d0, int cg) {
   pdl_enter();
   extern __shared__ float2 sm2[];
@@ -647,7 +648,7 @@ extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_g
   if (smem_col > 48 * 1024)
     FGS_CUDA(cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col), "attr");
   pdl_launch(k_fft_rows, H, kFftThreads, smem_row, st, rgb_gt, W, H, px, w.spec, w.max_bits + 1);
-  pdl_launch(k_fft_cols, (W + cg - 1) / cg, kFftThreads, smem_col, st, w.spec, W, H, py, prm->d0, cg);
+  pdl_launch(k_fft_cols, (W + cg - 1) / cg, kColThreads, smem_col, st, w.spec, W, H, py, prm->d0, cg);
   pdl_launch(k_ifft_rows, H, kFftThreads, smem_row, st, w.spec, W, H, px, E, w.max_bits);
   pdl_launch(k_hist, 4 * num_sms(), 256, 0, st, E, HW, w.max_bits, w.hist);
   pdl_launch(k_triangle, 1, 256, 0, st, w.hist, d_threshold);

@@ -170,6 +170,60 @@ def test_binned_equals_three_sigma_brute_force(W, H, tw, th, kind):
     assert P < P_box
 
 
+def _tile_meets_ellipse(mx, my, a, b, c, thr, x0, x1, y0, y1):
+    """Whether min over the rectangle [x0, x1] x [y0, y1] (offsets from the mean) of
+    q = a dx^2 + 2 b dx dy + c dy^2 is <= thr, by minimising over a dense grid of
+    each edge (q is convex, so the minimum over the rectangle lies inside it (0)
+    or on an edge) -- written here independently of the oracle's closed form."""
+    if x0 <= 0 <= x1 and y0 <= 0 <= y1:
+        return True
+    t = np.linspace(0.0, 1.0, 4097)
+    best = np.inf
+    for dx, dy in ((x0 + 0 * t, y0 + (y1 - y0) * t), (x1 + 0 * t, y0 + (y1 - y0) * t),
+                   (x0 + (x1 - x0) * t, y0 + 0 * t), (x0 + (x1 - x0) * t, y1 + 0 * t)):
+        best = min(best, float(np.min(a * dx * dx + 2 * b * dx * dy + c * dy * dy)))
+    return best <= thr
+
+
+@pytest.mark.parametrize("tw,th,kind", [(16, 16, "tiny"), (8, 8, "tiny"), (16, 16, "needle")])
+def test_row_interval_is_the_set_of_tiles_meeting_the_ellipse(tw, th, kind):
+    """Within a rect row the oracle keeps the tiles from the first that passes the
+    support test to the last (row_interval).  The ellipse {q <= thr} is convex and
+    each tile spans the row's full height, so these are exactly the tiles whose
+    pixel-centre rectangle meets it: checked per (Gaussian, tile) against a dense
+    minimisation over each tile's edges, away from the decision boundary."""
+    W, H = 70, 45
+    sc = syn.tiny_scene(1000, seed=5) if kind == "tiny" else syn.edge_scene(kind, 1000, seed=5)
+    cam = syn.pinhole(W, H, 60.0)
+    pr = orr.project(orr.aos(sc), cam, tw, th)
+    sup = orr.support_f64(pr)
+    _, ids, ranges = orr.bin_sort([cam], tw, th, pr["depth"].astype(np.float32)[None], pr["radius"][None],
+                                  pr["rect"][None], sup[None])
+    tx, ty = orr.tiles_of(cam, tw, th)
+    kept = set()
+    for t in range(tx * ty):
+        for j in range(ranges[t, 0], ranges[t, 1]):
+            kept.add((int(ids[j]), t))
+    checked = 0
+    for i in range(pr["radius"].size):
+        r = pr["rect"][i]
+        if pr["radius"][i] <= 0 or r[0] > r[2] or r[1] > r[3]:
+            continue
+        mx, my, a, b, c, thr = sup[i]
+        for yy in range(r[1], r[3] + 1):
+            for xx in range(r[0], r[2] + 1):
+                x0, x1 = xx * tw - mx, xx * tw + tw - 1 - mx
+                y0, y1 = yy * th - my, yy * th + th - 1 - my
+                meets = _tile_meets_ellipse(mx, my, a, b, c, thr, x0, x1, y0, y1)
+                near = _tile_meets_ellipse(mx, my, a, b, c, thr * (1 + 1e-3) + 1e-6, x0, x1, y0, y1) != \
+                    _tile_meets_ellipse(mx, my, a, b, c, thr * (1 - 1e-3) - 1e-6, x0, x1, y0, y1)
+                if near:
+                    continue
+                assert ((i, yy * tx + xx) in kept) == meets, (i, xx, yy)
+                checked += 1
+    assert checked > 1500
+
+
 def test_float32_support_drops_no_blending_pair():
     """The float32 support test the kernels take (teacher-forced binning) is safe
     too: on splats rounded to float32, lists binned over the plain 3-sigma boxes
