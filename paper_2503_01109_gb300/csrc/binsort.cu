@@ -730,11 +730,12 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_count(RowGeom G, const floa
                                                            uint32_t *__restrict__ tcnt,
                                                            EntryInfo *__restrict__ einfo) {
   pdl_enter();
-  extern __shared__ uint32_t s_cnt[];  // [tx_max]
+  extern __shared__ uint32_t s_cnt[];  // [tx_max + 1]: +1 at each kept interval's start, -1 past its end
   const int64_t NC = *d_nchunks;
+  const int lane = threadIdx.x & 31;
   for (int64_t c = blockIdx.x; c < NC; c += gridDim.x) {
     const TileChunk k = tile_chunk(G, chunk_row, chunk_start, row_start, c);
-    for (int x = threadIdx.x; x < k.tx; x += kTileChunk) s_cnt[x] = 0;
+    for (int x = threadIdx.x; x <= k.tx; x += kTileChunk) s_cnt[x] = 0;
     __syncthreads();
     const uint32_t e = k.e0 + threadIdx.x;
     if (e < k.e1) {
@@ -743,11 +744,28 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_count(RowGeom G, const floa
       const SupportSplat sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
       int a, b;
       kept_interval(sp, (int)(rc.x & 0xFFFFu), (int)(rc.y & 0xFFFFu), k.y, tw, th, a, b);
-      for (int x = a; x <= b; ++x) atomicAdd(&s_cnt[x], 1u);
+      if (a <= b) {
+        atomicAdd(&s_cnt[a], 1u);
+        atomicAdd(&s_cnt[b + 1], 0xFFFFFFFFu);  // -1 modulo 2^32
+      }
       einfo[e] = EntryInfo{rec - (uint32_t)k.v * (uint32_t)G.stride, (uint32_t)a | ((uint32_t)b << 16)};
     }
     __syncthreads();
-    for (int x = threadIdx.x; x < k.tx; x += kTileChunk) tcnt[c * G.tx_max + x] = s_cnt[x];
+    if (threadIdx.x < 32) {  // the differences summed along the row: the records keeping tile x
+      uint32_t carry = 0;
+      for (int xb = 0; xb < k.tx; xb += 32) {
+        const int x = xb + lane;
+        uint32_t v = x < k.tx ? s_cnt[x] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+          if (lane >= o) v += u;
+        }
+        v += carry;
+        if (x < k.tx) tcnt[c * G.tx_max + x] = v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
+      }
+    }
     __syncthreads();
   }
 }
@@ -1141,7 +1159,7 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   count_launch(4);
   FGS_CHECK_LAUNCH("fgs_bin_sort rows");
   const int tw = tiling.tile_w, th = tiling.tile_h;
-  const size_t tx_smem = sizeof(uint32_t) * (size_t)G.tx_max;
+  const size_t tx_smem = sizeof(uint32_t) * (size_t)(G.tx_max + 1);
   if (tx_smem > 16384) {  // with the static arrays, past the default 48 KB of shared memory
     FGS_CUDA(cudaFuncSetAttribute(k_tile_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tx_smem),
              "k_tile_count smem");

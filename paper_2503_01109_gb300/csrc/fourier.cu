@@ -104,23 +104,37 @@ __device__ __noinline__ void fft_butterfly(const float2 *__restrict__ src, float
       w[m].y *= sign;
     }
   }
+  if constexpr (kRegRoots) {
 #pragma unroll
-  for (int q = 0; q < P; ++q) {
-    float2 acc = v[0];
+    for (int q = 0; q < P; ++q) {
+      float2 acc = v[0];
 #pragma unroll
-    for (int r = 1; r < P; ++r) {
-      float2 root;
-      if constexpr (kRegRoots) {
-        root = w[(r * q) % P];
-      } else {
-        root = tw[((r * q) % P) * NP];
-        root.y *= sign;
+      for (int r = 1; r < P; ++r) {
+        const float2 t = cmul(v[r], w[(r * q) % P]);
+        acc.x += t.x;
+        acc.y += t.y;
       }
-      const float2 t = cmul(v[r], root);
-      acc.x += t.x;
-      acc.y += t.y;
+      dst[(s * Lp + k + L * q) * sstride] = acc;
     }
-    dst[(s * Lp + k + L * q) * sstride] = acc;
+  } else {
+    // the large odd primes: one output per iteration, so the code stays small (a
+    // fully unrolled P x P product overflowed the instruction cache); j = r q mod P
+#pragma unroll 1
+    for (int q = 0; q < P; ++q) {
+      float2 acc = v[0];
+      int j = 0;
+#pragma unroll
+      for (int r = 1; r < P; ++r) {
+        j += q;
+        if (j >= P) j -= P;
+        float2 root = tw[j * NP];
+        root.y *= sign;
+        const float2 t = cmul(v[r], root);
+        acc.x += t.x;
+        acc.y += t.y;
+      }
+      dst[(s * Lp + k + L * q) * sstride] = acc;
+    }
   }
 }
 
