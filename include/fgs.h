@@ -139,10 +139,10 @@ int64_t fgs_num_tiles(const fgs_camera *cams, int32_t n_views, fgs_tiling tiling
 /* ---------------------------------------------------------------------------------
  * fgs_bin_sort -- tile binning and depth ordering of the splats that eq1 blends
  * front to back.  Produces, for every global tile, the list of Gaussians whose
- * rect contains the tile and for which, within the rect's row of tiles, the tile
- * lies between the first and the last tile whose pixel-centre rectangle meets the
- * support ellipse {q <= thr} (float32 test; the ellipse is convex, so these are
- * the tiles it meets), ordered by (float32 depth bits, Gaussian id).
+ * rect contains the tile and whose support ellipse {q <= thr} meets the tile's
+ * rectangle of pixel centres, decided per tile row from the ellipse's x-extent
+ * within the row's strip (float32, a fixed order of rounded steps), ordered by
+ * (float32 depth bits, Gaussian id).
  *   tile_keys[k], ids[k] for k < *d_num_pairs: global tile index and Gaussian id,
  *   sorted by (tile, depth, id).  tile_ranges[2*t], [2*t+1] = [start, end) of tile t
  *   (0, 0 for an empty tile).

@@ -185,77 +185,82 @@ void or_project(int64_t n, const double *means, const double *log_scales, const 
 }
 
 /* ---------------------------------------------------------------------------------
- * Opacity-aware support of a splat on a tile: the minimum over the tile's pixel
- * centres of q(d) = a dx^2 + 2 b dx dy + c dy^2 (d = pixel - mean2d) is at most thr.
- * The minimum of this convex form over a rectangle is 0 when the mean lies inside,
- * else it lies on an edge, where it is a 1-D quadratic minimised at
- * dy = -b dx / c (vertical edges) or dx = -b dy / a (horizontal edges), clamped.
- * support_f32 takes every step in float32 (teacher-forced parity with the
- * kernels); support_f64 is the same test in double. */
-static float support_q32(float a, float b, float c, float dx, float dy) {
-  return (a * (dx * dx) + 2.f * (b * (dx * dy))) + c * (dy * dy);
+ * Opacity-aware support of a splat on a row of tiles.  The splat can reach
+ * alpha >= 1/255 only inside the ellipse E = {q(d) <= thr}, q(d) = a dx^2 +
+ * 2 b dx dy + c dy^2 (d = pixel - mean2d).  A tile of tile row ty spans the row's
+ * pixel-centre rows y0 <= dy <= y1, so it meets E iff its pixel-centre columns
+ * meet [xl, xr], the x-extent of E within that strip.  E is convex and its left
+ * boundary x(dy) = (-b dy - sqrt(thr a - det dy^2)) / a (det = a c - b^2) is convex
+ * in dy with its minimum -sqrt(thr c / det) at dy = b sqrt(thr c / det) / c; over
+ * the strip cut to E's y-range [-sqrt(thr a / det), +sqrt(thr a / det)] the
+ * leftmost point lies at that dy clamped into the range (the right boundary
+ * mirrors it).  Tile tx is kept iff tx tw + tw - 1 >= mx + xl and
+ * tx tw <= mx + xr, i.e. for tx in [ceil((mx + xl - (tw - 1)) / tw),
+ * floor((mx + xr) / tw)] cut to the rect's columns.
+ * strip_f32 takes every step in float32 in this order (parity with the kernels);
+ * strip_f64 is the same in double.  Both return 0 when the strip misses E. */
+static int strip_f32(float mx, float my, float a, float b, float c, float thr, int ty, int tw, int th, float *xl,
+                     float *xr) {
+  const float y0 = (float)(ty * th) - my, y1 = (float)(ty * th + th - 1) - my;
+  const float det = a * c - b * b;
+  if (!(det > 0.f) || !(thr >= 0.f)) return 0;
+  const float ta = thr * a;
+  const float ys = sqrtf(ta / det), xs = sqrtf((thr * c) / det);
+  const float lo = fmaxf(y0, -ys), hi = fminf(y1, ys);
+  if (lo > hi) return 0;
+  const float dl = (b * xs) / c;
+  const float yl = fminf(fmaxf(dl, lo), hi), yr = fminf(fmaxf(-dl, lo), hi);
+  const float rl = sqrtf(fmaxf(ta - det * (yl * yl), 0.f)), rr = sqrtf(fmaxf(ta - det * (yr * yr), 0.f));
+  *xl = (-(b * yl) - rl) / a;
+  *xr = (-(b * yr) + rr) / a;
+  return 1;
 }
 
-static int support_f32(float mx, float my, float a, float b, float c, float thr, int tx, int ty, int tw, int th) {
-  float x0 = (float)(tx * tw) - mx, x1 = (float)(tx * tw + tw - 1) - mx;
-  float y0 = (float)(ty * th) - my, y1 = (float)(ty * th + th - 1) - my;
-  if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return 1;
-  float sx = -b / a, sy = -b / c;   /* dx on a horizontal edge = sx dy, dy on a vertical one = sy dx */
-  float q0 = support_q32(a, b, c, x0, fminf(fmaxf(sy * x0, y0), y1));
-  float q1 = support_q32(a, b, c, x1, fminf(fmaxf(sy * x1, y0), y1));
-  float q2 = support_q32(a, b, c, fminf(fmaxf(sx * y0, x0), x1), y0);
-  float q3 = support_q32(a, b, c, fminf(fmaxf(sx * y1, x0), x1), y1);
-  return fminf(fminf(q0, q1), fminf(q2, q3)) <= thr;
+static int strip_f64(double mx, double my, double a, double b, double c, double thr, int ty, int tw, int th,
+                     double *xl, double *xr) {
+  const double y0 = (double)(ty * th) - my, y1 = (double)(ty * th + th - 1) - my;
+  const double det = a * c - b * b;
+  if (!(det > 0.0) || !(thr >= 0.0)) return 0;
+  const double ta = thr * a;
+  const double ys = sqrt(ta / det), xs = sqrt((thr * c) / det);
+  const double lo = fmax(y0, -ys), hi = fmin(y1, ys);
+  if (lo > hi) return 0;
+  const double dl = (b * xs) / c;
+  const double yl = fmin(fmax(dl, lo), hi), yr = fmin(fmax(-dl, lo), hi);
+  const double rl = sqrt(fmax(ta - det * (yl * yl), 0.0)), rr = sqrt(fmax(ta - det * (yr * yr), 0.0));
+  *xl = (-(b * yl) - rl) / a;
+  *xr = (-(b * yr) + rr) / a;
+  return 1;
 }
 
-static int support_f64(double mx, double my, double a, double b, double c, double thr, int tx, int ty, int tw,
-                       int th) {
-  double x0 = tx * tw - mx, x1 = tx * tw + tw - 1 - mx, y0 = ty * th - my, y1 = ty * th + th - 1 - my;
-  if (x0 <= 0 && x1 >= 0 && y0 <= 0 && y1 >= 0) return 1;
-  double best = 1e300;
-  for (int e = 0; e < 4; ++e) {
-    double dx, dy;
-    if (e < 2) {
-      dx = e == 0 ? x0 : x1;
-      dy = clampd(-b * dx / c, y0, y1);
-    } else {
-      dy = e == 2 ? y0 : y1;
-      dx = clampd(-b * dy / a, x0, x1);
-    }
-    double q = a * dx * dx + 2 * b * dx * dy + c * dy * dy;
-    if (q < best) best = q;
-  }
-  return best <= thr;
-}
-
-/* supp: per record mx, my, a, b, c, thr -- float32 [v][n][6] (supp_f32 = 1) or
- * double (supp_f32 = 0); NULL = the whole rect is the support. */
-static int in_support(const void *supp, int supp_f32, int64_t rec, int tx, int ty, int tw, int th) {
-  if (!supp) return 1;
-  if (supp_f32) {
-    const float *s = (const float *)supp + 6 * rec;
-    return support_f32(s[0], s[1], s[2], s[3], s[4], s[5], tx, ty, tw, th);
-  }
-  const double *s = (const double *)supp + 6 * rec;
-  return support_f64(s[0], s[1], s[2], s[3], s[4], s[5], tx, ty, tw, th);
-}
-
-/* The tiles of rect row ty that a splat keeps: from the first tile of [x0, x1]
- * that passes in_support to the last one (found by testing inward from each end).
- * The support ellipse is convex and every tile spans the full height of the row,
- * so in exact arithmetic the tiles that meet it are exactly this interval; taking
- * the interval makes the decision one cheap scan from each end.  Returns 0 (and
- * leaves *first > *last) when no tile of the row passes. */
+/* The tiles of rect row ty (rect columns [x0, x1]) that a splat keeps, as above;
+ * supp: per record mx, my, a, b, c, thr -- float32 [v][n][6] (supp_f32 = 1) or
+ * double (supp_f32 = 0); NULL = the whole rect row.  Returns 0 (and leaves
+ * *first > *last) when no tile is kept. */
 static int row_interval(const void *supp, int supp_f32, int64_t rec, int ty, int x0, int x1, int tw, int th,
                         int *first, int *last) {
+  *first = 1;
+  *last = 0;
   int a = x0, b = x1;
-  while (a <= x1 && !in_support(supp, supp_f32, rec, a, ty, tw, th)) ++a;
-  if (a > x1) {
-    *first = 1;
-    *last = 0;
-    return 0;
+  if (supp && supp_f32) {
+    const float *s = (const float *)supp + 6 * rec;
+    float xl, xr;
+    if (!strip_f32(s[0], s[1], s[2], s[3], s[4], s[5], ty, tw, th, &xl, &xr)) return 0;
+    /* the tile bounds, clamped in float to [x0 - 1, x1 + 1] before the conversion */
+    const float fa = fminf(fmaxf(ceilf(((s[0] + xl) - (float)(tw - 1)) / (float)tw), (float)x0), (float)x1 + 1.f);
+    const float fb = fminf(fmaxf(floorf((s[0] + xr) / (float)tw), (float)x0 - 1.f), (float)x1);
+    a = (int)fa;
+    b = (int)fb;
+  } else if (supp) {
+    const double *s = (const double *)supp + 6 * rec;
+    double xl, xr;
+    if (!strip_f64(s[0], s[1], s[2], s[3], s[4], s[5], ty, tw, th, &xl, &xr)) return 0;
+    const double fa = fmin(fmax(ceil(((s[0] + xl) - (double)(tw - 1)) / (double)tw), (double)x0), (double)x1 + 1.0);
+    const double fb = fmin(fmax(floor((s[0] + xr) / (double)tw), (double)x0 - 1.0), (double)x1);
+    a = (int)fa;
+    b = (int)fb;
   }
-  while (b > a && !in_support(supp, supp_f32, rec, b, ty, tw, th)) --b;
+  if (a > b) return 0;
   *first = a;
   *last = b;
   return 1;

@@ -698,27 +698,48 @@ struct EntryInfo {
   uint32_t id, xr;
 };
 
-// The tiles of rect columns [x0, x1] in tile row y that a splat keeps: from the
-// first one that passes tile_in_support to the last one, found by testing inward
-// from each end.  The support ellipse is convex and a tile spans the row's full
-// height, so in exact arithmetic these are exactly the tiles it meets; the
-// interval needs two short scans instead of a test per tile.  a > b when none.
-__device__ __forceinline__ void kept_interval(const SupportSplat &sp, int x0, int x1, int y, int tw, int th, int &a,
-                                              int &b) {
-  a = x0;
-  while (a <= x1 && !tile_in_support(sp, a, y, tw, th)) ++a;
-  b = x1;
-  if (a > x1) {
-    a = 1;
-    b = 0;
-    return;
+// The tiles of rect columns [x0, x1] in tile row y that a splat keeps.  It can
+// reach alpha >= 1/255 only inside E = {q <= thr}, q = a dx^2 + 2 b dx dy + c dy^2;
+// a tile spans the row's pixel-centre rows, so it meets E iff its pixel-centre
+// columns meet [xl, xr], E's x-extent within that strip.  E's left boundary is
+// convex in dy with its minimum -sqrt(thr c / det) at dy = b sqrt(thr c / det) / c
+// (det = a c - b^2); over the strip cut to E's y-range the leftmost point lies at
+// that dy clamped into the range, the rightmost one mirrors it.  Every step is
+// rounded to float32 in a fixed order (explicit intrinsics), so the decision is
+// the same wherever it is taken.  Writes a > b when no tile is kept.
+__device__ __forceinline__ void kept_columns(float mx, float my, float a, float b, float c, float thr, int x0, int x1,
+                                             int y, int tw, int th, int &ta, int &tb) {
+  ta = 1;
+  tb = 0;
+  const float y0 = __fsub_rn((float)(y * th), my), y1 = __fsub_rn((float)(y * th + th - 1), my);
+  const float det = __fsub_rn(__fmul_rn(a, c), __fmul_rn(b, b));
+  if (!(det > 0.f) || !(thr >= 0.f)) return;
+  const float tA = __fmul_rn(thr, a);
+  const float ys = __fsqrt_rn(__fdiv_rn(tA, det)), xs = __fsqrt_rn(__fdiv_rn(__fmul_rn(thr, c), det));
+  const float lo = fmaxf(y0, -ys), hi = fminf(y1, ys);
+  if (lo > hi) return;
+  const float dl = __fdiv_rn(__fmul_rn(b, xs), c);
+  const float yl = fminf(fmaxf(dl, lo), hi), yr = fminf(fmaxf(-dl, lo), hi);
+  const float rl = __fsqrt_rn(fmaxf(__fsub_rn(tA, __fmul_rn(det, __fmul_rn(yl, yl))), 0.f));
+  const float rr = __fsqrt_rn(fmaxf(__fsub_rn(tA, __fmul_rn(det, __fmul_rn(yr, yr))), 0.f));
+  const float xl = __fdiv_rn(__fsub_rn(-__fmul_rn(b, yl), rl), a);
+  const float xr = __fdiv_rn(__fadd_rn(-__fmul_rn(b, yr), rr), a);
+  // tile t is kept iff t tw + tw - 1 >= mx + xl and t tw <= mx + xr (clamped in
+  // float to [x0 - 1, x1 + 1] before the conversion)
+  const float fa = fminf(fmaxf(ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(mx, xl), (float)(tw - 1)), (float)tw)), (float)x0),
+                         (float)x1 + 1.f);
+  const float fb = fminf(fmaxf(floorf(__fdiv_rn(__fadd_rn(mx, xr), (float)tw)), (float)x0 - 1.f), (float)x1);
+  ta = (int)fa;
+  tb = (int)fb;
+  if (ta > tb) {
+    ta = 1;
+    tb = 0;
   }
-  while (b > a && !tile_in_support(sp, b, y, tw, th)) --b;
 }
 
 // Tiles, counting pass: per chunk c of a row list, the number of its records that
 // keep tile x of the row, into tcnt[c * tx_max + x], and every entry's EntryInfo.
-// A thread finds its own record's kept interval.
+// A thread finds its own record's kept columns.
 __global__ void __launch_bounds__(kTileChunk) k_tile_count(RowGeom G, const float4 *__restrict__ splat,
                                                            const uint32_t *__restrict__ srec,
                                                            const uint2 *__restrict__ rect, int tw, int th,
@@ -741,9 +762,10 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_count(RowGeom G, const floa
     if (e < k.e1) {
       const uint32_t rec = srec[rowlist[e]];
       const uint2 rc = rect[rec];
-      const SupportSplat sp = support_splat(splat[2 * (int64_t)rec], splat[2 * (int64_t)rec + 1]);
+      const float4 s0 = splat[2 * (int64_t)rec], s1 = splat[2 * (int64_t)rec + 1];
       int a, b;
-      kept_interval(sp, (int)(rc.x & 0xFFFFu), (int)(rc.y & 0xFFFFu), k.y, tw, th, a, b);
+      kept_columns(s0.x, s0.y, s0.z, s0.w, s1.x, s1.w, (int)(rc.x & 0xFFFFu), (int)(rc.y & 0xFFFFu), k.y, tw, th, a,
+                   b);
       if (a <= b) {
         atomicAdd(&s_cnt[a], 1u);
         atomicAdd(&s_cnt[b + 1], 0xFFFFFFFFu);  // -1 modulo 2^32
@@ -976,9 +998,10 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_emit(RowGeom G, const uint3
       __syncthreads();
       uint32_t before = xb + lane < k.tx ? s_base[xb + lane] : 0u;
       for (int w = 0; w < warp; ++w) before += s_wc[w][lane];
-      // tile by tile, so that the lanes keeping a tile store to consecutive slots
-#pragma unroll 4
-      for (int bit = 0; bit < 32; ++bit) {
+      // tile by tile, so that the lanes keeping a tile store to consecutive slots;
+      // only the tiles some lane of the warp keeps
+      for (uint32_t any = __reduce_or_sync(0xffffffffu, m); any; any &= any - 1u) {
+        const int bit = __ffs(any) - 1;
         const uint32_t cb = __shfl_sync(0xffffffffu, col, bit);
         const uint32_t base = __shfl_sync(0xffffffffu, before, bit);
         if ((m >> bit) & 1u) {

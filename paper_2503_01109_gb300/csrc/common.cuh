@@ -193,43 +193,9 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // Margin added to the opacity-aware support threshold 2 ln(255 o): it exceeds
-// every float32 rounding of the blend's alpha test, so a tile culled by
-// tile_in_support() can hold no pixel whose alpha reaches 1/255.
+// every float32 rounding of the blend's alpha test, so a tile the binning culls
+// (kept_columns() in binsort.cu) can hold no pixel whose alpha reaches 1/255.
 constexpr float kSupportMargin = 0.01f;
-
-// Minimum over the pixel centres of tile (tx, ty) of q(d) = a dx^2 + 2 b dx dy + c dy^2,
-// d = pixel - mean2d, compared with the splat's threshold thr: true when some
-// pixel of the tile may reach alpha >= 1/255.  The minimum of this convex form
-// over a rectangle is 0 when the mean lies inside, else it lies on an edge: at
-// dy = sy dx on a vertical edge and dx = sx dy on a horizontal one (sy = -b/c,
-// sx = -b/a, computed once per splat), clamped to the edge.  Explicit rounding
-// intrinsics make the decision identical wherever it is taken.
-struct SupportSplat {
-  float mx, my, a, b, c, thr, sx, sy;
-};
-
-__device__ __forceinline__ SupportSplat support_splat(float4 g0, float4 g1) {
-  SupportSplat s{g0.x, g0.y, g0.z, g0.w, g1.x, g1.w, 0.f, 0.f};
-  s.sx = __fdiv_rn(-s.b, s.a);
-  s.sy = __fdiv_rn(-s.b, s.c);
-  return s;
-}
-
-__device__ __forceinline__ float support_q(const SupportSplat &s, float dx, float dy) {
-  return __fadd_rn(__fadd_rn(__fmul_rn(s.a, __fmul_rn(dx, dx)), __fmul_rn(2.f, __fmul_rn(s.b, __fmul_rn(dx, dy)))),
-                   __fmul_rn(s.c, __fmul_rn(dy, dy)));
-}
-
-__device__ __forceinline__ bool tile_in_support(const SupportSplat &s, int tx, int ty, int tw, int th) {
-  const float x0 = __fsub_rn((float)(tx * tw), s.mx), x1 = __fsub_rn((float)(tx * tw + tw - 1), s.mx);
-  const float y0 = __fsub_rn((float)(ty * th), s.my), y1 = __fsub_rn((float)(ty * th + th - 1), s.my);
-  if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
-  const float q0 = support_q(s, x0, fminf(fmaxf(__fmul_rn(s.sy, x0), y0), y1));
-  const float q1 = support_q(s, x1, fminf(fmaxf(__fmul_rn(s.sy, x1), y0), y1));
-  const float q2 = support_q(s, fminf(fmaxf(__fmul_rn(s.sx, y0), x0), x1), y0);
-  const float q3 = support_q(s, fminf(fmaxf(__fmul_rn(s.sx, y1), x0), x1), y1);
-  return fminf(fminf(q0, q1), fminf(q2, q3)) <= s.thr;
-}
 
 // Round-to-nearest float -> bf16 bits (ties to even), finite inputs.
 __device__ __forceinline__ uint16_t f2bf(float x) {
