@@ -448,7 +448,7 @@ __global__ void k_mlp_adam(fgs_mlp_master ms, const float *__restrict__ grad, fg
 // Learned prior on freshly written high-frequency seeds: features, inference, then per seed the
 // predicted opacity logit, and the predicted log-scales unless one axis lies
 // further than max_dev from eq11's log-scale (then eq11's radius stays: eq11 is
-// the judge of the scale; it says nothing about opacity).
+// what arbitrates the scale; it says nothing about opacity).
 __global__ void k_apply_prior(const float *__restrict__ pred, const int32_t *__restrict__ xy,
                               const uint8_t *__restrict__ seed_hi, const int64_t *__restrict__ base,
                               const float *__restrict__ depth, int W, float alpha_h, float alpha_l, float f,
