@@ -336,6 +336,23 @@ size_t fgs_project_bwd_adam_workspace_size(int64_t n);
 fgs_status fgs_grid_barrier_probe(int32_t n_blocks, int32_t n_expected, int64_t timeout_ns, void *ws,
                                   size_t ws_bytes, uint32_t *d_passed, int32_t *d_status, void *stream);
 
+/* fgs_lookback_probe -- self-test of the bounded decoupled look-back that chains
+ * the tiles of the binning's depth sort (the paper has no counterpart: this is the
+ * failure detection of that wait).  n_tiles CTAs each take a tile by ticket, publish
+ * a count of 1 for each of 256 digits and sum the counts of the earlier tiles, as a
+ * sort pass does.  With skip_first the first tile publishes nothing, so every later
+ * wait can only end by its limit: it gives up after timeout_ns, or-es
+ * FGS_DEV_TIMEOUT into *d_status and returns, leaving the context usable.
+ * out: sums [n_tiles][256] int32: tile t's sums (t everywhere when no wait gave
+ *   up; the first tile's row is left unwritten with skip_first).
+ * ws: fgs_lookback_probe_workspace_size(n_tiles) bytes, 256-byte aligned (cleared
+ *   by the call).
+ * err: INVALID_ARGUMENT unless 1 <= n_tiles <= 4096 and 1 us <= timeout_ns <= 5 s;
+ *   NULLs; small workspace. */
+fgs_status fgs_lookback_probe(int32_t n_tiles, int32_t skip_first, int64_t timeout_ns, void *ws,
+                              size_t ws_bytes, int32_t *sums, int32_t *d_status, void *stream);
+size_t fgs_lookback_probe_workspace_size(int32_t n_tiles);
+
 /* ---------------------------------------------------------------------------------
  * fgs_prune -- Gaussian pruning (Sec. III-A, "Gaussian Pruning"): removes every
  * Gaussian that has grown too large in some dimension or whose opacity is below a

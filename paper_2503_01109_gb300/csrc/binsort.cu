@@ -128,6 +128,62 @@ __device__ __forceinline__ uint64_t sort_ns() {
   return t;
 }
 
+// Thread d's decoupled look-back for tile t over flags [tiles][256]: the sum of
+// digit d's counts over tiles 0 .. t - 1, reading kLookback earlier tiles' flags
+// at a time and summing own counts until it meets a running prefix.  A flag that
+// stays unknown for timeout_ns sets FGS_DEV_TIMEOUT and ends the wait (the sum is
+// then incomplete).
+__device__ __forceinline__ uint32_t lookback_sum(const uint32_t *flags, uint32_t t, int d, uint64_t timeout_ns,
+                                                 int32_t *d_status) {
+  uint32_t excl = 0;
+  int64_t j = (int64_t)t - 1;
+  const uint64_t t0 = sort_ns();
+  for (;;) {
+    uint32_t f[kLookback];
+#pragma unroll
+    for (int q = 0; q < kLookback; ++q) f[q] = j - q >= 0 ? ld_flag(flags + (size_t)(j - q) * 256 + d) : kFlagPrefix;
+    int q = 0;
+    bool done = false;
+#pragma unroll
+    for (; q < kLookback; ++q) {
+      const uint32_t st = f[q] & ~kFlagValue;
+      if (st == 0) break;  // not yet published: read again from here
+      excl += f[q] & kFlagValue;
+      if (st == kFlagPrefix) {
+        done = true;
+        break;
+      }
+    }
+    if (done) break;
+    j -= q;
+    if (q == 0 && sort_ns() - t0 > timeout_ns) {
+      if (d_status) atomicOr(d_status, FGS_DEV_TIMEOUT);
+      break;
+    }
+  }
+  return excl;
+}
+
+// The look-back alone, for its self-test: each CTA takes a tile by ticket and
+// publishes a count of 1 for each of the 256 digits, except the first tile when
+// skip_first (its flags then never become known, so every later wait can only end
+// by its limit); each tile's sums go to sums[t][d].
+__global__ void __launch_bounds__(kSortThreads) k_lookback_probe(uint32_t *__restrict__ flags,
+                                                                 uint32_t *__restrict__ ticket, int skip_first,
+                                                                 int64_t timeout_ns, int32_t *__restrict__ sums,
+                                                                 int32_t *d_status) {
+  __shared__ uint32_t s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const int d = threadIdx.x;
+  if (t == 0 && skip_first) return;
+  st_flag(flags + (size_t)t * 256 + d, (t == 0 ? kFlagPrefix : kFlagAgg) | 1u);
+  const uint32_t excl = t > 0 ? lookback_sum(flags, t, d, (uint64_t)timeout_ns, d_status) : 0u;
+  if (t > 0) st_flag(flags + (size_t)t * 256 + d, kFlagPrefix | (excl + 1u));
+  sums[(size_t)t * 256 + d] = (int32_t)excl;
+}
+
 // One stable LSD pass over the digit (key >> shift) & (2^nbits - 1).  Each CTA
 // takes the next 1024-item tile by ticket (so every tile it waits for belongs to
 // a CTA that is already running), ranks the tile stably with per-bit warp ballots,
@@ -199,32 +255,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
   // look-back over the earlier tiles for digit d
   uint32_t excl = 0;
   if (t > 0) {
-    int64_t j = (int64_t)t - 1;
-    const uint64_t t0 = sort_ns();
-    for (;;) {
-      uint32_t f[kLookback];
-#pragma unroll
-      for (int q = 0; q < kLookback; ++q)
-        f[q] = j - q >= 0 ? ld_flag(flags + (size_t)(j - q) * 256 + d) : kFlagPrefix;
-      int q = 0;
-      bool done = false;
-#pragma unroll
-      for (; q < kLookback; ++q) {
-        const uint32_t st = f[q] & ~kFlagValue;
-        if (st == 0) break;  // not yet published: read again from here
-        excl += f[q] & kFlagValue;
-        if (st == kFlagPrefix) {
-          done = true;
-          break;
-        }
-      }
-      if (done) break;
-      j -= q;
-      if (q == 0 && sort_ns() - t0 > kLookbackTimeoutNs) {
-        if (d_status) atomicOr(d_status, FGS_DEV_TIMEOUT);
-        break;
-      }
-    }
+    excl = lookback_sum(flags, t, d, kLookbackTimeoutNs, d_status);
     st_flag(my_flags + d, kFlagPrefix | (excl + run));
   }
   s_base[d] = digit_start + excl;
@@ -475,6 +506,36 @@ __device__ __forceinline__ void record_rows(const RowGeom &G, const uint2 *__res
   g1 = G.row_base[v] + (int)(rc.y >> 16);
 }
 
+// Exclusive scan of one value per thread over a CTA of 1024 threads with warp
+// shuffles and two barriers; `total` receives the sum.  s_warp holds 33 words;
+// the caller synchronises before s_warp is written again.
+__device__ __forceinline__ unsigned long long cta1024_exclusive(unsigned long long x, unsigned long long *s_warp,
+                                                                unsigned long long &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long v = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) s_warp[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long w = s_warp[lane];
+    unsigned long long wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    s_warp[lane] = wi - w;
+    if (lane == 31) s_warp[32] = wi;
+  }
+  __syncthreads();
+  total = s_warp[32];
+  return s_warp[warp] + v - x;
+}
+
 // Exclusive scan of n counts in place by one CTA of 1024 threads (a consecutive
 // slice per thread); every thread gets the total.
 __device__ uint64_t cta_scan_inplace(uint32_t *__restrict__ a, int64_t n, unsigned long long *part) {
@@ -482,21 +543,13 @@ __device__ uint64_t cta_scan_inplace(uint32_t *__restrict__ a, int64_t n, unsign
   const int64_t lo = threadIdx.x * per, hi = min(n, lo + per);
   unsigned long long s = 0;
   for (int64_t i = lo; i < hi; ++i) s += a[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    const unsigned long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  unsigned long long run = part[threadIdx.x] - s;
+  unsigned long long total;
+  unsigned long long run = cta1024_exclusive(s, part, total);
   for (int64_t i = lo; i < hi; ++i) {
     const uint32_t v = a[i];
     a[i] = (uint32_t)run;
     run += v;
   }
-  const uint64_t total = part[1023];
   __syncthreads();
   return total;
 }
@@ -555,7 +608,7 @@ __global__ void __launch_bounds__(kRecChunk) k_row_count(RowGeom G, const uint32
 __global__ void __launch_bounds__(1024) k_row_scan(const int64_t *__restrict__ d_vis, int64_t nb_cap,
                                                    uint32_t *__restrict__ rowcnt, uint32_t *__restrict__ rowtot) {
   pdl_enter();
-  __shared__ unsigned long long part[1024];
+  __shared__ unsigned long long part[33];
   const int64_t nb = (*d_vis + kRecChunk - 1) / kRecChunk;
   const uint64_t total = cta_scan_inplace(rowcnt + (int64_t)blockIdx.x * nb_cap, nb, part);
   if (threadIdx.x == 0) rowtot[blockIdx.x] = (uint32_t)min(total, (uint64_t)0xFFFFFFFFu);
@@ -573,7 +626,7 @@ __global__ void __launch_bounds__(1024) k_row_starts(RowGeom G, const uint32_t *
                                                      int64_t *__restrict__ d_num_pairs,
                                                      int64_t *__restrict__ d_sort_count) {
   pdl_enter();
-  __shared__ unsigned long long part[1024];
+  __shared__ unsigned long long part[33];
   __shared__ int s_over;
   const int NR = G.n_rows;
   for (int g = threadIdx.x; g < NR; g += 1024) row_start[g] = rowtot[g];
@@ -867,28 +920,20 @@ __global__ void __launch_bounds__(1024) k_tile_row_starts(RowGeom G, unsigned lo
                                                           int32_t *__restrict__ d_status,
                                                           int64_t *__restrict__ d_sort_count) {
   pdl_enter();
-  __shared__ unsigned long long part[1024];
+  __shared__ unsigned long long part[33];
   const int NR = G.n_rows;
   const int per = (NR + 1023) / 1024;
   const int lo = threadIdx.x * per, hi = min(NR, lo + per);
   unsigned long long s = 0;
   for (int i = lo; i < hi; ++i) s += rowp[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    const unsigned long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  unsigned long long run = part[threadIdx.x] - s;
+  unsigned long long total;
+  unsigned long long run = cta1024_exclusive(s, part, total);
   for (int i = lo; i < hi; ++i) {
     const unsigned long long v = rowp[i];
     rowp[i] = run;
     run += v;
   }
   if (threadIdx.x == 1023) {
-    const unsigned long long total = part[1023];
     if (*d_sort_count < 0) {  // the row lists overflowed: no pairs, count already recorded
       *d_sort_count = 0;
     } else {
@@ -1200,4 +1245,26 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   count_launch(5);
   FGS_CHECK_LAUNCH("fgs_bin_sort tiles");
   return FGS_OK;
+}
+
+extern "C" fgs_status fgs_lookback_probe(int32_t n_tiles, int32_t skip_first, int64_t timeout_ns, void *ws,
+                                         size_t ws_bytes, int32_t *sums, int32_t *d_status, void *stream) {
+  FGS_CHECK_ARG(n_tiles >= 1 && n_tiles <= 4096, "fgs_lookback_probe: n_tiles must be 1..4096");
+  FGS_CHECK_ARG(timeout_ns >= 1000 && timeout_ns <= 5000000000ll, "fgs_lookback_probe: timeout_ns");
+  FGS_CHECK_ARG(sums && d_status, "fgs_lookback_probe: NULL argument");
+  const size_t need = fgs_lookback_probe_workspace_size(n_tiles);
+  FGS_CHECK_ARG(ws && ws_bytes >= need && (reinterpret_cast<uintptr_t>(ws) & 255) == 0,
+                "fgs_lookback_probe: workspace");
+  cudaStream_t st = as_stream(stream);
+  FGS_CUDA(cudaMemsetAsync(ws, 0, need, st), "fgs_lookback_probe: clear");
+  uint32_t *flags = static_cast<uint32_t *>(ws);
+  uint32_t *ticket = flags + (size_t)n_tiles * 256;
+  k_lookback_probe<<<n_tiles, kSortThreads, 0, st>>>(flags, ticket, skip_first, timeout_ns, sums, d_status);
+  count_launch();
+  FGS_CHECK_LAUNCH("fgs_lookback_probe");
+  return FGS_OK;
+}
+
+extern "C" size_t fgs_lookback_probe_workspace_size(int32_t n_tiles) {
+  return n_tiles < 1 ? 0 : align_up((size_t)n_tiles * 256 * 4 + 4);
 }

@@ -173,6 +173,8 @@ _OPTIONAL = {
     "fgs_render_window_workspace_size": ([c_void_p, c_int32], c_size_t),
     "fgs_loss_noalloc": ([c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                           c_void_p, c_void_p], c_int32),
+    "fgs_lookback_probe": ([c_int32, c_int32, c_int64, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_lookback_probe_workspace_size": ([c_int32], c_size_t),
     "fgs_grid_barrier_probe": ([c_int32, c_int32, c_int64, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p],
                                c_int32),
     "fgs_autotune": ([c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p,
@@ -442,6 +444,16 @@ def fgs_loss_noalloc(cams: list, color, depth, color_gt, depth_gt, w_c, w_d, w_s
     _check(lib().fgs_loss_noalloc(camera_array(cams), len(cams), _ptr(color), _ptr(depth), _ptr(color_gt),
                                   _ptr(depth_gt), ctypes.byref(p), _ptr(dC), _ptr(dD), _ptr(loss_acc), _stream()),
            "fgs_loss_noalloc")
+
+
+def fgs_lookback_probe(n_tiles: int, skip_first: bool, timeout_ns: int, ws, sums, status):
+    _check(lib().fgs_lookback_probe(int(n_tiles), 1 if skip_first else 0, int(timeout_ns), _ptr(ws),
+                                    ws.numel() * ws.element_size(), _ptr(sums), _ptr(status), _stream()),
+           "fgs_lookback_probe")
+
+
+def fgs_lookback_probe_workspace_size(n_tiles: int) -> int:
+    return int(lib().fgs_lookback_probe_workspace_size(int(n_tiles)))
 
 
 def fgs_grid_barrier_probe(n_blocks: int, n_expected: int, timeout_ns: int, ws, passed, status):

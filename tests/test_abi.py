@@ -70,6 +70,25 @@ def test_barrier_probe_argument_checks(lib):
     assert rc == 1 and b"NULL" in L.fgs_last_error()
 
 
+def test_lookback_probe_argument_checks(lib):
+    """fgs_lookback_probe refuses bad tile counts, limits, NULLs and small
+    workspaces before any CUDA call."""
+    from paper_2503_01109_gb300 import fgs
+    L = fgs.lib()
+    assert L.fgs_lookback_probe_workspace_size(0) == 0
+    need = L.fgs_lookback_probe_workspace_size(10)
+    assert need >= 10 * 256 * 4
+    word = ctypes.c_int32(0)
+    p = ctypes.cast(ctypes.byref(word), ctypes.c_void_p)
+    fake_ws = ctypes.c_void_p(1 << 20)  # never dereferenced: every case fails its checks first
+    for n, timeout_ns, ws_bytes in ((0, 10**6, need), (5000, 10**6, need), (10, 10, need), (10, 6 * 10**9, need),
+                                    (10, 10**6, need - 1)):
+        rc = L.fgs_lookback_probe(n, 0, timeout_ns, fake_ws, ws_bytes, p, p, None)
+        assert rc == 1, (n, timeout_ns, ws_bytes)
+    rc = L.fgs_lookback_probe(10, 0, 10**6, fake_ws, need, None, p, None)
+    assert rc == 1 and b"NULL" in L.fgs_last_error()
+
+
 def test_kernel_timer_selects_spans():
     """The bench's timer records only the spans it was enabled for (no events are
     created for the others, so nothing here needs a GPU)."""

@@ -133,3 +133,33 @@ def test_checkpoint_resume(cuda_device, tmp_path):
     for x, y in ((resumed.g.buf, whole.g.buf), (resumed.m.buf, whole.m.buf)):
         close = torch.isclose(x, y, rtol=1e-4, atol=1e-5)
         assert close.float().mean().item() > 0.999
+
+
+def test_lookback_completes_and_gives_up(cuda_device):
+    """The depth sort's decoupled look-back: 300 tiles chained through it sum to
+    their index; when the first tile never publishes, every later wait gives up
+    after its limit with FGS_DEV_TIMEOUT and the context stays usable."""
+    n = 300
+    ws = fgs.ws_tensor(fgs.fgs_lookback_probe_workspace_size(n), "cuda")
+    sums = torch.full((n, 256), -1, dtype=torch.int32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    fgs.fgs_lookback_probe(n, False, 1_000_000_000, ws, sums, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert torch.equal(sums, torch.arange(n, dtype=torch.int32, device="cuda")[:, None].expand(n, 256))
+    sums.fill_(-1)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    fgs.fgs_lookback_probe(n, True, 50_000_000, ws, sums, status)
+    t1.record()
+    torch.cuda.synchronize()
+    assert int(status.item()) == fgs.FGS_DEV_TIMEOUT
+    assert 40.0 <= t0.elapsed_time(t1) < 2000.0
+    assert torch.all(sums[0] == -1)
+    with pytest.raises(fgs.FGSError):
+        fgs.fgs_lookback_probe(0, False, 50_000_000, ws, sums, status)
+    m = _mapper(syn.tiny_scene(2000, 0))
+    m.set_target(*_target())
+    m.iteration()
+    m.check_status()
+    assert torch.isfinite(m.loss_acc).all()
