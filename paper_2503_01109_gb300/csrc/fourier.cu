@@ -1,7 +1,8 @@
 // fourier.cu -- adaptive densification of Sec. III-A (eq2-eq11) for one frame.
 //
 //   k_fft_rows      gray = BT.601 luma of the frame, eq2's DFT along x for every row
-//   k_fft_cols      per group of columns: DFT along y, the Gaussian high-pass of
+//   k_fft_cols      per group of columns of the spectrum's left half (the right
+//                   half is its conjugate mirror): DFT along y, the Gaussian high-pass of
 //                   eq5/eq7 evaluated at the shifted frequency (eq3), inverse DFT
 //                   along y -- forward, filter and inverse fused in shared memory
 //   k_ifft_rows     inverse DFT along x, E = |I_h| / (H W) (eq8), running max of E
@@ -33,7 +34,7 @@ namespace fgs {
 
 constexpr int kFftMaxStages = 16;
 constexpr int kFftThreads = 256;
-constexpr int kColGroup = 2;    // columns per CTA in the column pass (1 for very tall frames)
+constexpr int kColGroup = 1;    // columns per CTA in the column pass
 constexpr int kColThreads = 128;  // six column CTAs per SM hide the stages' latency
 constexpr size_t kSmemMax = 227 * 1024;
 
@@ -227,14 +228,18 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows(const float *__restric
 }
 
 // Along y for cg columns: forward DFT, eq5/eq7 high-pass at the centred
-// frequency (eq3 read as the spectrum shift), inverse DFT.
+// frequency (eq3 read as the spectrum shift), inverse DFT.  Only columns
+// u = 0 .. W/2 are transformed: the frame is real, so its spectrum is Hermitian,
+// F(W - u, H - v) = conj F(u, v), and so is the filtered one (the high-pass is
+// even in u and v); after the inverse along y, column W - u is then the complex
+// conjugate of column u, and it is written from it.
 __global__ void __launch_bounds__(kColThreads, 6) k_fft_cols(float2 *__restrict__ spec, int W, int H, FftPlan plan,
                                                           float d0, int cg) {
   pdl_enter();
   extern __shared__ float2 sm2[];
   float2 *a = sm2, *b = sm2 + H * cg, *tw = sm2 + 2 * H * cg;
   const int x0 = blockIdx.x * cg;
-  const int ncol = min(cg, W - x0);
+  const int ncol = min(cg, W / 2 + 1 - x0);
   fft_twiddles(tw, H);
   for (int e = threadIdx.x; e < H * cg; e += blockDim.x) {
     const int y = e / cg, c = e - y * cg;
@@ -259,7 +264,11 @@ __global__ void __launch_bounds__(kColThreads, 6) k_fft_cols(float2 *__restrict_
   float2 *g = fft_smem(f, other, plan, cg, 1.f, tw);
   for (int e = threadIdx.x; e < H * cg; e += blockDim.x) {
     const int y = e / cg, c = e - y * cg;
-    if (c < ncol) spec[(int64_t)y * W + x0 + c] = g[e];
+    if (c < ncol) {
+      const int u = x0 + c, m = W - u;  // m: the mirror column
+      spec[(int64_t)y * W + u] = g[e];
+      if (u > 0 && m > u) spec[(int64_t)y * W + m] = make_float2(g[e].x, -g[e].y);
+    }
   }
 }
 
@@ -662,7 +671,7 @@ extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_g
   if (smem_col > 48 * 1024)
     FGS_CUDA(cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col), "attr");
   pdl_launch(k_fft_rows, H, kFftThreads, smem_row, st, rgb_gt, W, H, px, w.spec, w.max_bits + 1);
-  pdl_launch(k_fft_cols, (W + cg - 1) / cg, kColThreads, smem_col, st, w.spec, W, H, py, prm->d0, cg);
+  pdl_launch(k_fft_cols, (W / 2 + 1 + cg - 1) / cg, kColThreads, smem_col, st, w.spec, W, H, py, prm->d0, cg);
   pdl_launch(k_ifft_rows, H, kFftThreads, smem_row, st, w.spec, W, H, px, E, w.max_bits);
   pdl_launch(k_hist, 4 * num_sms(), 256, 0, st, E, HW, w.max_bits, w.hist);
   pdl_launch(k_triangle, 1, 256, 0, st, w.hist, d_threshold);

@@ -12,7 +12,7 @@ from paper_2503_01109_gb300.mapping import Mapper
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [(64, 48), (70, 45), (48, 64), (640, 480), (1200, 680)]
+SIZES = [(64, 48), (70, 45), (45, 64), (48, 64), (640, 480), (1200, 680)]  # (45, 64): an odd width
 
 
 def run_seed(W, H, seed, with_render=True, max_new=50000, capacity=None, prior=None, pose=None, grids=None):
