@@ -72,7 +72,8 @@ enum {
   FGS_DEV_TIMEOUT = 2,       /* a bounded device wait gave up                         */
   FGS_DEV_NONFINITE = 4,     /* a non-finite value was met where one is not allowed   */
   FGS_DEV_MAP_FULL = 8,      /* seeding wanted more Gaussians than the map capacity   */
-  FGS_DEV_WORK_OVERFLOW = 16 /* a window work list exceeded its capacity              */
+  FGS_DEV_WORK_OVERFLOW = 16, /* a window work list exceeded its capacity             */
+  FGS_DEV_BAD_ORDER = 32      /* a tile_order entry outside the view set's tiles       */
 };
 
 #define FGS_MAX_VIEWS 16
@@ -176,12 +177,19 @@ size_t fgs_bin_sort_workspace_size(const fgs_camera *cams, int32_t n_views, fgs_
  *   sum z alpha T), alpha [H][W] (sum alpha T), t_final [H][W] (T after the last
  *   blended Gaussian), n_contrib [H][W] (1 + list position of the last blended
  *   Gaussian, 0 if none).  The backward reads t_final and n_contrib.
- * Background is 0. */
+ * Background is 0.
+ * tile_order: NULL, or a permutation of the view set's tiles [total_tiles] int32
+ *   (device; e.g. from fgs_tile_order) giving the order in which the tiles'
+ *   CTAs are launched.  A permutation changes no output, only how well the
+ *   launch fills the GPU.  The entries are not checked for being one: a tile
+ *   missing from the list is not rendered, a repeated one is rendered (and by
+ *   the adjoint accumulated) twice.  An entry outside 0 .. total_tiles - 1 is
+ *   skipped and or-es FGS_DEV_BAD_ORDER into *d_status when d_status is not NULL. */
 fgs_status fgs_render_fwd(const fgs_projected *proj, const fgs_gaussians *g,
                           const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
-                          const int32_t *ids, const int32_t *tile_ranges, float *color,
-                          float *depth, float *alpha, float *t_final, int32_t *n_contrib,
-                          int32_t *d_status, void *stream);
+                          const int32_t *ids, const int32_t *tile_ranges,
+                          const int32_t *tile_order, float *color, float *depth, float *alpha,
+                          float *t_final, int32_t *n_contrib, int32_t *d_status, void *stream);
 
 /* fgs_render_fwd_sampled -- fgs_render_fwd on the grid of pixels with
  * x % s == 0 and y % s == 0 (s = sample_stride, which must be 2; tiling 16x16 or
@@ -191,13 +199,28 @@ fgs_status fgs_render_fwd(const fgs_projected *proj, const fgs_gaussians *g,
  * a grid: the seeding step (fgs_fourier_seed) places seeds only on the m- and
  * n-grids of Sec. III-A, so with m and n even its seeds are those of a full render
  * (its mask's bit 2, M_m, then reflects the background off the grid).  One thread
- * per grid pixel: a quarter of the blending work. */
+ * per grid pixel: a quarter of the blending work.  tile_order as fgs_render_fwd. */
 fgs_status fgs_render_fwd_sampled(const fgs_projected *proj, const fgs_gaussians *g,
                                   const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
                                   const int32_t *ids, const int32_t *tile_ranges,
-                                  int32_t sample_stride, float *color, float *depth, float *alpha,
-                                  float *t_final, int32_t *n_contrib, int32_t *d_status,
-                                  void *stream);
+                                  const int32_t *tile_order, int32_t sample_stride, float *color,
+                                  float *depth, float *alpha, float *t_final, int32_t *n_contrib,
+                                  int32_t *d_status, void *stream);
+
+/* fgs_tile_order -- the launch order of the render calls' tiles, heaviest first:
+ * the view set's tiles sorted by the largest n_contrib of their pixels
+ * (descending, capped at 4095; tiles with equal keys in no fixed order).  One
+ * CTA renders one tile and a tile's work grows with that count, so launching
+ * the heavy tiles first keeps the SMs busy to the end of the launch (longest
+ * processing time first).  n_contrib: a render's [n_views][H][W] output (the
+ * forward whose adjoint follows, or a recent render of the same views: any
+ * n_contrib gives a valid permutation).
+ * out: tile_order [total_tiles] int32 (device), a permutation of 0 .. total_tiles-1.
+ * ws: fgs_tile_order_workspace_size(...) bytes (device).  Two kernel launches. */
+fgs_status fgs_tile_order(const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
+                          const int32_t *n_contrib, int32_t *tile_order, void *ws, size_t ws_bytes,
+                          void *stream);
+size_t fgs_tile_order_workspace_size(const fgs_camera *cams, int32_t n_views, fgs_tiling tiling);
 
 /* ---------------------------------------------------------------------------------
  * fgs_render_bwd -- reverse-mode adjoint of fgs_render_fwd and fgs_project: the
@@ -207,11 +230,13 @@ fgs_status fgs_render_fwd_sampled(const fgs_projected *proj, const fgs_gaussians
  * stored per (pixel, Gaussian).
  * grad2d: scratch [n_views][stride][8] floats (zeroed by the call).
  * grads : gradients are ADDED into grads' planes (caller zeroes them); layout as g.
- * dL_ddepth and dL_dalpha may be NULL (treated as zero). */
+ * dL_ddepth and dL_dalpha may be NULL (treated as zero).
+ * tile_order as fgs_render_fwd (the forward's n_contrib through fgs_tile_order
+ *   gives this call's heaviest-first order). */
 fgs_status fgs_render_bwd(const fgs_gaussians *g, const fgs_projected *proj,
                           const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
                           const int32_t *ids, const int32_t *tile_ranges,
-                          const float *t_final, const int32_t *n_contrib,
+                          const int32_t *tile_order, const float *t_final, const int32_t *n_contrib,
                           const float *dL_dcolor, const float *dL_ddepth,
                           const float *dL_dalpha, float *grad2d, fgs_gaussians *grads,
                           int32_t *d_status, void *stream);
@@ -225,7 +250,8 @@ fgs_status fgs_render_bwd(const fgs_gaussians *g, const fgs_projected *proj,
 fgs_status fgs_render_bwd_splats(const fgs_gaussians *g, const fgs_projected *proj,
                                  const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
                                  const int32_t *ids, const int32_t *tile_ranges,
-                                 const float *t_final, const int32_t *n_contrib,
+                                 const int32_t *tile_order, const float *t_final,
+                                 const int32_t *n_contrib,
                                  const float *dL_dcolor, const float *dL_ddepth,
                                  const float *dL_dalpha, float *grad2d, fgs_gaussians *grads,
                                  int32_t *d_status, void *stream);

@@ -19,11 +19,22 @@
 namespace fgs {
 
 
+// Tile of this CTA: blockIdx.x, or its entry of the launch order (fgs_tile_order).
+// An entry outside the view set's tiles is reported and its CTA does nothing.
+__device__ __forceinline__ int ordered_tile(const int32_t *order, int total_tiles, int32_t *d_status) {
+  if (!order) return blockIdx.x;
+  const int t = order[blockIdx.x];
+  if ((unsigned)t < (unsigned)total_tiles) return t;
+  if (d_status && threadIdx.x == 0) atomicOr(d_status, FGS_DEV_BAD_ORDER);
+  return -1;
+}
+
 template <int TW, int TH, int BATCH, int PX, int S = 1>
 __global__ void __launch_bounds__((TW / S) * (TH / S) / PX) k_render_fwd(RenderArgs a) {
   pdl_enter();
   __shared__ __align__(16) char smem[TileSmem<BATCH>::fwd];
-  render_fwd_tile<TW, TH, BATCH, PX, S>(a, blockIdx.x, smem);
+  const int t = ordered_tile(a.order, a.vs.total_tiles, a.d_status);
+  if (t >= 0) render_fwd_tile<TW, TH, BATCH, PX, S>(a, t, smem);
 }
 
 #ifndef FGS_BWD_MINB
@@ -33,7 +44,8 @@ template <int TW, int TH, int BATCH, int PX>
 __global__ void __launch_bounds__(TW *TH / PX, FGS_BWD_MINB) k_render_bwd(RenderBwdArgs a) {
   pdl_enter();
   __shared__ __align__(16) char smem[TileSmem<BATCH>::bwd];
-  render_bwd_tile<TW, TH, BATCH, PX>(a, blockIdx.x, smem);
+  const int t = ordered_tile(a.order, a.vs.total_tiles, a.d_status);
+  if (t >= 0) render_bwd_tile<TW, TH, BATCH, PX>(a, t, smem);
 }
 
 template <int TW, int TH, int BATCH>
@@ -82,10 +94,9 @@ using namespace fgs;
 
 extern "C" fgs_status fgs_render_fwd(const fgs_projected *proj, const fgs_gaussians *g,
                                      const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
-                                     const int32_t *ids, const int32_t *tile_ranges, float *color,
-                                     float *depth, float *alpha, float *t_final, int32_t *n_contrib,
-                                     int32_t *d_status, void *stream) {
-  (void)d_status;
+                                     const int32_t *ids, const int32_t *tile_ranges,
+                                     const int32_t *tile_order, float *color, float *depth, float *alpha,
+                                     float *t_final, int32_t *n_contrib, int32_t *d_status, void *stream) {
   FGS_CHECK_ARG(proj && proj->splat, "fgs_render_fwd: NULL projection");
   if (!gaussians_ok(g, "g")) return FGS_ERR_INVALID_ARGUMENT;
   FGS_CHECK_ARG(tiling_ok(tiling), "fgs_render_fwd: unsupported tiling");
@@ -95,7 +106,8 @@ extern "C" fgs_status fgs_render_fwd(const fgs_projected *proj, const fgs_gaussi
   DevViews vs;
   if (!make_views(cams, n_views, tiling.tile_w, tiling.tile_h, &vs)) return FGS_ERR_INVALID_ARGUMENT;
   RenderArgs a{vs, reinterpret_cast<const float4 *>(proj->splat), proj->stride, g->rgb, g->capacity, ids,
-               reinterpret_cast<const int2 *>(tile_ranges), color, depth, alpha, t_final, n_contrib};
+               reinterpret_cast<const int2 *>(tile_ranges), color, depth, alpha, t_final, n_contrib,
+               tile_order, d_status};
   FGS_DISPATCH_TILING(tiling, launch_fwd, a, vs.total_tiles, as_stream(stream));
   count_launch();
   FGS_CHECK_LAUNCH("fgs_render_fwd");
@@ -104,10 +116,10 @@ extern "C" fgs_status fgs_render_fwd(const fgs_projected *proj, const fgs_gaussi
 
 extern "C" fgs_status fgs_render_fwd_sampled(const fgs_projected *proj, const fgs_gaussians *g,
                                              const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
-                                             const int32_t *ids, const int32_t *tile_ranges, int32_t sample_stride,
-                                             float *color, float *depth, float *alpha, float *t_final,
-                                             int32_t *n_contrib, int32_t *d_status, void *stream) {
-  (void)d_status;
+                                             const int32_t *ids, const int32_t *tile_ranges,
+                                             const int32_t *tile_order, int32_t sample_stride, float *color,
+                                             float *depth, float *alpha, float *t_final, int32_t *n_contrib,
+                                             int32_t *d_status, void *stream) {
   FGS_CHECK_ARG(proj && proj->splat, "fgs_render_fwd_sampled: NULL projection");
   if (!gaussians_ok(g, "g")) return FGS_ERR_INVALID_ARGUMENT;
   FGS_CHECK_ARG(tiling_ok(tiling), "fgs_render_fwd_sampled: unsupported tiling");
@@ -119,7 +131,8 @@ extern "C" fgs_status fgs_render_fwd_sampled(const fgs_projected *proj, const fg
   DevViews vs;
   if (!make_views(cams, n_views, tiling.tile_w, tiling.tile_h, &vs)) return FGS_ERR_INVALID_ARGUMENT;
   RenderArgs a{vs, reinterpret_cast<const float4 *>(proj->splat), proj->stride, g->rgb, g->capacity, ids,
-               reinterpret_cast<const int2 *>(tile_ranges), color, depth, alpha, t_final, n_contrib};
+               reinterpret_cast<const int2 *>(tile_ranges), color, depth, alpha, t_final, n_contrib,
+               tile_order, d_status};
   cudaStream_t st = as_stream(stream);
   const int bd = tiling.batch_depth, blocks = vs.total_tiles;
   if (tiling.tile_h == 16) {
@@ -140,12 +153,12 @@ extern "C" fgs_status fgs_render_fwd_sampled(const fgs_projected *proj, const fg
 
 static fgs_status render_bwd_splats(const fgs_gaussians *g, const fgs_projected *proj, const DevViews &vs,
                                     fgs_tiling tiling, const int32_t *ids, const int32_t *tile_ranges,
-                                    const float *t_final, const int32_t *n_contrib, const float *dL_dcolor,
-                                    const float *dL_ddepth, const float *dL_dalpha, float *grad2d,
-                                    fgs_gaussians *grads, cudaStream_t st) {
+                                    const int32_t *tile_order, const float *t_final, const int32_t *n_contrib,
+                                    const float *dL_dcolor, const float *dL_ddepth, const float *dL_dalpha,
+                                    float *grad2d, fgs_gaussians *grads, int32_t *d_status, cudaStream_t st) {
   RenderBwdArgs a{vs,      reinterpret_cast<const float4 *>(proj->splat), proj->stride, g->rgb, g->capacity,
                   ids,     reinterpret_cast<const int2 *>(tile_ranges), t_final, n_contrib, dL_dcolor,
-                  dL_ddepth, dL_dalpha, grad2d, grads->rgb};
+                  dL_ddepth, dL_dalpha, grad2d, grads->rgb, tile_order, d_status};
   FGS_DISPATCH_TILING(tiling, launch_bwd, a, vs.total_tiles, st);
   count_launch();
   FGS_CHECK_LAUNCH("fgs_render_bwd");
@@ -169,27 +182,25 @@ static fgs_status check_bwd_args(const fgs_gaussians *g, const fgs_projected *pr
 extern "C" fgs_status fgs_render_bwd_splats(const fgs_gaussians *g, const fgs_projected *proj,
                                             const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
                                             const int32_t *ids, const int32_t *tile_ranges,
-                                            const float *t_final, const int32_t *n_contrib,
-                                            const float *dL_dcolor, const float *dL_ddepth,
-                                            const float *dL_dalpha, float *grad2d, fgs_gaussians *grads,
-                                            int32_t *d_status, void *stream) {
-  (void)d_status;
+                                            const int32_t *tile_order, const float *t_final,
+                                            const int32_t *n_contrib, const float *dL_dcolor,
+                                            const float *dL_ddepth, const float *dL_dalpha, float *grad2d,
+                                            fgs_gaussians *grads, int32_t *d_status, void *stream) {
   fgs_status s = check_bwd_args(g, proj, tiling, ids, tile_ranges, t_final, n_contrib, dL_dcolor, grad2d, grads);
   if (s != FGS_OK) return s;
   DevViews vs;
   if (!make_views(cams, n_views, tiling.tile_w, tiling.tile_h, &vs)) return FGS_ERR_INVALID_ARGUMENT;
-  return render_bwd_splats(g, proj, vs, tiling, ids, tile_ranges, t_final, n_contrib, dL_dcolor, dL_ddepth,
-                           dL_dalpha, grad2d, grads, as_stream(stream));
+  return render_bwd_splats(g, proj, vs, tiling, ids, tile_ranges, tile_order, t_final, n_contrib, dL_dcolor,
+                           dL_ddepth, dL_dalpha, grad2d, grads, d_status, as_stream(stream));
 }
 
 extern "C" fgs_status fgs_render_bwd(const fgs_gaussians *g, const fgs_projected *proj,
                                      const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
                                      const int32_t *ids, const int32_t *tile_ranges,
-                                     const float *t_final, const int32_t *n_contrib,
-                                     const float *dL_dcolor, const float *dL_ddepth,
-                                     const float *dL_dalpha, float *grad2d, fgs_gaussians *grads,
-                                     int32_t *d_status, void *stream) {
-  (void)d_status;
+                                     const int32_t *tile_order, const float *t_final,
+                                     const int32_t *n_contrib, const float *dL_dcolor,
+                                     const float *dL_ddepth, const float *dL_dalpha, float *grad2d,
+                                     fgs_gaussians *grads, int32_t *d_status, void *stream) {
   fgs_status s = check_bwd_args(g, proj, tiling, ids, tile_ranges, t_final, n_contrib, dL_dcolor, grad2d, grads);
   if (s != FGS_OK) return s;
   DevViews vs;
@@ -197,8 +208,8 @@ extern "C" fgs_status fgs_render_bwd(const fgs_gaussians *g, const fgs_projected
   cudaStream_t st = as_stream(stream);
   FGS_CUDA(cudaMemsetAsync(grad2d, 0, sizeof(float) * 8 * (size_t)n_views * (size_t)proj->stride, st),
            "memset grad2d");
-  s = render_bwd_splats(g, proj, vs, tiling, ids, tile_ranges, t_final, n_contrib, dL_dcolor, dL_ddepth, dL_dalpha,
-                        grad2d, grads, st);
+  s = render_bwd_splats(g, proj, vs, tiling, ids, tile_ranges, tile_order, t_final, n_contrib, dL_dcolor,
+                        dL_ddepth, dL_dalpha, grad2d, grads, d_status, st);
   if (s != FGS_OK) return s;
   return launch_project_bwd(g, vs, proj->radius, grad2d, proj->stride, grads, st);
 }

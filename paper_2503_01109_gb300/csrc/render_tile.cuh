@@ -16,6 +16,8 @@ struct RenderArgs {
   const int2 *ranges;
   float *color, *depth, *alpha, *t_final;
   int32_t *n_contrib;
+  const int32_t *order = nullptr;  // launch order of the tiles (NULL: CTA i takes tile i)
+  int32_t *d_status = nullptr;
 };
 
 // Pixels per thread: a thread owns PX vertically adjacent pixels of its tile
@@ -210,6 +212,8 @@ struct RenderBwdArgs {
   const float *dC, *dD, *dA;
   float *grad2d;     // [V][stride][8]
   float *grad_rgb;   // [3][cap]
+  const int32_t *order = nullptr;  // launch order of the tiles (NULL: CTA i takes tile i)
+  int32_t *d_status = nullptr;
 };
 
 // Sum of 10 per-lane values over the warp by recursive halving: at each
@@ -333,6 +337,15 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
     for (int k = min(cnt, warp_last - start) - 1; k >= 0; --k) {
       const int j = start + k;
       const float4 g0 = s_g0[k], g1 = s_g1[k];
+      float dx, dy[PX], power2[PX];
+      bool hit[PX], any_hit = false;
+#pragma unroll
+      for (int q = 0; q < PX; ++q) {
+        power2[q] = splat_power2(g0.x, g0.y, g0.z, g0.w, g1.x, fpx, (float)(py0 + q), dx, dy[q]);
+        hit[q] = j < last[q] && !(power2[q] > 0.f || power2[q] < g1.w);
+        any_hit = any_hit || hit[q];
+      }
+      if (!__ballot_sync(0xffffffffu, any_hit)) continue;  // the splat reaches no pixel of this warp
       const float4 c = s_rgb[k];
       // Sums over this thread's pixels.  The power's derivatives are linear in
       // e = dL/dalpha * G with coefficients (dx, dy, dx^2, dx dy, dy^2) and the
@@ -340,21 +353,18 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
       // flush below applies the per-splat factors once:
       //   0..4: sum e dx, e dy, e dx^2, e dx dy, e dy^2;  5: sum e (= dL/dopacity);
       //   6: sum dL/dD w;  7..9: sum dL/dC w.
+      // The body has no branch: a pixel the splat does not reach (past its last
+      // contributor, or alpha below 1/255) takes G = 0, so alpha = w = e = 0 and
+      // rom = 1, and every update below leaves its value unchanged exactly.
       float acc[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) acc[f] = 0.f;
-      bool contrib = false;
 #pragma unroll
       for (int q = 0; q < PX; ++q) {
-        if (j >= last[q]) continue;
-        float dx, dy;
-        const float power2 = splat_power2(g0.x, g0.y, g0.z, g0.w, g1.x, fpx, (float)(py0 + q), dx, dy);
-        if (power2 > 0.f || power2 < g1.w) continue;
-        const float G = ex2_approx(power2);
+        const float G = hit[q] ? ex2_approx(power2[q]) : 0.f;
         const float raw = __fmul_rn(g1.y, G);
         const float alpha = fminf(kAlphaMax, raw);
-        contrib = true;
-        const float rom = __fdividef(1.f, 1.f - alpha);
+        const float rom = hit[q] ? __fdividef(1.f, 1.f - alpha) : 1.f;
         T[q] *= rom;  // transmittance in front of this splat
         const float w = alpha * T[q];
         const float dot_gam = gc0[q] * c.x + gc1[q] * c.y + gc2[q] * c.z + gd[q] * g1.z + ga[q];
@@ -364,21 +374,17 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
         acc[7] += gc0[q] * w;
         acc[8] += gc1[q] * w;
         acc[9] += gc2[q] * w;
-        if (raw < kAlphaMax) {  // d alpha / d power = alpha (unclamped)
-          const float e = dalpha * G;
-          const float ex = e * dx, ey = e * dy;
-          acc[0] += ex;
-          acc[1] += ey;
-          acc[2] += ex * dx;
-          acc[3] += ex * dy;
-          acc[4] += ey * dy;
-          acc[5] += e;
-        }
+        const float e = raw < kAlphaMax ? dalpha * G : 0.f;  // d alpha / d power = alpha (unclamped)
+        const float ex = e * dx, ey = e * dy[q];
+        acc[0] += ex;
+        acc[1] += ey;
+        acc[2] += ex * dx;
+        acc[3] += ex * dy[q];
+        acc[4] += ey * dy[q];
+        acc[5] += e;
       }
-      if (__ballot_sync(0xffffffffu, contrib)) {
-        warp_sum10(acc, lane);
-        if (my_field >= 0) atomicAdd(&s_acc[k][my_field], acc[0]);
-      }
+      warp_sum10(acc, lane);
+      if (my_field >= 0) atomicAdd(&s_acc[k][my_field], acc[0]);
     }
     __syncthreads();
     // dL/dmean = -o (Q m), dL/d(a, b, c) = -o (m_xx / 2, m_xy, m_yy / 2) with Q the

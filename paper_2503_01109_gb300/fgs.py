@@ -111,13 +111,17 @@ _SIGS = {
                       c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "fgs_bin_sort_workspace_size": ([c_void_p, c_int32, Tiling, c_int64, c_int64], c_size_t),
     "fgs_render_fwd": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p, c_void_p,
-                        c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
-    "fgs_render_fwd_sampled": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_int32,
-                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+                        c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_render_fwd_sampled": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p,
+                                c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p],
+                               c_int32),
+    "fgs_tile_order": ([c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p], c_int32),
+    "fgs_tile_order_workspace_size": ([c_void_p, c_int32, Tiling], c_size_t),
     "fgs_render_bwd": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p, c_void_p,
-                        c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+                        c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "fgs_render_bwd_splats": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p,
-                               c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+                               c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                               c_void_p], c_int32),
     "fgs_project_bwd": ([c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p], c_int32),
     "fgs_loss": ([c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                   c_void_p, c_size_t, c_void_p], c_int32),
@@ -380,44 +384,56 @@ def fgs_bin_sort(proj: Projection, n: int, cams: list, til: Tiling, ws: torch.Te
 
 
 def fgs_render_fwd(proj: Projection, g: GaussianMap, cams: list, til: Tiling, ids, tile_ranges, frame: Frame,
-                   status=None):
+                   status=None, tile_order=None):
     ps = proj.struct()
     gs = g.struct()
     _check(lib().fgs_render_fwd(ctypes.byref(ps), ctypes.byref(gs), camera_array(cams), len(cams), til, _ptr(ids),
-                                _ptr(tile_ranges), _ptr(frame.color), _ptr(frame.depth), _ptr(frame.alpha),
-                                _ptr(frame.t_final), _ptr(frame.n_contrib), _ptr(status), _stream()),
-           "fgs_render_fwd")
+                                _ptr(tile_ranges), _ptr(tile_order), _ptr(frame.color), _ptr(frame.depth),
+                                _ptr(frame.alpha), _ptr(frame.t_final), _ptr(frame.n_contrib), _ptr(status),
+                                _stream()), "fgs_render_fwd")
 
 
 def fgs_render_fwd_sampled(proj: Projection, g: GaussianMap, cams: list, til: Tiling, ids, tile_ranges,
-                           frame: Frame, sample_stride: int = 2, status=None):
+                           frame: Frame, sample_stride: int = 2, status=None, tile_order=None):
     ps = proj.struct()
     gs = g.struct()
     _check(lib().fgs_render_fwd_sampled(ctypes.byref(ps), ctypes.byref(gs), camera_array(cams), len(cams), til,
-                                        _ptr(ids), _ptr(tile_ranges), int(sample_stride), _ptr(frame.color),
-                                        _ptr(frame.depth), _ptr(frame.alpha), _ptr(frame.t_final),
-                                        _ptr(frame.n_contrib), _ptr(status), _stream()),
+                                        _ptr(ids), _ptr(tile_ranges), _ptr(tile_order), int(sample_stride),
+                                        _ptr(frame.color), _ptr(frame.depth), _ptr(frame.alpha),
+                                        _ptr(frame.t_final), _ptr(frame.n_contrib), _ptr(status), _stream()),
            "fgs_render_fwd_sampled")
 
 
+def fgs_tile_order_workspace_size(cams: list, til: Tiling) -> int:
+    return int(lib().fgs_tile_order_workspace_size(camera_array(cams), len(cams), til))
+
+
+def fgs_tile_order(cams: list, til: Tiling, n_contrib, tile_order, ws):
+    """Heaviest-first launch order of the view set's tiles from a render's n_contrib."""
+    _check(lib().fgs_tile_order(camera_array(cams), len(cams), til, _ptr(n_contrib), _ptr(tile_order), _ptr(ws),
+                                ws.numel() * ws.element_size(), _stream()), "fgs_tile_order")
+
+
 def fgs_render_bwd(g: GaussianMap, proj: Projection, cams: list, til: Tiling, ids, tile_ranges, frame: Frame,
-                   dC, dD, dA, grad2d, grads: GaussianMap, status=None, use_device_count: bool = False):
+                   dC, dD, dA, grad2d, grads: GaussianMap, status=None, use_device_count: bool = False,
+                   tile_order=None):
     gs = g.struct(use_device_count)
     ps = proj.struct()
     gr = grads.struct(use_device_count)
     _check(lib().fgs_render_bwd(ctypes.byref(gs), ctypes.byref(ps), camera_array(cams), len(cams), til, _ptr(ids),
-                                _ptr(tile_ranges), _ptr(frame.t_final), _ptr(frame.n_contrib), _ptr(dC), _ptr(dD),
-                                _ptr(dA), _ptr(grad2d), ctypes.byref(gr), _ptr(status), _stream()),
-           "fgs_render_bwd")
+                                _ptr(tile_ranges), _ptr(tile_order), _ptr(frame.t_final), _ptr(frame.n_contrib),
+                                _ptr(dC), _ptr(dD), _ptr(dA), _ptr(grad2d), ctypes.byref(gr), _ptr(status),
+                                _stream()), "fgs_render_bwd")
 
 
 def fgs_render_bwd_splats(g: GaussianMap, proj: Projection, cams: list, til: Tiling, ids, tile_ranges, frame: Frame,
-                          dC, dD, dA, grad2d, grads: GaussianMap, status=None, use_device_count: bool = False):
+                          dC, dD, dA, grad2d, grads: GaussianMap, status=None, use_device_count: bool = False,
+                          tile_order=None):
     gs, ps, gr = g.struct(use_device_count), proj.struct(), grads.struct(use_device_count)
     _check(lib().fgs_render_bwd_splats(ctypes.byref(gs), ctypes.byref(ps), camera_array(cams), len(cams), til,
-                                       _ptr(ids), _ptr(tile_ranges), _ptr(frame.t_final), _ptr(frame.n_contrib),
-                                       _ptr(dC), _ptr(dD), _ptr(dA), _ptr(grad2d), ctypes.byref(gr), _ptr(status),
-                                       _stream()), "fgs_render_bwd_splats")
+                                       _ptr(ids), _ptr(tile_ranges), _ptr(tile_order), _ptr(frame.t_final),
+                                       _ptr(frame.n_contrib), _ptr(dC), _ptr(dD), _ptr(dA), _ptr(grad2d),
+                                       ctypes.byref(gr), _ptr(status), _stream()), "fgs_render_bwd_splats")
 
 
 def fgs_project_bwd(g: GaussianMap, proj: Projection, cams: list, grad2d, grads: GaussianMap,

@@ -89,6 +89,8 @@ class TimedMapper(Mapper):
                              self.num_pairs, self.status)
         with self.timer.span("render_fwd" if sample_stride == 1 else "render_fwd_sampled"):
             self._blend(sample_stride)
+        with self.timer.span("tile_order"):
+            self._order()
         if self.timer.on and sample_stride == 1:  # the roofline covers the full-frame renders
             snap = torch.empty_like(self.frame.n_contrib)
             fgs.fgs_memcpy_async(snap, self.frame.n_contrib)   # copy engine; summed after timing
@@ -99,7 +101,8 @@ class TimedMapper(Mapper):
         fgs.fgs_memset_async(self.grad2d)
         with self.timer.span("render_bwd"):
             fgs.fgs_render_bwd_splats(self.g, self.proj, self.cams, self.til, self.ids, self.ranges, self.frame, dC,
-                                      dD, dA, self.grad2d, self.grads, self.status, self.use_dc)
+                                      dD, dA, self.grad2d, self.grads, self.status, self.use_dc,
+                                      tile_order=self.tile_order)
         with self.timer.span("project_bwd"):
             fgs.fgs_project_bwd(self.g, self.proj, self.cams, self.grad2d, self.grads, self.use_dc)
         self._clean = False
@@ -116,7 +119,8 @@ class TimedMapper(Mapper):
             self.ensure_clean()
             with self.timer.span("render_bwd"):
                 fgs.fgs_render_bwd_splats(self.g, self.proj, self.cams, self.til, self.ids, self.ranges, self.frame,
-                                          self.dC, self.dD, None, self.grad2d, self.grads, self.status, self.use_dc)
+                                          self.dC, self.dD, None, self.grad2d, self.grads, self.status, self.use_dc,
+                                          tile_order=self.tile_order)
             with self.timer.span("project_bwd_adam"):
                 self.fused_tail_step()
             return

@@ -43,6 +43,10 @@ class Mapper:
         self.tile_keys = torch.zeros(self.pair_capacity, dtype=torch.int32, device=dev)
         self.ids = torch.zeros(self.pair_capacity, dtype=torch.int32, device=dev)
         self.ranges = torch.zeros(self.n_tiles, 2, dtype=torch.int32, device=dev)
+        # launch order of the render kernels' tiles: heaviest first by the last
+        # render's contributor counts (fgs_tile_order), any permutation being valid
+        self.tile_order = torch.arange(self.n_tiles, dtype=torch.int32, device=dev)
+        self.ws_order = fgs.ws_tensor(fgs.fgs_tile_order_workspace_size(self.cams, self.til), dev)
         self.num_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         self.ws_bin = fgs.ws_tensor(fgs.fgs_bin_sort_workspace_size(self.cams, self.til, self.V * cap,
@@ -87,13 +91,20 @@ class Mapper:
         fgs.fgs_bin_sort(self.proj, n, self.cams, self.til, self.ws_bin, self.tile_keys, self.ids, self.ranges,
                          self.num_pairs, self.status)
         self._blend(sample_stride)
+        self._order()
 
     def _blend(self, sample_stride: int):
         if sample_stride == 1:
-            fgs.fgs_render_fwd(self.proj, self.g, self.cams, self.til, self.ids, self.ranges, self.frame, self.status)
+            fgs.fgs_render_fwd(self.proj, self.g, self.cams, self.til, self.ids, self.ranges, self.frame, self.status,
+                               tile_order=self.tile_order)
         else:
             fgs.fgs_render_fwd_sampled(self.proj, self.g, self.cams, self.til, self.ids, self.ranges, self.frame,
-                                       sample_stride, self.status)
+                                       sample_stride, self.status, tile_order=self.tile_order)
+
+    def _order(self):
+        """The tiles heaviest first by this render's contributor counts: the order of
+        the adjoint that follows and of the next render."""
+        fgs.fgs_tile_order(self.cams, self.til, self.frame.n_contrib, self.tile_order, self.ws_order)
 
     def can_sample(self, stride: int) -> bool:
         """Whether render(sample_stride=stride) is available for this tiling."""
@@ -103,7 +114,7 @@ class Mapper:
         """a7-a8 into self.grads (cleared first)."""
         fgs.fgs_memset_async(self.grads.buf)
         fgs.fgs_render_bwd(self.g, self.proj, self.cams, self.til, self.ids, self.ranges, self.frame, dC, dD, dA,
-                           self.grad2d, self.grads, self.status, self.use_dc)
+                           self.grad2d, self.grads, self.status, self.use_dc, tile_order=self.tile_order)
         self._clean = False
 
     def ensure_clean(self):
@@ -131,7 +142,8 @@ class Mapper:
         if self.fused_tail:
             self.ensure_clean()
             fgs.fgs_render_bwd_splats(self.g, self.proj, self.cams, self.til, self.ids, self.ranges, self.frame,
-                                      self.dC, self.dD, None, self.grad2d, self.grads, self.status, self.use_dc)
+                                      self.dC, self.dD, None, self.grad2d, self.grads, self.status, self.use_dc,
+                                      tile_order=self.tile_order)
             self.fused_tail_step()
             return
         self.backward(self.dC, self.dD)

@@ -173,3 +173,25 @@ def test_autotune_argument_checks(lib):
     rc = L.fgs_autotune(ctypes.byref(g), cams, 2, dummy, dummy, ctypes.byref(lp), 1 << 16, 0, dummy, need,
                         ctypes.byref(best), None, None)
     assert rc == 1 and b"reps" in L.fgs_last_error()
+
+
+def test_tile_order_argument_checks(lib):
+    """fgs_tile_order refuses bad tilings, NULLs and small workspaces before any CUDA
+    call; its workspace holds one int32 per tile of the view set."""
+    from paper_2503_01109_gb300 import fgs, synthetic as syn
+    L = fgs.lib()
+    L.fgs_tile_order_workspace_size.restype = ctypes.c_size_t
+    cams = fgs.camera_array([syn.pinhole(64, 48, 60.0), syn.pinhole(40, 30, 40.0)])
+    til = fgs.tiling(16, 16, 128)
+    tiles = L.fgs_num_tiles(cams, 2, til)
+    need = L.fgs_tile_order_workspace_size(cams, 2, til)
+    assert tiles == 12 + 6 and need >= 4 * tiles and need % 256 == 0
+    assert L.fgs_tile_order_workspace_size(cams, 2, fgs.tiling(12, 12, 128)) == 0
+    assert L.fgs_tile_order_workspace_size(cams, 0, til) == 0
+    dummy = ctypes.c_void_p(256)  # never dereferenced: every case fails its checks first
+    rc = L.fgs_tile_order(cams, 2, fgs.tiling(12, 12, 128), dummy, dummy, dummy, need, None)
+    assert rc == 1 and b"tiling" in L.fgs_last_error()
+    rc = L.fgs_tile_order(cams, 2, til, None, dummy, dummy, need, None)
+    assert rc == 1 and b"NULL" in L.fgs_last_error()
+    rc = L.fgs_tile_order(cams, 2, til, dummy, dummy, dummy, 4 * tiles - 1, None)
+    assert rc == 1 and b"workspace" in L.fgs_last_error()
