@@ -579,13 +579,17 @@ size_t fgs_fourier_seed_workspace_size(int32_t width, int32_t height, int32_t ma
  *   grad2d [n_views][stride][8] and grads->rgb (the caller zeroes both); chain them
  *   to the Gaussians with fgs_project_bwd.
  *   ws: fgs_render_window_workspace_size(cams, n_views) bytes, 256-byte aligned.
+ *   tile_order: NULL or a permutation of the view set's tiles (fgs_tile_order of
+ *   an earlier window's n_contrib): the blend and adjoint phases claim their
+ *   (view, tile) items in that order, heaviest first; as for fgs_render_fwd, an
+ *   entry outside the tiles is skipped and or-es FGS_DEV_BAD_ORDER into *d_status.
  *   Device errors: every barrier wait is bounded (2 s); a CTA that gives up sets
  *   FGS_DEV_TIMEOUT and returns, and the outputs are then invalid.
  *   err: UNSUPPORTED when the kernel cannot be made co-resident. */
 fgs_status fgs_render_window(const fgs_gaussians *g, const fgs_projected *proj,
                              const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
                              const int32_t *ids, const int32_t *tile_ranges,
-                             const float *color_gt, const float *depth_gt,
+                             const int32_t *tile_order, const float *color_gt, const float *depth_gt,
                              const fgs_loss_params *lp, float *color, float *depth, float *alpha,
                              float *t_final, int32_t *n_contrib, float *dL_dcolor,
                              float *dL_ddepth, float *grad2d, fgs_gaussians *grads, float *d_loss,
@@ -597,7 +601,8 @@ size_t fgs_render_window_workspace_size(const fgs_camera *cams, int32_t n_views)
  * are measured rather than fixed): every supported tiling -- 8x8, 16x16 and 16x32
  * tiles (w x h) times batch depths 32, 64, 128, 256, FGS_AUTOTUNE_CONFIGS in the
  * order 8x8/32, 8x8/64, ..., 16x32/256 -- runs fgs_project, fgs_bin_sort,
- * fgs_render_window and fgs_project_bwd on the caller's map g, views cams and
+ * fgs_render_window (in the heaviest-first tile order of the previous pass),
+ * fgs_tile_order and fgs_project_bwd on the caller's map g, views cams and
  * targets (color_gt, depth_gt as for fgs_render_window, weights `loss`), once
  * untimed and `reps` times timed with CUDA events; the fastest is written to
  * *best and, when ms_out (host, FGS_AUTOTUNE_CONFIGS floats) is not NULL, the

@@ -20,9 +20,9 @@ static const fgs_tiling kTunings[FGS_AUTOTUNE_CONFIGS] = {
 
 // Byte offsets of the scratch buffers inside the caller's workspace.
 struct TuneLayout {
-  size_t splat, radius, rect, keys, ids, ranges, counters, bin, win, color, depth, alpha, t_final, n_contrib, dC,
-      dD, grad2d, grads, total;
-  size_t bin_bytes, win_bytes;
+  size_t splat, radius, rect, keys, ids, ranges, order, order_ws, counters, bin, win, color, depth, alpha, t_final,
+      n_contrib, dC, dD, grad2d, grads, total;
+  size_t bin_bytes, win_bytes, order_bytes;
   int64_t max_tiles, pix;
 };
 
@@ -58,6 +58,9 @@ static bool tune_layout(const fgs_gaussians *g, const fgs_camera *cams, int32_t 
   L->keys = take(sizeof(uint32_t) * pair_capacity);
   L->ids = take(sizeof(int32_t) * pair_capacity);
   L->ranges = take(sizeof(int32_t) * 2 * L->max_tiles);
+  L->order = take(sizeof(int32_t) * L->max_tiles);
+  L->order_bytes = align_up(sizeof(int32_t) * L->max_tiles);
+  L->order_ws = take(L->order_bytes);
   L->counters = take(64);  // num_pairs (int64), status (int32), loss (float)
   L->bin = take(L->bin_bytes);
   L->win = take(L->win_bytes);
@@ -74,10 +77,13 @@ static bool tune_layout(const fgs_gaussians *g, const fgs_camera *cams, int32_t 
   return true;
 }
 
-// One window pass of tiling t: everything whose cost depends on the tiling.
+// One window pass of tiling t: everything whose cost depends on the tiling.  The
+// window takes its tiles in the heaviest-first order of the previous pass's
+// render (none on the first pass), and the pass ends by ordering them for the
+// next, as a mapping loop over the window does.
 static fgs_status tune_pass(const fgs_gaussians *g, const fgs_camera *cams, int32_t n_views, const float *color_gt,
                             const float *depth_gt, const fgs_loss_params *lp, int64_t pair_capacity, char *ws,
-                            const TuneLayout &L, fgs_tiling t, cudaStream_t st) {
+                            const TuneLayout &L, fgs_tiling t, bool ordered, cudaStream_t st) {
   const int64_t cap = g->capacity;
   fgs_projected proj{cap, reinterpret_cast<float *>(ws + L.splat), reinterpret_cast<int32_t *>(ws + L.radius),
                      reinterpret_cast<uint16_t *>(ws + L.rect)};
@@ -95,13 +101,17 @@ static fgs_status tune_pass(const fgs_gaussians *g, const fgs_camera *cams, int3
   FGS_CUDA(cudaMemsetAsync(ws + L.grad2d, 0, sizeof(float) * 8 * n_views * cap, st), "fgs_autotune: memset");
   FGS_CUDA(cudaMemsetAsync(ws + L.grads, 0, sizeof(float) * 14 * cap, st), "fgs_autotune: memset");
   FGS_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), st), "fgs_autotune: memset");
+  int32_t *order = reinterpret_cast<int32_t *>(ws + L.order);
   s = fgs_render_window(g, &proj, cams, n_views, t, reinterpret_cast<int32_t *>(ws + L.ids),
-                        reinterpret_cast<int32_t *>(ws + L.ranges), color_gt, depth_gt, lp,
+                        reinterpret_cast<int32_t *>(ws + L.ranges), ordered ? order : nullptr, color_gt, depth_gt, lp,
                         reinterpret_cast<float *>(ws + L.color), reinterpret_cast<float *>(ws + L.depth),
                         reinterpret_cast<float *>(ws + L.alpha), reinterpret_cast<float *>(ws + L.t_final),
                         reinterpret_cast<int32_t *>(ws + L.n_contrib), reinterpret_cast<float *>(ws + L.dC),
                         reinterpret_cast<float *>(ws + L.dD), reinterpret_cast<float *>(ws + L.grad2d), &grads, loss,
                         ws + L.win, L.win_bytes, status, st);
+  if (s != FGS_OK) return s;
+  s = fgs_tile_order(cams, n_views, t, reinterpret_cast<int32_t *>(ws + L.n_contrib), order, ws + L.order_ws,
+                     L.order_bytes, st);
   if (s != FGS_OK) return s;
   return fgs_project_bwd(g, &proj, cams, n_views, reinterpret_cast<float *>(ws + L.grad2d), &grads, st);
 }
@@ -148,11 +158,11 @@ extern "C" fgs_status fgs_autotune(const fgs_gaussians *g, const fgs_camera *cam
       break;
     }
     // one untimed pass (first use of the tiling's kernels), then `reps` timed ones
-    result = tune_pass(g, cams, n_views, color_gt, depth_gt, loss, pair_capacity, w, L, t, st);
+    result = tune_pass(g, cams, n_views, color_gt, depth_gt, loss, pair_capacity, w, L, t, false, st);
     if (result != FGS_OK) break;
     if (cudaEventRecord(e0, st) != cudaSuccess) result = FGS_ERR_CUDA;
     for (int r = 0; r < reps && result == FGS_OK; ++r)
-      result = tune_pass(g, cams, n_views, color_gt, depth_gt, loss, pair_capacity, w, L, t, st);
+      result = tune_pass(g, cams, n_views, color_gt, depth_gt, loss, pair_capacity, w, L, t, true, st);
     if (result != FGS_OK) break;
     int32_t status = 0;
     if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||

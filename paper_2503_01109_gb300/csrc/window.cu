@@ -92,14 +92,26 @@ __device__ __forceinline__ int claim(uint32_t *counter, int *s_item) {
 // (38 KB) stays below the render phases' and does not lower the grid's residency.
 constexpr int kWinLT = 16;
 
+// Tile of render work item i: i itself, or its entry of the launch order
+// (fgs_tile_order: heaviest first); an entry outside the tiles is reported and
+// skipped.
+__device__ __forceinline__ int window_tile(const WindowArgs &w, int i) {
+  if (!w.f.order) return i;
+  const int t = w.f.order[i];
+  if ((unsigned)t < (unsigned)w.n_tiles) return t;
+  if (threadIdx.x == 0) atomicOr(w.status, FGS_DEV_BAD_ORDER);
+  return -1;
+}
+
 template <int TW, int TH, int BATCH>
 __global__ void __launch_bounds__(TW *TH / 2) k_window(WindowArgs w) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int s_item, s_flag;
   for (;;) {
-    const int t = claim(w.ctl + 0, &s_item);
-    if (t >= w.n_tiles) break;
-    render_fwd_tile<TW, TH, BATCH, 2>(w.f, t, smem);
+    const int i = claim(w.ctl + 0, &s_item);
+    if (i >= w.n_tiles) break;
+    const int t = window_tile(w, i);
+    if (t >= 0) render_fwd_tile<TW, TH, BATCH, 2>(w.f, t, smem);
   }
   if (!grid_barrier(w, &s_flag)) return;
   for (;;) {
@@ -109,9 +121,10 @@ __global__ void __launch_bounds__(TW *TH / 2) k_window(WindowArgs w) {
   }
   if (!grid_barrier(w, &s_flag)) return;
   for (;;) {
-    const int t = claim(w.ctl + 2, &s_item);
-    if (t >= w.n_tiles) break;
-    render_bwd_tile<TW, TH, BATCH, 2>(w.b, t, smem);
+    const int i = claim(w.ctl + 2, &s_item);
+    if (i >= w.n_tiles) break;
+    const int t = window_tile(w, i);
+    if (t >= 0) render_bwd_tile<TW, TH, BATCH, 2>(w.b, t, smem);
   }
 }
 
@@ -220,7 +233,8 @@ extern "C" size_t fgs_render_window_workspace_size(const fgs_camera *cams, int32
 
 extern "C" fgs_status fgs_render_window(const fgs_gaussians *g, const fgs_projected *proj,
                                         const fgs_camera *cams, int32_t n_views, fgs_tiling tiling,
-                                        const int32_t *ids, const int32_t *tile_ranges, const float *color_gt,
+                                        const int32_t *ids, const int32_t *tile_ranges,
+                                        const int32_t *tile_order, const float *color_gt,
                                         const float *depth_gt, const fgs_loss_params *lp, float *color,
                                         float *depth, float *alpha, float *t_final, int32_t *n_contrib,
                                         float *dL_dcolor, float *dL_ddepth, float *grad2d, fgs_gaussians *grads,
@@ -240,7 +254,8 @@ extern "C" fgs_status fgs_render_window(const fgs_gaussians *g, const fgs_projec
   FGS_CHECK_ARG(ws && ws_bytes >= need, "fgs_render_window: workspace %zu < %zu bytes", ws_bytes, need);
   WindowArgs w;
   w.f = RenderArgs{vs, reinterpret_cast<const float4 *>(proj->splat), proj->stride, g->rgb, g->capacity, ids,
-                   reinterpret_cast<const int2 *>(tile_ranges), color, depth, alpha, t_final, n_contrib};
+                   reinterpret_cast<const int2 *>(tile_ranges), color, depth, alpha, t_final, n_contrib,
+                   tile_order, d_status};
   w.b = RenderBwdArgs{vs,        reinterpret_cast<const float4 *>(proj->splat), proj->stride, g->rgb, g->capacity,
                       ids,       reinterpret_cast<const int2 *>(tile_ranges), t_final, n_contrib, dL_dcolor,
                       dL_ddepth, nullptr, grad2d, grads->rgb};

@@ -173,7 +173,7 @@ _OPTIONAL = {
     "fgs_prior_num_params": ([], c_int64),
     "fgs_render_window": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p, c_void_p,
                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
-                           c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
+                           c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], c_int32),
     "fgs_render_window_workspace_size": ([c_void_p, c_int32], c_size_t),
     "fgs_loss_noalloc": ([c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                           c_void_p, c_void_p], c_int32),
@@ -723,11 +723,11 @@ def fgs_render_window_workspace_size(cams: list) -> int:
 
 def fgs_render_window(g: GaussianMap, proj: Projection, cams: list, til: Tiling, ids, tile_ranges, color_gt, depth_gt,
                       w_c, w_d, w_s, frame: Frame, dC, dD, grad2d, grads: GaussianMap, loss_acc, ws, status,
-                      use_device_count: bool = True):
+                      use_device_count: bool = True, tile_order=None):
     gs, ps, gr = g.struct(use_device_count), proj.struct(), grads.struct(use_device_count)
     lp = LossParams(float(w_c), float(w_d), float(w_s))
     _check(lib().fgs_render_window(ctypes.byref(gs), ctypes.byref(ps), camera_array(cams), len(cams), til, _ptr(ids),
-                                   _ptr(tile_ranges), _ptr(color_gt), _ptr(depth_gt), ctypes.byref(lp),
+                                   _ptr(tile_ranges), _ptr(tile_order), _ptr(color_gt), _ptr(depth_gt), ctypes.byref(lp),
                                    _ptr(frame.color), _ptr(frame.depth), _ptr(frame.alpha), _ptr(frame.t_final),
                                    _ptr(frame.n_contrib), _ptr(dC), _ptr(dD), _ptr(grad2d), ctypes.byref(gr),
                                    _ptr(loss_acc), _ptr(ws), ws.numel() * ws.element_size(), _ptr(status),

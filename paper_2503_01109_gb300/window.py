@@ -34,7 +34,8 @@ class Window(Mapper):
         fgs.fgs_memset_async(self.loss_acc)
         fgs.fgs_render_window(self.g, self.proj, self.cams, self.til, self.ids, self.ranges, self.color_gt,
                               self.depth_gt, *self.loss_w, self.frame, self.dC, self.dD, self.grad2d, self.grads,
-                              self.loss_acc, self.ws_win, self.status, self.use_dc)
+                              self.loss_acc, self.ws_win, self.status, self.use_dc, tile_order=self.tile_order)
+        self._order()   # heaviest first for the next window iteration
         if self.fused_tail:
             self.fused_tail_step()
             return

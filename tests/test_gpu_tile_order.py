@@ -136,3 +136,23 @@ def test_an_order_entry_outside_the_tiles_is_reported(cuda_device):
     m.status.zero_()
     _splat_grads(m, bad)
     assert int(m.status.item()) & FGS_DEV_BAD_ORDER
+
+
+def test_window_reports_an_order_entry_outside_the_tiles(cuda_device):
+    from paper_2503_01109_gb300.window import Window
+    cams = [syn.pinhole(70, 45, 60.0), syn.pinhole(33, 20, 30.0)]
+    til = fgs.tiling(16, 16, 128)
+    win = Window(fgs.GaussianMap.from_scene(syn.tiny_scene(1500, seed=7)), cams, til, reg_w=0.0)
+    fr = [syn.textured_frame(c["width"], c["height"], 3 + i) for i, c in enumerate(cams)]
+    cg, dg = fgs.pack_images(cams, [f["rgb"] for f in fr], [f["depth"] for f in fr])
+    fgs.fgs_project(win.g, cams, til, win.proj, win.status, True)
+    fgs.fgs_bin_sort(win.proj, win.g.capacity, cams, til, win.ws_bin, win.tile_keys, win.ids, win.ranges,
+                     win.num_pairs, win.status)
+    bad = torch.arange(win.n_tiles, dtype=torch.int32, device="cuda")
+    bad[1] = 1 << 20
+    for t in (win.grads.buf, win.grad2d, win.loss_acc):
+        fgs.fgs_memset_async(t)
+    fgs.fgs_render_window(win.g, win.proj, cams, til, win.ids, win.ranges, cg, dg, 0.9, 0.1, 0.1, win.frame, win.dC,
+                          win.dD, win.grad2d, win.grads, win.loss_acc, win.ws_win, win.status, tile_order=bad)
+    torch.cuda.synchronize()
+    assert int(win.status.item()) == FGS_DEV_BAD_ORDER

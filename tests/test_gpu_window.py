@@ -26,8 +26,12 @@ def targets(cams, seed):
     return fgs.pack_images(cams, [f["rgb"] for f in fr], [f["depth"] for f in fr])
 
 
+@pytest.mark.parametrize("ordered", [False, True])
 @pytest.mark.parametrize("tile,batch", [((16, 16), 128), ((8, 8), 32), ((16, 32), 256), ((16, 16), 64)])
-def test_window_equals_separate_calls(cuda_device, tile, batch):
+def test_window_equals_separate_calls(cuda_device, tile, batch, ordered):
+    """ordered: the window claims its tiles in the heaviest-first order of the
+    separate render (fgs_tile_order), which changes no value beyond the order of
+    the adjoint's float atomics."""
     cams = views()
     sc = syn.tiny_scene(2500, seed=7)
     cg, dg = targets(cams, 3)
@@ -48,10 +52,13 @@ def test_window_equals_separate_calls(cuda_device, tile, batch):
                      win.num_pairs, win.status)
     for t in (win.grads.buf, win.grad2d, win.loss_acc):
         fgs.fgs_memset_async(t)
+    order = ref.tile_order if ordered else None
     fgs.fgs_render_window(win.g, win.proj, cams, til, win.ids, win.ranges, cg, dg, 0.9, 0.1, 0.1, win.frame, win.dC,
-                          win.dD, win.grad2d, win.grads, win.loss_acc, win.ws_win, win.status)
+                          win.dD, win.grad2d, win.grads, win.loss_acc, win.ws_win, win.status, tile_order=order)
     fgs.fgs_project_bwd(win.g, win.proj, cams, win.grad2d, win.grads, True)
     torch.cuda.synchronize()
+    if ordered:
+        assert not torch.equal(order.cpu(), torch.arange(ref.n_tiles, dtype=torch.int32))
     assert int(win.status.item()) == 0 and int(ref.status.item()) == 0
     for k in ("color", "depth", "alpha", "t_final"):
         assert torch.equal(getattr(win.frame, k), getattr(ref.frame, k)), k
