@@ -3,7 +3,8 @@ at 640x480 (f = 525) and 4 at 1200x680 (f = 600) of the benchmark trajectory ove
 the 1M-Gaussian room map, 16x32 tiles with batch depth 256.  A property that holds
 at any size: the one persistent launch equals the separate forward, loss and
 adjoint calls -- images, contributor counts and image gradients bit-identical,
-the loss to 1e-6, the atomically summed gradients within 1e-4 relative."""
+the loss to 1e-6, every entry of the atomically summed gradients within the 1e-3
+gradient contract."""
 import pytest
 import torch
 
@@ -58,5 +59,7 @@ def test_full_size_window_equals_separate_calls(cuda_device):
         assert torch.equal(getattr(win.frame, k), v), k
     assert torch.equal(win.dC, ref_dC) and torch.equal(win.dD, ref_dD)
     assert float(win.loss_acc.item()) == pytest.approx(ref_loss, rel=1e-6)
-    bad, _ = grad_close(win.grads.buf.cpu().numpy(), ref_grads, rel=1e-4)
-    assert bad.mean() < 1e-4, int(bad.sum())
+    # the two sum the same terms with float atomics in different orders: every
+    # entry within the gradient contract
+    bad, r = grad_close(win.grads.buf.cpu().numpy(), ref_grads, rel=1e-3)
+    assert not bad.any(), (int(bad.sum()), float(r.max()))
