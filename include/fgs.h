@@ -565,6 +565,29 @@ fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_gt, const fl
                             void *stream);
 size_t fgs_fourier_seed_workspace_size(int32_t width, int32_t height, int32_t max_new);
 
+/* fgs_fourier_seed in two calls, for a caller that overlaps the first with other
+ * work on a second stream: the first needs only the frame, the second the render.
+ * fgs_fourier_energy -- eq2-eq8 and the threshold: E (into energy, or into ws when
+ *   energy is NULL), its histogram and the triangle threshold *d_threshold.
+ * fgs_fourier_seed_from_energy -- the rest of fgs_fourier_seed (eq9-eq11, the
+ *   prior), with the same arguments, reading E, the threshold and the maxima that
+ *   fgs_fourier_energy left in `energy` (or ws), *d_threshold and ws.
+ * The pair gives fgs_fourier_seed's outputs bit for bit when both calls get the
+ * same cam size, params, energy, d_threshold and ws, and the second runs after the
+ * first has completed (same stream, or an event between the streams); nothing
+ * checks that, and in between neither ws nor energy may be used by another call.
+ * Errors as fgs_fourier_seed. */
+fgs_status fgs_fourier_energy(const float *rgb_gt, const fgs_camera *cam, const fgs_seed_params *params,
+                              float *energy, int32_t *d_threshold, void *ws, size_t ws_bytes,
+                              void *stream);
+fgs_status fgs_fourier_seed_from_energy(const float *rgb_gt, const float *depth_gt,
+                                        const float *r_color, const float *r_depth,
+                                        const float *r_alpha, const fgs_camera *cam,
+                                        const fgs_seed_params *params, const fgs_mlp *prior,
+                                        uint8_t *mask, const float *energy, fgs_gaussians *g,
+                                        int32_t *d_num_new, int32_t *d_threshold, int32_t *seed_xy,
+                                        void *ws, size_t ws_bytes, int32_t *d_status, void *stream);
+
 /* ---------------------------------------------------------------------------------
  * fgs_render_window -- a keyframe window (the co-visible and random keyframes the
  * map is optimised over, Sec. III-C/D) rendered (eq1), scored (eq16 without eq15)

@@ -634,31 +634,36 @@ extern "C" size_t fgs_fourier_seed_workspace_size(int32_t width, int32_t height,
   return carve_seed(nullptr, width, height, max_new).bytes;
 }
 
-extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_gt, const float *r_color,
-                                       const float *r_depth, const float *r_alpha, const fgs_camera *cam,
-                                       const fgs_seed_params *prm, const fgs_mlp *prior, uint8_t *mask,
-                                       float *energy, fgs_gaussians *g, int32_t *d_num_new, int32_t *d_threshold,
-                                       int32_t *seed_xy, void *ws, size_t ws_bytes, int32_t *d_status,
-                                       void *stream) {
-  FGS_CHECK_ARG(rgb_gt && depth_gt && cam && prm && mask && d_num_new && d_threshold,
-                "fgs_fourier_seed: NULL argument");
-  FGS_CHECK_ARG(!r_alpha || (r_color && r_depth), "fgs_fourier_seed: r_alpha needs r_color and r_depth");
-  if (!gaussians_ok(g, "g")) return FGS_ERR_INVALID_ARGUMENT;
+namespace fgs {
+
+// The two halves of fgs_fourier_seed.  Both check the frame size and the
+// parameters the same way and carve the same workspace, so the energy map, the
+// threshold and the running maximum that the first leaves in the workspace are
+// where the second looks for them.
+static fgs_status seed_setup(const char *what, const fgs_camera *cam, const fgs_seed_params *prm, void *ws,
+                             size_t ws_bytes, FftPlan *px, FftPlan *py, SeedWs *w) {
+  FGS_CHECK_ARG(cam && prm, "%s: NULL argument", what);
   const int W = cam->width, H = cam->height;
-  FGS_CHECK_ARG(W > 0 && H > 0 && W <= 8192 && H <= 8192, "fgs_fourier_seed: image size");
+  FGS_CHECK_ARG(W > 0 && H > 0 && W <= 8192 && H <= 8192, "%s: image size", what);
   FGS_CHECK_ARG(prm->m >= 1 && prm->n >= 1 && prm->max_new >= 0 && prm->max_new <= kMaxNewLimit && prm->d0 > 0,
-                "fgs_fourier_seed: bad parameters");
-  FGS_CHECK_ARG(ws && (reinterpret_cast<uintptr_t>(ws) & 255) == 0, "fgs_fourier_seed: workspace alignment");
-  FftPlan px, py;
-  if (!make_plan(W, &px) || !make_plan(H, &py)) {
-    set_error("fgs_fourier_seed: %dx%d has a prime factor above 17", W, H);
+                "%s: bad parameters", what);
+  FGS_CHECK_ARG(ws && (reinterpret_cast<uintptr_t>(ws) & 255) == 0, "%s: workspace alignment", what);
+  if (!make_plan(W, px) || !make_plan(H, py)) {
+    set_error("%s: %dx%d has a prime factor above 17", what, W, H);
     return FGS_ERR_UNSUPPORTED;
   }
-  SeedWs w = carve_seed(ws, W, H, prm->max_new);
-  FGS_CHECK_ARG(ws_bytes >= w.bytes, "fgs_fourier_seed: workspace %zu < %zu bytes", ws_bytes, w.bytes);
-  cudaStream_t st = as_stream(stream);
+  *w = carve_seed(ws, W, H, prm->max_new);
+  FGS_CHECK_ARG(ws_bytes >= w->bytes, "%s: workspace %zu < %zu bytes", what, ws_bytes, w->bytes);
+  return FGS_OK;
+}
+
+// eq2-eq8 and the threshold: the frame's high-frequency energy E, its histogram
+// over E / max E and the triangle threshold.
+static fgs_status launch_energy(const float *rgb_gt, const fgs_camera *cam, const fgs_seed_params *prm,
+                                const FftPlan &px, const FftPlan &py, const SeedWs &w, float *E,
+                                int32_t *d_threshold, cudaStream_t st) {
+  const int W = cam->width, H = cam->height;
   const int64_t HW = (int64_t)W * H;
-  float *E = energy ? energy : w.energy;
   FGS_CUDA(cudaMemsetAsync(w.hist, 0, 258 * 4, st), "memset hist");
   const size_t smem_row = 3 * (size_t)W * sizeof(float2);  // two buffers + twiddles
   int cg = kColGroup;
@@ -676,7 +681,18 @@ extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_g
   pdl_launch(k_hist, 4 * num_sms(), 256, 0, st, E, HW, w.max_bits, w.hist);
   pdl_launch(k_triangle, 1, 256, 0, st, w.hist, d_threshold);
   count_launch(5);
-  FGS_CHECK_LAUNCH("fgs_fourier_seed fft");
+  FGS_CHECK_LAUNCH("fgs_fourier_energy");
+  return FGS_OK;
+}
+
+// eq9-eq11 (and the learned prior) from E and the threshold.
+static fgs_status launch_seeds(const float *rgb_gt, const float *depth_gt, const float *r_color,
+                               const float *r_depth, const float *r_alpha, const fgs_camera *cam,
+                               const fgs_seed_params *prm, const fgs_mlp *prior, uint8_t *mask, const float *E,
+                               fgs_gaussians *g, int32_t *d_num_new, int32_t *d_threshold, int32_t *seed_xy,
+                               const SeedWs &w, int32_t *d_status, cudaStream_t st) {
+  const int W = cam->width, H = cam->height;
+  const int64_t HW = (int64_t)W * H;
   SeedArgs a;
   a.rgb = rgb_gt;
   a.depth_gt = depth_gt;
@@ -723,4 +739,65 @@ extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_g
                                 w.prior_bytes, gauss_grads(g), d_status, st);
   }
   return FGS_OK;
+}
+
+static fgs_status seed_args_ok(const char *what, const float *rgb_gt, const float *depth_gt, const float *r_color,
+                               const float *r_depth, const float *r_alpha, uint8_t *mask, const fgs_gaussians *g,
+                               int32_t *d_num_new, int32_t *d_threshold) {
+  FGS_CHECK_ARG(rgb_gt && depth_gt && mask && d_num_new && d_threshold, "%s: NULL argument", what);
+  FGS_CHECK_ARG(!r_alpha || (r_color && r_depth), "%s: r_alpha needs r_color and r_depth", what);
+  if (!gaussians_ok(g, "g")) return FGS_ERR_INVALID_ARGUMENT;
+  return FGS_OK;
+}
+
+}  // namespace fgs
+
+using namespace fgs;
+
+extern "C" fgs_status fgs_fourier_seed(const float *rgb_gt, const float *depth_gt, const float *r_color,
+                                       const float *r_depth, const float *r_alpha, const fgs_camera *cam,
+                                       const fgs_seed_params *prm, const fgs_mlp *prior, uint8_t *mask,
+                                       float *energy, fgs_gaussians *g, int32_t *d_num_new, int32_t *d_threshold,
+                                       int32_t *seed_xy, void *ws, size_t ws_bytes, int32_t *d_status,
+                                       void *stream) {
+  const char *what = "fgs_fourier_seed";
+  fgs_status s = seed_args_ok(what, rgb_gt, depth_gt, r_color, r_depth, r_alpha, mask, g, d_num_new, d_threshold);
+  if (s != FGS_OK) return s;
+  FftPlan px, py;
+  SeedWs w;
+  if ((s = seed_setup(what, cam, prm, ws, ws_bytes, &px, &py, &w)) != FGS_OK) return s;
+  cudaStream_t st = as_stream(stream);
+  float *E = energy ? energy : w.energy;
+  if ((s = launch_energy(rgb_gt, cam, prm, px, py, w, E, d_threshold, st)) != FGS_OK) return s;
+  return launch_seeds(rgb_gt, depth_gt, r_color, r_depth, r_alpha, cam, prm, prior, mask, E, g, d_num_new,
+                      d_threshold, seed_xy, w, d_status, st);
+}
+
+extern "C" fgs_status fgs_fourier_energy(const float *rgb_gt, const fgs_camera *cam, const fgs_seed_params *prm,
+                                         float *energy, int32_t *d_threshold, void *ws, size_t ws_bytes,
+                                         void *stream) {
+  const char *what = "fgs_fourier_energy";
+  FGS_CHECK_ARG(rgb_gt && d_threshold, "%s: NULL argument", what);
+  FftPlan px, py;
+  SeedWs w;
+  fgs_status s = seed_setup(what, cam, prm, ws, ws_bytes, &px, &py, &w);
+  if (s != FGS_OK) return s;
+  return launch_energy(rgb_gt, cam, prm, px, py, w, energy ? energy : w.energy, d_threshold, as_stream(stream));
+}
+
+extern "C" fgs_status fgs_fourier_seed_from_energy(const float *rgb_gt, const float *depth_gt, const float *r_color,
+                                                   const float *r_depth, const float *r_alpha,
+                                                   const fgs_camera *cam, const fgs_seed_params *prm,
+                                                   const fgs_mlp *prior, uint8_t *mask, const float *energy,
+                                                   fgs_gaussians *g, int32_t *d_num_new, int32_t *d_threshold,
+                                                   int32_t *seed_xy, void *ws, size_t ws_bytes, int32_t *d_status,
+                                                   void *stream) {
+  const char *what = "fgs_fourier_seed_from_energy";
+  fgs_status s = seed_args_ok(what, rgb_gt, depth_gt, r_color, r_depth, r_alpha, mask, g, d_num_new, d_threshold);
+  if (s != FGS_OK) return s;
+  FftPlan px, py;
+  SeedWs w;
+  if ((s = seed_setup(what, cam, prm, ws, ws_bytes, &px, &py, &w)) != FGS_OK) return s;
+  return launch_seeds(rgb_gt, depth_gt, r_color, r_depth, r_alpha, cam, prm, prior, mask, energy ? energy : w.energy,
+                      g, d_num_new, d_threshold, seed_xy, w, d_status, as_stream(stream));
 }

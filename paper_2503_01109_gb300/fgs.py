@@ -165,6 +165,10 @@ _OPTIONAL = {
                           c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p],
                          c_int32),
     "fgs_fourier_seed_workspace_size": ([c_int32, c_int32, c_int32], c_size_t),
+    "fgs_fourier_energy": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p], c_int32),
+    "fgs_fourier_seed_from_energy": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
+                                      c_void_p, c_void_p], c_int32),
     "fgs_prior_features": ([c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p], c_int32),
     "fgs_prior_infer": ([c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p], c_int32),
     "fgs_prior_train": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_size_t,
@@ -680,14 +684,24 @@ def fgs_fourier_seed_workspace_size(width: int, height: int, max_new: int) -> in
 
 def fgs_fourier_seed(rgb_gt, depth_gt, r_color, r_depth, r_alpha, cam: dict, params: SeedParams, prior, mask,
                      energy, g: GaussianMap, num_new, threshold, ws, status=None, use_device_count: bool = True,
-                     seed_xy=None):
+                     seed_xy=None, from_energy: bool = False):
+    """fgs_fourier_seed, or with from_energy its second half
+    (fgs_fourier_seed_from_energy) after an fgs_fourier_energy call on `ws`."""
     gs = g.struct(use_device_count)
     cs = camera_struct(cam)
-    _check(lib().fgs_fourier_seed(_ptr(rgb_gt), _ptr(depth_gt), _ptr(r_color), _ptr(r_depth), _ptr(r_alpha),
-                                  ctypes.byref(cs), ctypes.byref(params),
-                                  None if prior is None else ctypes.byref(prior), _ptr(mask), _ptr(energy),
-                                  ctypes.byref(gs), _ptr(num_new), _ptr(threshold), _ptr(seed_xy), _ptr(ws),
-                                  ws.numel() * ws.element_size(), _ptr(status), _stream()), "fgs_fourier_seed")
+    name = "fgs_fourier_seed_from_energy" if from_energy else "fgs_fourier_seed"
+    _check(getattr(lib(), name)(_ptr(rgb_gt), _ptr(depth_gt), _ptr(r_color), _ptr(r_depth), _ptr(r_alpha),
+                                ctypes.byref(cs), ctypes.byref(params),
+                                None if prior is None else ctypes.byref(prior), _ptr(mask), _ptr(energy),
+                                ctypes.byref(gs), _ptr(num_new), _ptr(threshold), _ptr(seed_xy), _ptr(ws),
+                                ws.numel() * ws.element_size(), _ptr(status), _stream()), name)
+
+
+def fgs_fourier_energy(rgb_gt, cam: dict, params: SeedParams, energy, threshold, ws):
+    cs = camera_struct(cam)
+    _check(lib().fgs_fourier_energy(_ptr(rgb_gt), ctypes.byref(cs), ctypes.byref(params), _ptr(energy),
+                                    _ptr(threshold), _ptr(ws), ws.numel() * ws.element_size(), _stream()),
+           "fgs_fourier_energy")
 
 
 def fgs_prior_features(rgb, depth, width: int, height: int, seed_xy, n: int, features):

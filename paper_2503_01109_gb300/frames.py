@@ -165,7 +165,8 @@ def render_targets_views(gt_scene: dict, cams: list, tile=(16, 16), batch=128, d
 class FramePipeline:
     def __init__(self, scene: dict, cams: list, gt_scene: dict, capacity: int, tile=(16, 16), batch=128,
                  iters_per_frame: int = 3, device="cuda", loss_w=PAPER_LOSS, reg_w=PAPER_REG, seed_params=None,
-                 prior=None, extra_views: list | None = None, prune: fgs.PruneParams | None = None):
+                 prior=None, extra_views: list | None = None, prune: fgs.PruneParams | None = None,
+                 overlap_seeding: bool = True):
         self.cams = cams
         # Gaussian pruning after each frame's iterations (Sec. III-A): opacity below
         # 0.005 or a scale above 0.5 m (a tenth of the 4 x 3 x 3 m room's extent)
@@ -182,6 +183,7 @@ class FramePipeline:
                                   use_device_count=True, timer=self.kernel_timer)
         from .seeding import Seeder
         self.seeder = Seeder(self.mapper, seed_params, prior)
+        self.side = torch.cuda.Stream(device=device) if overlap_seeding else None
         self.loss_host = torch.zeros(1, dtype=torch.float32).pin_memory()
         self.stage_c = torch.zeros_like(self.colors[0])
         self.stage_d = torch.zeros_like(self.depths[0])
@@ -204,8 +206,16 @@ class FramePipeline:
 
     def frame_step(self, k: int, from_host=None):
         self._use_frame(k % len(self.cams), from_host)
+        cam = self.cams[k % len(self.cams)]
+        # The seeding's frame-only half (the FFTs, E and its threshold) runs on a
+        # second stream beside the render at the frame's pose, whose projection and
+        # binning kernels leave SMs idle; the seeds wait for both.
+        if self.side is not None:
+            self.side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(self.side):
+                self.seeder.compute_energy(self.mapper.color_gt, cam)
         with self.kernel_timer.span("seed"):
-            self.seeder.seed_frame(self.mapper.color_gt, self.mapper.depth_gt, self.cams[k % len(self.cams)])
+            self.seeder.seed_frame(self.mapper.color_gt, self.mapper.depth_gt, cam, energy_stream=self.side)
         for _ in range(self.iters):
             self.mapper.iteration()
         with self.kernel_timer.span("prune"):

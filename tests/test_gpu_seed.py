@@ -15,7 +15,10 @@ pytestmark = pytest.mark.gpu
 SIZES = [(64, 48), (70, 45), (45, 64), (48, 64), (640, 480), (1200, 680)]  # (45, 64): an odd width
 
 
-def run_seed(W, H, seed, with_render=True, max_new=50000, capacity=None, prior=None, pose=None, grids=None):
+def run_seed(W, H, seed, with_render=True, max_new=50000, capacity=None, prior=None, pose=None, grids=None,
+             split=None):
+    """split: None = fgs_fourier_seed; "same_stream" / "side_stream" = fgs_fourier_energy
+    (on the current stream / on a second one) then fgs_fourier_seed_from_energy."""
     fr = syn.textured_frame(W, H, seed)
     cam = syn.pinhole(W, H, 0.9 * W, pose)
     rr = syn.fake_render(W, H, seed + 1) if with_render else None
@@ -34,7 +37,17 @@ def run_seed(W, H, seed, with_render=True, max_new=50000, capacity=None, prior=N
     num_new = torch.zeros(1, dtype=torch.int32, device="cuda")
     thr = torch.zeros(1, dtype=torch.int32, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    fgs.fgs_fourier_seed(rgb, depth, rc, rd, ra, cam, prm, prior, mask, energy, g, num_new, thr, ws, status)
+    if split is None:
+        fgs.fgs_fourier_seed(rgb, depth, rc, rd, ra, cam, prm, prior, mask, energy, g, num_new, thr, ws, status)
+    else:
+        main = torch.cuda.current_stream()
+        side = torch.cuda.Stream() if split == "side_stream" else main
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            fgs.fgs_fourier_energy(rgb, cam, prm, energy, thr, ws)
+        main.wait_stream(side)
+        fgs.fgs_fourier_seed(rgb, depth, rc, rd, ra, cam, prm, prior, mask, energy, g, num_new, thr, ws, status,
+                             from_energy=True)
     torch.cuda.synchronize()
     return {"frame": fr, "cam": cam, "render": rr, "g": g, "mask": mask.view(H, W).cpu().numpy(),
             "energy": energy.view(H, W).cpu().numpy(), "num_new": int(num_new.item()), "threshold": int(thr.item()),
@@ -128,3 +141,20 @@ def test_unsupported_size_is_rejected(cuda_device):
     with pytest.raises(fgs.FGSError):
         fgs.fgs_fourier_seed(t, t, None, None, None, syn.pinhole(W, H, 30.0), fgs.seed_params(max_new=10), None,
                              torch.zeros(W * H, dtype=torch.uint8, device="cuda"), None, g, z, z.clone(), ws)
+
+
+@pytest.mark.parametrize("W,H", [(45, 64), (1200, 680)])
+@pytest.mark.parametrize("split", ["same_stream", "side_stream"])
+def test_energy_then_seeds_equals_one_call(cuda_device, W, H, split):
+    """fgs_fourier_energy followed by fgs_fourier_seed_from_energy (the frame-only half
+    on a second stream, as the frame pipeline runs it) gives fgs_fourier_seed's
+    outputs bit for bit."""
+    ref = run_seed(W, H, seed=5)
+    got = run_seed(W, H, seed=5, split=split)
+    assert ref["num_new"] > 100 and ref["status"] == 0
+    for k in ("num_new", "threshold", "status"):
+        assert got[k] == ref[k], k
+    assert np.array_equal(got["mask"], ref["mask"]) and np.array_equal(got["energy"], ref["energy"])
+    a, b = ref["g"].to_scene(ref["num_new"]), got["g"].to_scene(got["num_new"])
+    for name in a:
+        assert np.array_equal(a[name], b[name]), name
