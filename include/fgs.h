@@ -127,6 +127,8 @@ typedef struct {
  *   tiles of the rect on which q exceeds thr at every pixel centre.
  * in : g (n Gaussians), cams[n_views] (host), tiling.
  * out: out->splat/radius/rect for n_views x g->n records (stride out->stride >= n).
+ *   With g->d_n the slots at or past *g->d_n get radius 0 and keep their splat and
+ *   rect as they were (only the records of live Gaussians are written in full).
  * Failure detection: a Gaussian whose mean, scales exp(log_scales), normalised
  *   quaternion, opacity or colour is not finite is culled from every view (radius
  *   0), and FGS_DEV_NONFINITE is or-ed into *d_status when d_status is not NULL.
@@ -155,9 +157,13 @@ int64_t fgs_num_tiles(const fgs_camera *cams, int32_t n_views, fgs_tiling tiling
  *   the lists are not valid.  The compaction and the depth sort chain their tiles
  *   through decoupled look-backs whose waits are bounded (1 s): one that gives up
  *   sets FGS_DEV_TIMEOUT and the lists are not valid.
+ * n, d_n: the records of slots 0 .. n-1 of every view are binned, or, when d_n
+ *   (device) is not NULL, of slots 0 .. min(n, *d_n) - 1: the live count of a map
+ *   whose count stays on the device, whose records past it fgs_project leaves
+ *   with radius 0 but does not rewrite.
  * err: INVALID_ARGUMENT for small workspace, pair_capacity outside 1..2^31-1, more
  *   than 4096 tile rows over all views, n_views * n above 2^30 - 1. */
-fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const fgs_camera *cams,
+fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const int64_t *d_n, const fgs_camera *cams,
                         int32_t n_views, fgs_tiling tiling, void *ws, size_t ws_bytes,
                         uint32_t *tile_keys, int32_t *ids, int64_t pair_capacity,
                         int32_t *tile_ranges, int64_t *d_num_pairs, int32_t *d_status,

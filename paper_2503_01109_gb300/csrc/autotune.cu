@@ -94,7 +94,7 @@ static fgs_status tune_pass(const fgs_gaussians *g, const fgs_camera *cams, int3
   fgs_gaussians grads{g->n, cap, g->d_n, gr, gr + 3 * cap, gr + 6 * cap, gr + 10 * cap, gr + 11 * cap};
   fgs_status s = fgs_project(g, cams, n_views, t, &proj, status, st);
   if (s != FGS_OK) return s;
-  s = fgs_bin_sort(&proj, g->d_n ? cap : g->n, cams, n_views, t, ws + L.bin, L.bin_bytes,
+  s = fgs_bin_sort(&proj, g->d_n ? cap : g->n, g->d_n, cams, n_views, t, ws + L.bin, L.bin_bytes,
                    reinterpret_cast<uint32_t *>(ws + L.keys), reinterpret_cast<int32_t *>(ws + L.ids), pair_capacity,
                    reinterpret_cast<int32_t *>(ws + L.ranges), num_pairs, status, st);
   if (s != FGS_OK) return s;

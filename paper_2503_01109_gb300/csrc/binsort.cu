@@ -366,8 +366,9 @@ constexpr int kVisTile = kVisThreads * kVisItems;  // 4096 records: ~250 tiles f
 
 __global__ void __launch_bounds__(kVisThreads) k_vis_compact(const float4 *__restrict__ splat,
                                                             const int32_t *__restrict__ radius,
-                                                            const uint2 *__restrict__ rect, int64_t n, int64_t stride,
-                                                            int64_t R, uint32_t *__restrict__ flags,
+                                                            const uint2 *__restrict__ rect, int64_t n_max,
+                                                            const int64_t *__restrict__ d_n, int64_t stride,
+                                                            int64_t R_max, uint32_t *__restrict__ flags,
                                                             uint32_t *__restrict__ ticket, int64_t *__restrict__ total,
                                                             uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
                                                             int32_t *d_status) {
@@ -379,8 +380,13 @@ __global__ void __launch_bounds__(kVisThreads) k_vis_compact(const float4 *__res
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
   __syncthreads();
   const uint32_t t = s_tile;
+  // the records of the live slots only: n per view, the grid sized for n_max
+  const int64_t n = live_count(d_n, n_max), R = R_max / n_max * n;
   const int64_t nt = (R + kVisTile - 1) / kVisTile;
-  if ((int64_t)t >= nt) return;  // (the whole CTA)
+  if ((int64_t)t >= nt) {  // (the whole CTA)
+    if (t == 0 && threadIdx.x == 0) *total = 0;  // no live record at all
+    return;
+  }
   const int64_t j0 = (int64_t)t * kVisTile + warp * (32 * kVisItems) + lane;
   int64_t r[kVisItems];
   int32_t rad[kVisItems];
@@ -1167,7 +1173,7 @@ extern "C" size_t fgs_bin_sort_workspace_size(const fgs_camera *cams, int32_t n_
   return carve(nullptr, n_records, pair_capacity, G.n_rows, G.tx_max).bytes;
 }
 
-extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const fgs_camera *cams,
+extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const int64_t *d_n, const fgs_camera *cams,
                                    int32_t n_views, fgs_tiling tiling, void *ws, size_t ws_bytes,
                                    uint32_t *tile_keys, int32_t *ids, int64_t pair_capacity,
                                    int32_t *tile_ranges, int64_t *d_num_pairs, int32_t *d_status,
@@ -1201,7 +1207,7 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const f
   // ordered compaction of the visible records, then the depth sort over them
   // (4 passes, stable: equal depths keep record order = id order within a view)
   FGS_CUDA(cudaMemsetAsync(w.vis_flags, 0, w.clear_bytes, st), "fgs_bin_sort: clear");
-  pdl_launch(k_vis_compact, (unsigned)nb, kVisThreads, 0, st, splat, proj->radius, rect, n, proj->stride, R,
+  pdl_launch(k_vis_compact, (unsigned)nb, kVisThreads, 0, st, splat, proj->radius, rect, n, d_n, proj->stride, R,
              w.vis_flags, w.vis_flags + nb, w.vis_count, w.dk0, w.dv0, d_status);
   count_launch();
   const SortWs sw = sort_ws(w.sort, R);

@@ -113,9 +113,14 @@ __global__ void k_project(GaussPtrs g, int64_t n, const int64_t *__restrict__ d_
   pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  bool alive = i < live_count(d_n, n);
+  if (i >= live_count(d_n, n)) {  // a slot past the live count: culled, its record otherwise untouched
+#pragma unroll 1
+    for (int v = 0; v < vs.n; ++v) radius[v * stride + i] = 0;
+    return;
+  }
+  bool alive = true;
   GaussLocal L;
-  if (alive) {
+  {
     load_gaussian(g, i, L);
     const bool bad = !gaussian_finite(g, i, L);
     const unsigned m = __ballot_sync(__activemask(), bad);

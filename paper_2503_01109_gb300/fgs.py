@@ -107,8 +107,8 @@ _lib = None
 _SIGS = {
     "fgs_project": ([c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p], c_int32),
     "fgs_num_tiles": ([c_void_p, c_int32, Tiling], c_int64),
-    "fgs_bin_sort": ([c_void_p, c_int64, c_void_p, c_int32, Tiling, c_void_p, c_size_t, c_void_p, c_void_p, c_int64,
-                      c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "fgs_bin_sort": ([c_void_p, c_int64, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_size_t, c_void_p, c_void_p,
+                      c_int64, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "fgs_bin_sort_workspace_size": ([c_void_p, c_int32, Tiling, c_int64, c_int64], c_size_t),
     "fgs_render_fwd": ([c_void_p, c_void_p, c_void_p, c_int32, Tiling, c_void_p, c_void_p, c_void_p, c_void_p,
                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
@@ -380,9 +380,11 @@ def fgs_bin_sort_workspace_size(cams: list, til: Tiling, n_records: int, pair_ca
 
 
 def fgs_bin_sort(proj: Projection, n: int, cams: list, til: Tiling, ws: torch.Tensor, tile_keys: torch.Tensor,
-                 ids: torch.Tensor, tile_ranges: torch.Tensor, num_pairs: torch.Tensor, status: torch.Tensor | None):
+                 ids: torch.Tensor, tile_ranges: torch.Tensor, num_pairs: torch.Tensor, status: torch.Tensor | None,
+                 d_n: torch.Tensor | None = None):
+    """d_n: the map's device live count (int64), bounding the slots binned."""
     ps = proj.struct()
-    _check(lib().fgs_bin_sort(ctypes.byref(ps), int(n), camera_array(cams), len(cams), til, _ptr(ws),
+    _check(lib().fgs_bin_sort(ctypes.byref(ps), int(n), _ptr(d_n), camera_array(cams), len(cams), til, _ptr(ws),
                               ws.numel() * ws.element_size(), _ptr(tile_keys), _ptr(ids), tile_keys.numel(),
                               _ptr(tile_ranges), _ptr(num_pairs), _ptr(status), _stream()), "fgs_bin_sort")
 

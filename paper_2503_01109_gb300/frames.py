@@ -86,7 +86,7 @@ class TimedMapper(Mapper):
         n = self.g.capacity if self.use_dc else self.g.n
         with self.timer.span("bin_sort"):
             fgs.fgs_bin_sort(self.proj, n, self.cams, self.til, self.ws_bin, self.tile_keys, self.ids, self.ranges,
-                             self.num_pairs, self.status)
+                             self.num_pairs, self.status, d_n=self.g.d_n if self.use_dc else None)
         with self.timer.span("render_fwd" if sample_stride == 1 else "render_fwd_sampled"):
             self._blend(sample_stride)
         with self.timer.span("tile_order"):

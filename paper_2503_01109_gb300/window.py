@@ -25,7 +25,7 @@ class Window(Mapper):
         fgs.fgs_project(self.g, self.cams, self.til, self.proj, self.status, self.use_dc)
         n = self.g.capacity if self.use_dc else self.g.n
         fgs.fgs_bin_sort(self.proj, n, self.cams, self.til, self.ws_bin, self.tile_keys, self.ids, self.ranges,
-                         self.num_pairs, self.status)
+                         self.num_pairs, self.status, d_n=self.g.d_n if self.use_dc else None)
         if self.fused_tail:
             self.ensure_clean()
         else:
