@@ -147,7 +147,8 @@ int64_t fgs_num_tiles(const fgs_camera *cams, int32_t n_views, fgs_tiling tiling
  * within the row's strip (float32, a fixed order of rounded steps), ordered by
  * (float32 depth bits, Gaussian id).
  *   tile_keys[k], ids[k] for k < *d_num_pairs: global tile index and Gaussian id,
- *   sorted by (tile, depth, id).  tile_ranges[2*t], [2*t+1] = [start, end) of tile t
+ *   sorted by (tile, depth, id).  tile_keys may be NULL: the renders read only ids
+ *   and tile_ranges, which determine the tile of every pair.  tile_ranges[2*t], [2*t+1] = [start, end) of tile t
  *   (0, 0 for an empty tile).
  * ws/ws_bytes: scratch of at least fgs_bin_sort_workspace_size(cams, n_views,
  *   tiling, n_views*stride, pair_capacity) bytes, 256-byte aligned.

@@ -1057,7 +1057,7 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_emit(RowGeom G, const uint3
         const uint32_t base = __shfl_sync(0xffffffffu, before, bit);
         if ((m >> bit) & 1u) {
           const uint32_t pos = base + __popc(cb & lt);
-          tile_keys[pos] = tbase + (uint32_t)(xb + bit);
+          if (tile_keys) tile_keys[pos] = tbase + (uint32_t)(xb + bit);
           ids[pos] = inf.id;
         }
       }
@@ -1182,7 +1182,7 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const i
   FGS_CHECK_ARG(tiling_ok(tiling), "fgs_bin_sort: unsupported tiling");
   FGS_CHECK_ARG(n >= 0 && proj->stride >= n, "fgs_bin_sort: need 0 <= n <= stride");
   FGS_CHECK_ARG(pair_capacity >= 1 && pair_capacity <= 0x7FFFFFFFll, "fgs_bin_sort: pair_capacity");
-  FGS_CHECK_ARG(tile_keys && ids && tile_ranges && d_num_pairs, "fgs_bin_sort: NULL output");
+  FGS_CHECK_ARG(ids && tile_ranges && d_num_pairs, "fgs_bin_sort: NULL output");
   DevViews vs;
   if (!make_views(cams, n_views, tiling.tile_w, tiling.tile_h, &vs)) return FGS_ERR_INVALID_ARGUMENT;
   FGS_CHECK_ARG((int64_t)n_views * proj->stride < 0xFFFFFFFFll, "fgs_bin_sort: too many records");

@@ -385,7 +385,7 @@ def fgs_bin_sort(proj: Projection, n: int, cams: list, til: Tiling, ws: torch.Te
     """d_n: the map's device live count (int64), bounding the slots binned."""
     ps = proj.struct()
     _check(lib().fgs_bin_sort(ctypes.byref(ps), int(n), _ptr(d_n), camera_array(cams), len(cams), til, _ptr(ws),
-                              ws.numel() * ws.element_size(), _ptr(tile_keys), _ptr(ids), tile_keys.numel(),
+                              ws.numel() * ws.element_size(), _ptr(tile_keys), _ptr(ids), ids.numel(),
                               _ptr(tile_ranges), _ptr(num_pairs), _ptr(status), _stream()), "fgs_bin_sort")
 
 

@@ -180,7 +180,7 @@ class FramePipeline:
             self.extra = render_targets_views(gt_scene, extra_views, tile, batch, device)
         self.g = fgs.GaussianMap.from_scene(scene, capacity, device)
         self.mapper = TimedMapper(self.g, cams[:1], fgs.tiling(*tile, batch), loss_w=loss_w, reg_w=reg_w,
-                                  use_device_count=True, timer=self.kernel_timer)
+                                  use_device_count=True, timer=self.kernel_timer, keep_tile_keys=False)
         from .seeding import Seeder
         self.seeder = Seeder(self.mapper, seed_params, prior)
         self.side = torch.cuda.Stream(device=device) if overlap_seeding else None

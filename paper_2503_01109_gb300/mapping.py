@@ -26,7 +26,7 @@ PAPER_REG = 0.01
 class Mapper:
     def __init__(self, g: fgs.GaussianMap, cams: list, til: fgs.Tiling | None = None, pair_capacity: int | None = None,
                  loss_w=PAPER_LOSS, reg_w: float = PAPER_REG, lr=fgs.DEFAULT_LR, use_device_count: bool = True,
-                 fused_tail: bool = True):
+                 fused_tail: bool = True, keep_tile_keys: bool = True):
         dev = g.buf.device
         self.g, self.cams = g, list(cams)
         self.til = til or fgs.tiling(16, 16, 128)
@@ -40,7 +40,8 @@ class Mapper:
         if pair_capacity is None:
             pair_capacity = min(2 ** 31 - 1, max(1 << 20, 64 * cap * self.V))
         self.pair_capacity = int(pair_capacity)
-        self.tile_keys = torch.zeros(self.pair_capacity, dtype=torch.int32, device=dev)
+        # the pairs' tile indices: redundant with `ranges`, kept for inspection
+        self.tile_keys = torch.zeros(self.pair_capacity, dtype=torch.int32, device=dev) if keep_tile_keys else None
         self.ids = torch.zeros(self.pair_capacity, dtype=torch.int32, device=dev)
         self.ranges = torch.zeros(self.n_tiles, 2, dtype=torch.int32, device=dev)
         # launch order of the render kernels' tiles: heaviest first by the last

@@ -122,6 +122,28 @@ def test_bin_sort_bit_exact(cuda_device, W, H, tw, th, bd, n, views):
     assert np.array_equal(ranges, rranges)
 
 
+def test_bin_sort_without_tile_keys(cuda_device):
+    """tile_keys NULL: the same ids and ranges, and the ranges give back every
+    pair's tile."""
+    sc = syn.tiny_scene(3000, seed=9)
+    cams = cams_for(96, 64, 2)
+    m = make_mapper(sc, cams, (16, 16), 64)
+    m.render()
+    torch.cuda.synchronize()
+    tk, ids, ranges = gpu_lists(m)
+    m.ids.fill_(-1)
+    m.ranges.fill_(-1)
+    fgs.fgs_bin_sort(m.proj, m.g.n, cams, m.til, m.ws_bin, None, m.ids, m.ranges, m.num_pairs, m.status)
+    torch.cuda.synchronize()
+    P = int(m.num_pairs.item())
+    assert P == len(tk) > 1000 and int(m.status.item()) == 0
+    assert np.array_equal(m.ids[:P].cpu().numpy(), ids)
+    r = m.ranges.cpu().numpy()
+    assert np.array_equal(r, ranges)
+    tile_of = np.repeat(np.arange(len(r)), r[:, 1] - r[:, 0])
+    assert np.array_equal(tile_of, tk.astype(np.int64))
+
+
 @pytest.mark.parametrize("W,H,tw,th,bd,n,views", CASES)
 def test_render_forward_matches_oracle(cuda_device, W, H, tw, th, bd, n, views):
     """Teacher-forced splats: colour, depth, alpha, T and contributor counts per
