@@ -350,10 +350,11 @@ def run_ours(args):
     barrier()
     pipe.check()
     stream = torch.cuda.current_stream()
-    # events around the two render kernels only (the roofline's launches); every
-    # other span would end the programmatic-launch overlap at its boundaries, so
-    # the per-call breakdown comes from a separate pass after the timed region
-    pipe.kernel_timer.enable(("render_fwd", "render_bwd"))
+    # events around the adjoint only (the roofline's kernel: the dominant one, as
+    # the breakdown pass shows); every other span would end the programmatic-launch
+    # overlap at its boundaries, so the per-call breakdown comes from a separate
+    # pass after the timed region
+    pipe.kernel_timer.enable(("render_bwd",))
     with ClockSampler(local) as clk:
         barrier()
         l0 = fgs.launch_count()
