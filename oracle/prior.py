@@ -21,7 +21,7 @@ differences are their FP32 accumulation order):
   use     : for a high-frequency seed the predicted opacity logit replaces
             eq11's initial logit, and the predicted log-scales replace eq11's
             radius unless one of the three lies further than max_dev from
-            eq11's log-scale (then all three stay eq11's: eq11 judges the
+            eq11's log-scale (then all three stay eq11's: eq11 bounds the
             prediction's scale and says nothing about opacity); low-frequency
             seeds keep eq11's values.  The distance test is taken in float32.
 GELU is the erf form x Phi(x); its derivative Phi(x) + x phi(x).

@@ -1,6 +1,6 @@
 """What the trained prior gains over eq11 alone.  The prior is trained on the
 GPU from pairs the plain mapping loop produces (seed features at seeding time,
-the seed's parameters after mapping), then judged on held-out seeds: its initial
+the seed's parameters after mapping), then evaluated on held-out seeds: its initial
 log-scales and opacity must lie closer to the converged parameters than eq11's
 (log(d / f) on every axis, logit 0).  The convergence of the loop with and
 without the prior is run as well and must not get worse."""
