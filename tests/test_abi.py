@@ -195,3 +195,29 @@ def test_tile_order_argument_checks(lib):
     assert rc == 1 and b"NULL" in L.fgs_last_error()
     rc = L.fgs_tile_order(cams, 2, til, dummy, dummy, dummy, 4 * tiles - 1, None)
     assert rc == 1 and b"workspace" in L.fgs_last_error()
+
+
+def test_fourier_halves_argument_checks(lib):
+    """fgs_fourier_energy and fgs_fourier_seed_from_energy refuse NULLs, sizes the
+    FFT does not cover and small workspaces before any CUDA call, with their own
+    names in the message."""
+    from paper_2503_01109_gb300 import fgs, synthetic as syn
+    L = fgs.lib()
+    prm = fgs.seed_params(max_new=1000)
+    need = L.fgs_fourier_seed_workspace_size(64, 48, 1000)
+    dummy = ctypes.c_void_p(256)  # never dereferenced: every case fails its checks first
+    cam = fgs.camera_struct(syn.pinhole(64, 48, 60.0))
+    rc = L.fgs_fourier_energy(None, ctypes.byref(cam), ctypes.byref(prm), None, dummy, dummy, need, None)
+    assert rc == 1 and b"fgs_fourier_energy" in L.fgs_last_error()
+    rc = L.fgs_fourier_energy(dummy, ctypes.byref(cam), ctypes.byref(prm), None, dummy, dummy, need - 1, None)
+    assert rc == 1 and b"workspace" in L.fgs_last_error()
+    odd = fgs.camera_struct(syn.pinhole(64 * 19, 48, 60.0))   # a prime factor of 19
+    rc = L.fgs_fourier_energy(dummy, ctypes.byref(odd), ctypes.byref(prm), None, dummy, dummy, 1 << 30, None)
+    assert rc == 5 and b"prime factor" in L.fgs_last_error()
+    g = fgs.Gaussians()
+    g.n, g.capacity = 0, 1000
+    for k in ("means", "log_scales", "quats", "opacity_logits", "rgb"):
+        setattr(g, k, 256)
+    rc = L.fgs_fourier_seed_from_energy(dummy, None, None, None, None, ctypes.byref(cam), ctypes.byref(prm), None,
+                                        dummy, None, ctypes.byref(g), dummy, dummy, None, dummy, need, None, None)
+    assert rc == 1 and b"fgs_fourier_seed_from_energy" in L.fgs_last_error()
