@@ -312,7 +312,7 @@ static SortWs sort_ws(void *base, int64_t cap) {
 // caller has already zeroed w's block.
 static fgs_status radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int64_t *d_count,
                              int64_t host_count, int64_t cap, int bits, const SortWs &w, int32_t *d_status,
-                             cudaStream_t st, bool clear = true) {
+                             cudaStream_t st, bool clear = true, bool hist_ready = false) {
   const int passes = (bits + 7) / 8;
   if (passes < 1 || passes > kSortMaxPasses || cap > (int64_t)kFlagValue) {
     set_error("radix_sort: %d key bits over up to %lld items", bits, (long long)cap);
@@ -320,7 +320,7 @@ static fgs_status radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
   }
   if (clear) FGS_CUDA(cudaMemsetAsync(w.hist, 0, w.bytes, st), "radix_sort: clear");
   const int hist_grid = (int)std::max<int64_t>(1, std::min<int64_t>(w.tiles, 2 * (int64_t)num_sms()));
-  pdl_launch(k_sort_hist, hist_grid, kSortThreads, 0, st, k0, d_count, host_count, cap, bits, w.hist);
+  if (!hist_ready) pdl_launch(k_sort_hist, hist_grid, kSortThreads, 0, st, k0, d_count, host_count, cap, bits, w.hist);
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
     const int nbits = std::min(8, bits - shift);
@@ -329,7 +329,7 @@ static fgs_status radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
     pdl_launch(k_sort_pass, (int)w.tiles, kSortThreads, 0, st, ki, vi, ko, vo, d_count, host_count, cap, shift,
                nbits, w.hist + 256 * p, w.flags + (size_t)p * w.tiles * 256, w.ticket + p, d_status);
   }
-  count_launch(1 + passes);
+  count_launch((hist_ready ? 0 : 1) + passes);
   FGS_CHECK_LAUNCH("radix_sort");
   return FGS_OK;
 }
@@ -371,12 +371,14 @@ __global__ void __launch_bounds__(kVisThreads) k_vis_compact(const float4 *__res
                                                             int64_t R_max, uint32_t *__restrict__ flags,
                                                             uint32_t *__restrict__ ticket, int64_t *__restrict__ total,
                                                             uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                                                            int32_t *d_status) {
+                                                            uint32_t *__restrict__ hist, int32_t *d_status) {
   pdl_enter();
   constexpr int NW = kVisThreads / 32;
   __shared__ uint32_t wsum[32];
   __shared__ uint32_t s_tile, s_excl, s_count;
+  __shared__ uint32_t s_hist[4][256];  // the depth sort's four digit histograms of this tile's keys
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < 4 * 256; i += kVisThreads) (&s_hist[0][0])[i] = 0u;
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
   __syncthreads();
   const uint32_t t = s_tile;
@@ -455,14 +457,31 @@ __global__ void __launch_bounds__(kVisThreads) k_vis_compact(const float4 *__res
   const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
   for (int it = 0; it < kVisItems; ++it) {
-    if ((bal[it] >> lane) & 1u) {
+    const bool mine = (bal[it] >> lane) & 1u;
+    const uint32_t key = mine ? __float_as_uint(splat[2 * r[it] + 1].z) : 0u;  // depth > 0: bits order like it
+    if (mine) {
       const uint32_t q = pos + __popc(bal[it] & lt);
       if ((int64_t)q < R) {  // always, unless a look-back gave up
-        keys[q] = __float_as_uint(splat[2 * r[it] + 1].z);  // depth > 0: its bits order like the value
+        keys[q] = key;
         vals[q] = (uint32_t)r[it];
       }
     }
     pos += __popc(bal[it]);
+    if (hist && bal[it]) {  // lanes with the same digit add once (the high digits repeat across the warp)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const uint32_t d = (key >> (8 * p)) & 255u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, mine ? d : 0xFFFFFFFFu);
+        if (mine && lane == __ffs(peers) - 1) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
+      }
+    }
+  }
+  if (hist) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * 256; i += kVisThreads) {
+      const uint32_t c = (&s_hist[0][0])[i];
+      if (c) atomicAdd(hist + i, c);
+    }
   }
 }
 
@@ -1207,11 +1226,12 @@ extern "C" fgs_status fgs_bin_sort(const fgs_projected *proj, int64_t n, const i
   // ordered compaction of the visible records, then the depth sort over them
   // (4 passes, stable: equal depths keep record order = id order within a view)
   FGS_CUDA(cudaMemsetAsync(w.vis_flags, 0, w.clear_bytes, st), "fgs_bin_sort: clear");
-  pdl_launch(k_vis_compact, (unsigned)nb, kVisThreads, 0, st, splat, proj->radius, rect, n, d_n, proj->stride, R,
-             w.vis_flags, w.vis_flags + nb, w.vis_count, w.dk0, w.dv0, d_status);
-  count_launch();
   const SortWs sw = sort_ws(w.sort, R);
-  fgs_status s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, w.vis_count, 0, R, 32, sw, d_status, st, false);
+  // the compaction also forms the depth sort's four digit histograms (sw.hist, cleared above)
+  pdl_launch(k_vis_compact, (unsigned)nb, kVisThreads, 0, st, splat, proj->radius, rect, n, d_n, proj->stride, R,
+             w.vis_flags, w.vis_flags + nb, w.vis_count, w.dk0, w.dv0, sw.hist, d_status);
+  count_launch();
+  fgs_status s = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, w.vis_count, 0, R, 32, sw, d_status, st, false, true);
   if (s != FGS_OK) return s;
   const uint32_t *srec = w.dv0;
   if (n_views > 1) {
