@@ -391,24 +391,22 @@ __device__ __forceinline__ void render_bwd_tile(const RenderBwdArgs &a, int t, c
     // conic [[a, b], [b, c]] and m the moments above; dL/dopacity = sum e.  The
     // staged conic is (A, B, C) = -log2(e) (a/2, b, c/2), so -o Q m =
     // o ln2 (2A m_x + B m_y, B m_x + 2C m_y).
-    for (int e = threadIdx.x; e < cnt * NF; e += NT) {
-      const int k = e / NF, f = e - k * NF;
-      float val = s_acc[k][f];
-      if (f < 5) {
-        const float4 g0 = s_g0[k];
-        const float cC = s_g1[k].x, o = s_g1[k].y;
-        if (f == 0) val = o * kLn2 * (2.f * g0.z * val + g0.w * s_acc[k][1]);
-        else if (f == 1) val = o * kLn2 * (g0.w * s_acc[k][0] + 2.f * cC * val);
-        else if (f == 3) val = -o * val;
-        else val = -0.5f * o * val;
-      }
-      if (val != 0.f) {
-        const int id = s_id[k];
-        if (f < 7)
-          atomicAdd(a.grad2d + 8 * ((int64_t)v * a.stride + id) + f, val);
-        else
-          atomicAdd(a.grad_rgb + (int64_t)(f - 7) * a.cap + id, val);
-      }
+    // One thread per splat: its seven splat-record fields as two float4 atomics
+    // (each field still receives one add per tile), the colour as three.
+    for (int k = threadIdx.x; k < cnt; k += NT) {
+      const float *m = s_acc[k];
+      const float4 g0 = s_g0[k];
+      const float cC = s_g1[k].x, o = s_g1[k].y;
+      const float4 lo = make_float4(o * kLn2 * (2.f * g0.z * m[0] + g0.w * m[1]),
+                                    o * kLn2 * (g0.w * m[0] + 2.f * cC * m[1]), -0.5f * o * m[2], -o * m[3]);
+      const float4 hi = make_float4(-0.5f * o * m[4], m[5], m[6], 0.f);
+      const int id = s_id[k];
+      float4 *rec = reinterpret_cast<float4 *>(a.grad2d + 8 * ((int64_t)v * a.stride + id));
+      if (lo.x != 0.f || lo.y != 0.f || lo.z != 0.f || lo.w != 0.f) atomicAdd(rec, lo);
+      if (hi.x != 0.f || hi.y != 0.f || hi.z != 0.f) atomicAdd(rec + 1, hi);
+#pragma unroll
+      for (int f = 7; f < NF; ++f)
+        if (m[f] != 0.f) atomicAdd(a.grad_rgb + (int64_t)(f - 7) * a.cap + id, m[f]);
     }
     __syncthreads();
   }
